@@ -1,0 +1,302 @@
+"""Plain FP64 NumPy oracle of the eRTIS energyscape chain.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; never by the library.  It shares no
+code with the CUDA path.
+
+The paper (arXiv 2208.10839) describes the processing in words only:
+
+* Fig. 3 caption and Sec. 4.1 -- the recorded channels go through a matched
+  filter against the emitted broadband FM sweep, a delay-and-sum beamformer
+  forms one beam per direction of interest, and an envelope detector turns
+  each beam into a reflector distribution whose time axis is range.
+* Sec. 4.3 -- filters are applied as FFT convolutions, the filters' group
+  delay is removed, and the envelope is subsampled.
+
+Every function below writes one of those steps out plainly in FP64, with the
+readings of the unstated details given in its docstring:
+
+1. input   x_m[n] = int16 / 32768, n in [0, N)
+2. matched filter + analytic signal (Sec. 4.1, 4.3): with F the smallest
+   power of two >= N + L - 1, A_m[k] = 2 X_m[k] conj(S[k]) for k in
+   [ceil(20 kHz F/fs), floor(80 kHz F/fs)], zero elsewhere;
+   a_m = IFFT_F(A_m)[0:N] (correlation aligned at lag 0, which removes the
+   filter's group delay)
+3. far-field steering delays delta_dm = -fs (p_m . u_d)/c + fs Delta_m
+4. time-domain delay-and-sum (Sec. 4.1): b_d[n] = sum_m g_m I(a_m, n + delta_dm),
+   I = Catmull-Rom (Keys, a = -1/2) interpolation, a = 0 outside [0, N)
+   or frequency-domain delay-and-sum: B_d[k] = sum_m g_m e^{+j 2 pi k delta_dm / F} A_m[k],
+   b_d = IFFT_F(B_d)[0:N]
+5. envelope |b|, zero-phase low-pass FIR h (4R+1 taps) and subsampling by R
+   (Sec. 4.3): E[d][i] = sum_j h[j] |b_d|[R i + j - 2R], i < floor(N/R)
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "fft_length", "band_bins", "to_float", "mf_spectrum", "matched_filter", "catmull_rom",
+    "steering_delays", "das_td", "das_td_bruteforce", "das_fd", "lpf_taps", "envelope_decimate",
+    "energyscape", "steering_matrix", "fd_gemm", "DEFAULT_BAND", "DEFAULT_DECIM",
+]
+
+DEFAULT_BAND = (20e3, 80e3)   # chirp band: the 80 -> 20 kHz sweep
+DEFAULT_DECIM = 10            # R: 8192 samples -> 8192/10 range bins
+
+
+# --------------------------------------------------------------------------
+# sizes
+# --------------------------------------------------------------------------
+def fft_length(n_samples: int, chirp_len: int) -> int:
+    """Smallest power of two F with F >= N + L - 1 (linear, not circular, correlation)."""
+    F = 1
+    while F < n_samples + chirp_len - 1:
+        F *= 2
+    return F
+
+
+def band_bins(F: int, fs: float, band=DEFAULT_BAND):
+    """First and last FFT bin inside the chirp band: ceil(f_lo F/fs), floor(f_hi F/fs)."""
+    k_lo = int(math.ceil(band[0] * F / fs))
+    k_hi = int(math.floor(band[1] * F / fs))
+    return k_lo, k_hi
+
+
+def to_float(x_int16):
+    """Step 1: int16 samples to real values in [-1, 1)."""
+    return np.asarray(x_int16, dtype=np.float64) / 32768.0
+
+
+# --------------------------------------------------------------------------
+# matched filter (Fig. 3, Sec. 4.1; FFT convolution and group delay: Sec. 4.3)
+# --------------------------------------------------------------------------
+def mf_spectrum(x_int16, chirp, fs: float, band=DEFAULT_BAND):
+    """Band-limited one-sided matched-filter spectrum.
+
+    Returns (A, k_lo, F) with A[m][k - k_lo] = 2 X_m[k] conj(S[k]) for the
+    in-band bins k = k_lo..k_hi.  X_m and S are F-point DFTs of the
+    zero-padded channel and chirp.  Multiplying by conj(S) correlates the
+    channel with the sweep; keeping only positive in-band frequencies (x2)
+    makes the inverse transform the analytic signal of the band-limited
+    correlation.
+    """
+    x = to_float(x_int16)
+    s = np.asarray(chirp, dtype=np.float64)
+    M, N = x.shape
+    F = fft_length(N, s.shape[0])
+    k_lo, k_hi = band_bins(F, fs, band)
+    X = np.fft.fft(x, n=F, axis=1)
+    S = np.fft.fft(s, n=F)
+    k = np.arange(k_lo, k_hi + 1)
+    A = 2.0 * X[:, k] * np.conj(S[k])[None, :]
+    return A, k_lo, F
+
+
+def matched_filter(x_int16, chirp, fs: float, band=DEFAULT_BAND, mask: str = "band"):
+    """Analytic matched-filter output a_m[n], n in [0, N) (complex128 [M][N]).
+
+    mask="band": the in-band one-sided spectrum of :func:`mf_spectrum`.
+    mask="analytic": no band limit -- the textbook analytic-signal mask
+    (1 at DC and F/2, 2 on positive bins, 0 on negative bins), so that the
+    real part is exactly the linear correlation sum_l x[n+l] s[l].
+    """
+    x = to_float(x_int16)
+    s = np.asarray(chirp, dtype=np.float64)
+    M, N = x.shape
+    F = fft_length(N, s.shape[0])
+    if mask == "band":
+        A, k_lo, _ = mf_spectrum(x_int16, chirp, fs, band)
+        full = np.zeros((M, F), dtype=np.complex128)
+        full[:, k_lo:k_lo + A.shape[1]] = A
+    elif mask == "analytic":
+        X = np.fft.fft(x, n=F, axis=1)
+        S = np.fft.fft(s, n=F)
+        H = np.zeros(F)
+        H[0] = 1.0
+        H[F // 2] = 1.0
+        H[1:F // 2] = 2.0
+        full = X * np.conj(S)[None, :] * H[None, :]
+    else:
+        raise ValueError(mask)
+    return np.fft.ifft(full, axis=1)[:, :N]
+
+
+# --------------------------------------------------------------------------
+# delay-and-sum (Fig. 3, Sec. 4.1)
+# --------------------------------------------------------------------------
+def catmull_rom(mu):
+    """Catmull-Rom (Keys a = -1/2) weights for taps j-1, j, j+1, j+2 at fraction mu."""
+    mu = np.asarray(mu, dtype=np.float64)
+    mu2 = mu * mu
+    mu3 = mu2 * mu
+    w_m1 = 0.5 * (-mu3 + 2.0 * mu2 - mu)
+    w_0 = 0.5 * (3.0 * mu3 - 5.0 * mu2 + 2.0)
+    w_1 = 0.5 * (-3.0 * mu3 + 4.0 * mu2 + mu)
+    w_2 = 0.5 * (mu3 - mu2)
+    return w_m1, w_0, w_1, w_2
+
+
+def steering_delays(mic_xyz, dirs, fs: float, c: float, delay_s=None):
+    """Far-field steering delays in samples: delta_dm = fs (Delta_m - (p_m . u_d)/c).
+
+    A plane wave from direction u reaches mic m earlier by (p_m . u)/c than
+    the array origin; reading channel m at n + delta_dm lines all channels
+    up on the origin's time axis.  Delta_m is an optional per-mic hardware
+    delay (seconds) that is advanced out.
+    """
+    p = np.asarray(mic_xyz, dtype=np.float64)
+    u = np.asarray(dirs, dtype=np.float64)
+    tau = -(u @ p.T) / c
+    if delay_s is not None:
+        tau = tau + np.asarray(delay_s, dtype=np.float64)[None, :]
+    return fs * tau
+
+
+def _zero_padded(a, pad):
+    M, N = a.shape
+    out = np.zeros((M, N + 2 * pad), dtype=np.complex128)
+    out[:, pad:pad + N] = a
+    return out
+
+
+def das_td(a, delta, gain=None, chunk: int = 64):
+    """Time-domain delay-and-sum with Catmull-Rom fractional delays.
+
+    b_d[n] = sum_m g_m sum_{q=-1..2} w_q(mu) a_m[j+q], with t = n + delta_dm,
+    j = floor(t), mu = t - j, and a_m = 0 outside [0, N).
+    """
+    a = np.asarray(a, dtype=np.complex128)
+    delta = np.asarray(delta, dtype=np.float64)
+    M, N = a.shape
+    D = delta.shape[0]
+    g = np.ones(M) if gain is None else np.asarray(gain, dtype=np.float64)
+    pad = int(math.ceil(np.max(np.abs(delta)))) + 4 if delta.size else 4
+    ap = _zero_padded(a, pad)
+    n = np.arange(N, dtype=np.float64)
+    b = np.zeros((D, N), dtype=np.complex128)
+    for d0 in range(0, D, chunk):
+        dd = delta[d0:d0 + chunk]
+        for m in range(M):
+            t = n[None, :] + dd[:, m:m + 1]
+            j = np.floor(t)
+            w = catmull_rom(t - j)
+            idx = j.astype(np.int64) + pad
+            acc = (w[0] * ap[m][idx - 1] + w[1] * ap[m][idx]
+                   + w[2] * ap[m][idx + 1] + w[3] * ap[m][idx + 2])
+            b[d0:d0 + chunk] += g[m] * acc
+    return b
+
+
+def das_td_bruteforce(a, delta, gain=None):
+    """Triple loop over (d, n, m) of the same definition (tiny inputs only)."""
+    a = np.asarray(a, dtype=np.complex128)
+    M, N = a.shape
+    D = delta.shape[0]
+    g = np.ones(M) if gain is None else gain
+    b = np.zeros((D, N), dtype=np.complex128)
+    for d in range(D):
+        for n in range(N):
+            acc = 0j
+            for m in range(M):
+                t = n + float(delta[d][m])
+                j = math.floor(t)
+                mu = t - j
+                ws = catmull_rom(mu)
+                for q, wq in zip((-1, 0, 1, 2), ws):
+                    if 0 <= j + q < N:
+                        acc += g[m] * float(wq) * a[m][j + q]
+            b[d][n] = acc
+    return b
+
+
+def das_fd(A_band, k_lo: int, F: int, n_samples: int, delta, gain=None):
+    """Frequency-domain delay-and-sum.
+
+    B_d[k] = sum_m g_m exp(+j 2 pi k delta_dm / F) A_m[k] on the in-band bins
+    (zero elsewhere); b_d = IFFT_F(B_d)[0:N].  The +j sign makes the phase
+    ramp a circular advance by delta_dm, matching the time-domain reading.
+    """
+    A_band = np.asarray(A_band, dtype=np.complex128)
+    M, Kb = A_band.shape
+    delta = np.asarray(delta, dtype=np.float64)
+    D = delta.shape[0]
+    g = np.ones(M) if gain is None else np.asarray(gain, dtype=np.float64)
+    k = np.arange(k_lo, k_lo + Kb, dtype=np.float64)
+    b = np.zeros((D, n_samples), dtype=np.complex128)
+    for d in range(D):
+        W = g[None, :] * np.exp(2j * np.pi * np.outer(k, delta[d]) / F)     # [Kb][M]
+        B = np.zeros(F, dtype=np.complex128)
+        B[k_lo:k_lo + Kb] = np.sum(W * A_band.T, axis=1)
+        b[d] = np.fft.ifft(B)[:n_samples]
+    return b
+
+
+# --------------------------------------------------------------------------
+# envelope, low-pass and subsampling (Fig. 3, Sec. 4.1, Sec. 4.3)
+# --------------------------------------------------------------------------
+def lpf_taps(R: int = DEFAULT_DECIM):
+    """Zero-phase low-pass FIR for the envelope: 4R+1 taps, cutoff fs/(2R).
+
+    h[j] ~ sinc(t/R) * (1 + cos(pi t/(2R+1)))/2 with t = j - 2R (a Hann
+    window whose zeros fall one sample beyond the ends), scaled to unit DC
+    gain (sum h = 1).
+    """
+    t = np.arange(-2 * R, 2 * R + 1, dtype=np.float64)
+    h = np.sinc(t / R) * 0.5 * (1.0 + np.cos(np.pi * t / (2 * R + 1)))
+    return h / np.sum(h)
+
+
+def envelope_decimate(b, h, R: int = DEFAULT_DECIM):
+    """E[d][i] = sum_{j=0}^{len(h)-1} h[j] |b_d|[R i + j - (len(h)-1)/2], |b| = 0 outside [0, N)."""
+    env = np.abs(np.asarray(b))
+    D, N = env.shape
+    h = np.asarray(h, dtype=np.float64)
+    half = (h.shape[0] - 1) // 2
+    n_out = N // R
+    ep = np.zeros((D, N + 2 * half + R))
+    ep[:, half:half + N] = env
+    E = np.zeros((D, n_out))
+    for j in range(h.shape[0]):
+        E += h[j] * ep[:, j:j + R * n_out:R]
+    return E
+
+
+def energyscape(x_int16, chirp, mic_xyz, dirs, fs: float, c: float, path: str = "td",
+                R: int = DEFAULT_DECIM, gain=None, delay_s=None, band=DEFAULT_BAND, h=None,
+                return_stages: bool = False):
+    """Whole chain: int16 [M][N] -> energyscape E [D][floor(N/R)]."""
+    N = np.asarray(x_int16).shape[1]
+    delta = steering_delays(mic_xyz, dirs, fs, c, delay_s)
+    h = lpf_taps(R) if h is None else np.asarray(h, dtype=np.float64)
+    if path == "td":
+        a = matched_filter(x_int16, chirp, fs, band)
+        b = das_td(a, delta, gain)
+    elif path == "fd":
+        A, k_lo, F = mf_spectrum(x_int16, chirp, fs, band)
+        a = None
+        b = das_fd(A, k_lo, F, N, delta, gain)
+    else:
+        raise ValueError(path)
+    E = envelope_decimate(b, h, R)
+    if return_stages:
+        return E, dict(a=a, b=b, delta=delta, h=h)
+    return E
+
+
+# --------------------------------------------------------------------------
+# frequency-domain beamforming as a batched complex GEMM
+# --------------------------------------------------------------------------
+def steering_matrix(freqs, mic_xyz, dirs, c: float, gain=None, delay_s=None):
+    """W[k][d][m] = g_m exp(+j 2 pi f_k tau_dm), tau_dm = Delta_m - (p_m . u_d)/c."""
+    tau = steering_delays(mic_xyz, dirs, 1.0, c, delay_s)            # seconds, [D][M]
+    f = np.asarray(freqs, dtype=np.float64)
+    M = tau.shape[1]
+    g = np.ones(M) if gain is None else np.asarray(gain, dtype=np.float64)
+    return g[None, None, :] * np.exp(2j * np.pi * f[:, None, None] * tau[None, :, :])
+
+
+def fd_gemm(W, X):
+    """Y[k][d][t] = sum_m W[k][d][m] X[k][m][t] (per-bin complex matrix product)."""
+    return np.matmul(np.asarray(W, dtype=np.complex128), np.asarray(X, dtype=np.complex128))

@@ -1,0 +1,287 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test ties one step of the oracle to a closed form, an invariant, brute
+force, or an independent library routine, so that a dropped term, a sign
+flip, a transposed operand or an off-by-one in it fails here.  CPU only.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.signal
+
+import oracle as orc
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+FS = synth.FS
+C = synth.C_SOUND
+
+
+def _short_chirp(L=40):
+    n = np.arange(L)
+    return np.hanning(L) * np.cos(2 * np.pi * (0.15 * n + 0.002 * n * n))
+
+
+# -------------------------------------------------------------- sizes / band
+def test_band_bins_golden():
+    rows = [list(map(int, ln.split())) for ln in open(os.path.join(GOLDEN, "band_bins.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    L = synth.chirp_length()
+    assert L == 900
+    for N, F, k_lo, k_hi, Kb, n_out in rows:
+        assert orc.fft_length(N, L) == F
+        assert orc.band_bins(F, FS) == (k_lo, k_hi)
+        assert k_hi - k_lo + 1 == Kb
+        assert N // orc.DEFAULT_DECIM == n_out
+
+
+# -------------------------------------------------------------- matched filter
+def test_mf_analytic_real_part_is_bruteforce_correlation():
+    rng = np.random.default_rng(1)
+    M, N, L = 2, 150, 40
+    x = rng.integers(-3000, 3000, size=(M, N)).astype(np.int16)
+    s = _short_chirp(L)
+    a = orc.matched_filter(x, s, FS, mask="analytic")
+    xf = x.astype(np.float64) / 32768.0
+    F = orc.fft_length(N, L)
+    for m in range(M):
+        # circular correlation over F (no wrap for n < N since F >= N + L - 1)
+        c_circ = np.zeros(F)
+        for n in range(F):
+            for l in range(L):
+                j = (n + l) % F
+                if j < N:
+                    c_circ[n] += xf[m][j] * s[l]
+        np.testing.assert_allclose(a[m].real, c_circ[:N], rtol=0, atol=1e-13)
+        # imaginary part: the textbook analytic signal of the same sequence
+        h = scipy.signal.hilbert(c_circ)
+        np.testing.assert_allclose(a[m].imag, h.imag[:N], rtol=0, atol=1e-12)
+
+
+def test_chirp_autocorrelation_peak_equals_energy():
+    s_q = np.rint(synth.chirp() * 2 ** 14)
+    N = 2048
+    x = np.zeros((1, N), dtype=np.int16)
+    x[0, :s_q.size] = s_q.astype(np.int16)
+    s = s_q / 32768.0                        # the template equals the recorded sweep
+    a = orc.matched_filter(x, s, FS, mask="analytic")
+    energy = float(np.sum(s * s))
+    assert abs(a[0, 0].real - energy) <= 1e-12 * energy
+    # the analytic envelope peaks at lag 0 and |a[0]| >= its real part
+    assert int(np.argmax(np.abs(a[0]))) == 0
+
+
+@pytest.mark.parametrize("n0", [0, 1, 333, 1000])
+def test_mf_band_alignment_integer_onset(n0):
+    s = synth.chirp()
+    N = 4096
+    x = np.zeros((1, N), dtype=np.int16)
+    x[0, n0:n0 + s.size] = np.rint(s * 20000).astype(np.int16)
+    a = orc.matched_filter(x, s.astype(np.float32), FS)
+    assert int(np.argmax(np.abs(a[0]))) == n0
+
+
+def test_mf_band_limit_removes_out_of_band_tone():
+    # a long Hann-windowed 150 kHz tone lies outside [20, 80] kHz: the banded
+    # filter output is tiny while the unbanded one is not.
+    N = 8192
+    n = np.arange(N)
+    tone = np.hanning(N) * np.cos(2 * np.pi * 150e3 / FS * n)
+    x = np.rint(tone * 30000).astype(np.int16)[None, :]
+    s = np.cos(2 * np.pi * 150e3 / FS * np.arange(64)) * np.hanning(64)
+    a_band = orc.matched_filter(x, s, FS)
+    a_full = orc.matched_filter(x, s, FS, mask="analytic")
+    assert np.max(np.abs(a_band)) < 1e-6 * np.max(np.abs(a_full))
+
+
+# -------------------------------------------------------------- interpolation
+def test_catmull_rom_partition_identity_and_quadratics():
+    mu = np.linspace(0, 1, 101)
+    w = orc.catmull_rom(mu)
+    np.testing.assert_allclose(sum(w), 1.0, atol=1e-15)
+    w0 = orc.catmull_rom(0.0)
+    assert [float(v) for v in w0] == [0.0, 1.0, 0.0, 0.0]
+    w1 = orc.catmull_rom(1.0)
+    assert [float(v) for v in w1] == [0.0, 0.0, 1.0, 0.0]
+    j = 7
+    for coeffs in ([2.0, 0, 0], [0.5, -3.0, 0], [1.0, 0.25, -0.75]):
+        f = lambda t: coeffs[0] + coeffs[1] * t + coeffs[2] * t * t
+        interp = sum(wq * f(j + q) for wq, q in zip(w, (-1, 0, 1, 2)))
+        np.testing.assert_allclose(interp, f(j + mu), atol=1e-12)
+    cubic = lambda t: t ** 3
+    interp = sum(wq * cubic(j + q) for wq, q in zip(w, (-1, 0, 1, 2)))
+    assert np.max(np.abs(interp - cubic(j + mu))) > 1e-3      # third order is not reproduced
+
+
+# -------------------------------------------------------------- delay-and-sum
+def test_das_td_vectorised_equals_bruteforce():
+    rng = np.random.default_rng(7)
+    M, N, D = 3, 48, 4
+    a = rng.normal(size=(M, N)) + 1j * rng.normal(size=(M, N))
+    delta = rng.uniform(-12, 12, size=(D, M))
+    delta[0, 0] = -0.25          # reads before sample 0
+    delta[1, 2] = 3.0            # exactly integer
+    g = rng.uniform(0.5, 1.5, size=M)
+    b_vec = orc.das_td(a, delta, g)
+    b_bf = orc.das_td_bruteforce(a, delta, g)
+    np.testing.assert_allclose(b_vec, b_bf, rtol=0, atol=1e-13)
+
+
+def test_das_td_integer_delays_is_plain_shift():
+    rng = np.random.default_rng(8)
+    M, N, D = 4, 64, 3
+    a = rng.normal(size=(M, N)) + 1j * rng.normal(size=(M, N))
+    delta = rng.integers(-9, 9, size=(D, M)).astype(np.float64)
+    b = orc.das_td(a, delta)
+    ref = np.zeros((D, N), dtype=complex)
+    for d in range(D):
+        for m in range(M):
+            s = int(delta[d, m])
+            for n in range(N):
+                if 0 <= n + s < N:
+                    ref[d, n] += a[m, n + s]
+    np.testing.assert_allclose(b, ref, atol=1e-13)
+
+
+def test_steering_delays_sign_convention():
+    # a mic displaced by +x sees a wave from +x (az = +90 deg) earlier by x/c:
+    # it must be read later (positive n index shift is an advance -> negative delta)
+    mic = np.array([[0.01, 0.0, 0.0]])
+    u = synth.unit_vector(np.deg2rad([90.0, -90.0, 0.0]), np.zeros(3))
+    d = orc.steering_delays(mic, u, FS, C)
+    np.testing.assert_allclose(d[:, 0], [-FS * 0.01 / C, FS * 0.01 / C, 0.0], atol=1e-12)
+
+
+def test_td_equals_fd_on_integer_delays():
+    rng = np.random.default_rng(11)
+    M, N, L = 3, 512, 40
+    x = rng.integers(-20000, 20000, size=(M, N)).astype(np.int16)
+    s = _short_chirp(L)
+    fs = 450e3
+    A, k_lo, F = orc.mf_spectrum(x, s, fs)
+    a = orc.matched_filter(x, s, fs)
+    delta = rng.integers(-20, 20, size=(5, M)).astype(np.float64)
+    b_td = orc.das_td(a, delta)
+    b_fd = orc.das_fd(A, k_lo, F, N, delta)
+    lo = int(np.max(np.maximum(0, -delta)))
+    hi = N - int(np.max(np.maximum(0, delta)))
+    np.testing.assert_allclose(b_td[:, lo:hi], b_fd[:, lo:hi], rtol=0, atol=1e-12 * np.max(np.abs(b_td)))
+
+
+def _plane_wave_case(n0=2000, M=8, N=4096, d_star=37):
+    """Mics placed so the true direction has integer delays -k_m; echo onset n0 - k_m."""
+    rng = np.random.default_rng(5)
+    dirs = synth.azimuth_fan(91).astype(np.float64)
+    u = dirs[d_star]
+    perp = np.array([u[2], 0.0, -u[0]])                # in the horizontal plane, orthogonal to u
+    k = rng.integers(-6, 7, size=M)
+    mic = (k[:, None] * (C / FS)) * u[None, :] + rng.uniform(-0.05, 0.05, size=(M, 1)) * perp[None, :]
+    mic += rng.uniform(-0.05, 0.05, size=(M, 1)) * np.array([0.0, 1.0, 0.0])[None, :]
+    s = synth.chirp()
+    sq = np.rint(s * 16000).astype(np.int16)
+    x = np.zeros((M, N), dtype=np.int16)
+    for m in range(M):
+        x[m, n0 - k[m]:n0 - k[m] + s.size] = sq
+    return x, s.astype(np.float32), mic, dirs, k
+
+
+def test_plane_wave_point_reflector_peaks_exactly():
+    n0, M, d_star = 2000, 8, 37
+    x, s, mic, dirs, k = _plane_wave_case(n0, M, 4096, d_star)
+    delta = orc.steering_delays(mic, dirs, FS, C)
+    np.testing.assert_allclose(delta[d_star], -k, atol=1e-9)
+    E = orc.energyscape(x, s, mic, dirs, FS, C)
+    d_pk, i_pk = np.unravel_index(np.argmax(E), E.shape)
+    assert d_pk == d_star
+    assert i_pk == n0 // orc.DEFAULT_DECIM
+    # coherent sum: the beam at the true direction is M times one channel's
+    # matched-filter output (channel 0 shifted to onset n0)
+    single = np.zeros((1, x.shape[1]), dtype=np.int16)
+    single[0, n0:n0 + s.size] = x[0, n0 - k[0]:n0 - k[0] + s.size]
+    a1 = orc.matched_filter(single, s, FS)
+    E1 = orc.envelope_decimate(M * a1, orc.lpf_taps())
+    np.testing.assert_allclose(E[d_star].max(), E1.max(), rtol=1e-12)
+
+
+def test_spherical_scene_peak_near_truth():
+    cfg = synth.single_sensor()
+    E = orc.energyscape(cfg["x"], cfg["chirp"], cfg["mic_xyz"], cfg["dirs"], cfg["fs"], cfg["c"])
+    sc = cfg["scene"]
+    d_pk, i_pk = np.unravel_index(np.argmax(E), E.shape)
+    az = np.deg2rad(np.linspace(-90, 90, 181))
+    hits = []
+    for q in range(sc.pos.shape[0]):
+        r = sc.meta["range"][q]
+        tof_bin = (2 * r / C) * FS / orc.DEFAULT_DECIM
+        d_true = int(np.argmin(np.abs(az - sc.meta["az"][q])))
+        hits.append(abs(i_pk - tof_bin) <= 1.5 and abs(d_pk - d_true) <= 2)
+    assert any(hits)
+
+
+# -------------------------------------------------------------- envelope / LPF
+def test_lpf_unit_dc_gain_and_stopband():
+    R = orc.DEFAULT_DECIM
+    h = orc.lpf_taps(R)
+    assert h.size == 4 * R + 1
+    np.testing.assert_allclose(np.sum(h), 1.0, atol=1e-15)
+    np.testing.assert_allclose(h, h[::-1], atol=0)
+    # response at the first alias of the decimated rate, f = fs/R
+    t = np.arange(-2 * R, 2 * R + 1)
+    resp = abs(np.sum(h * np.exp(-2j * np.pi * t / R)))
+    assert resp < 1e-2
+    # a constant envelope passes unchanged away from the edges
+    b = np.ones((1, 400), dtype=complex) * (3 + 4j)
+    E = orc.envelope_decimate(b, h, R)
+    np.testing.assert_allclose(E[0, 3:-3], 5.0, rtol=1e-14)
+    # at i = 0 only the right half of the taps sees signal
+    np.testing.assert_allclose(E[0, 0], 5.0 * np.sum(h[2 * R:]), rtol=1e-14)
+
+
+def test_envelope_decimate_bruteforce():
+    rng = np.random.default_rng(3)
+    b = rng.normal(size=(2, 97)) + 1j * rng.normal(size=(2, 97))
+    h = rng.uniform(size=9)
+    R = 4
+    E = orc.envelope_decimate(b, h, R)
+    assert E.shape == (2, 97 // R)
+    for d in range(2):
+        for i in range(97 // R):
+            acc = 0.0
+            for j in range(9):
+                n = R * i + j - 4
+                if 0 <= n < 97:
+                    acc += h[j] * abs(b[d, n])
+            assert abs(E[d, i] - acc) < 1e-13
+
+
+# -------------------------------------------------------------- FD GEMM
+def test_steering_matrix_focuses_plane_wave_to_gain_M():
+    mic = synth.mic_array(0).astype(np.float64)
+    dirs = synth.fibonacci_hemisphere(64).astype(np.float64)
+    f = np.array([20e3, 47e3, 80e3])
+    W = orc.steering_matrix(f, mic, dirs, C)
+    d_star = 21
+    # plane wave from u*: mic m is advanced by (p_m . u*)/c -> phase +2 pi f (p.u)/c
+    X = np.exp(2j * np.pi * f[:, None] * (mic @ dirs[d_star])[None, :] / C)[:, :, None]
+    Y = orc.fd_gemm(W, X)[:, :, 0]
+    M = mic.shape[0]
+    np.testing.assert_allclose(Y[:, d_star], M, atol=1e-10)
+    assert np.all(np.abs(Y) <= M + 1e-9)
+    assert np.all(np.argmax(np.abs(Y), axis=1) == d_star)
+
+
+def test_fd_gemm_bruteforce():
+    rng = np.random.default_rng(4)
+    K, D, M, T = 3, 5, 4, 2
+    W = rng.normal(size=(K, D, M)) + 1j * rng.normal(size=(K, D, M))
+    X = rng.normal(size=(K, M, T)) + 1j * rng.normal(size=(K, M, T))
+    Y = orc.fd_gemm(W, X)
+    for k in range(K):
+        for d in range(D):
+            for t in range(T):
+                acc = 0j
+                for m in range(M):
+                    acc += W[k, d, m] * X[k, m, t]
+                assert abs(Y[k, d, t] - acc) < 1e-12
