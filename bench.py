@@ -1,0 +1,296 @@
+"""Throughput benchmark: energyscapes/s at 32 ch x 16384 samples x 2048 directions.
+
+A step is one seeded synthetic measurement (32 mics, 16384 int16 samples,
+20 reflectors on the frontal hemisphere, 20 dB SNR) through the whole chain
+on one GPU: matched filter -> time-domain delay-and-sum over 2048 Fibonacci
+half-sphere directions -> envelope, low-pass, subsample -> energyscape
+2048 x 1638 (FP32).  The input sits in HBM when the clock starts; L2 is
+flushed (a 512 MiB write) between steps, outside the timed events.
+
+Printed (rank 0, one JSON line): value = energyscapes/s over all ranks,
+e2e = the same through rtis_process with pinned host buffers (H2D input and
+D2H energyscape inside the timed region), roofline of the dominant kernel
+(the beamformer, FP32-FMA bound), the FP64 oracle timed on the host as
+cpu_baseline, and SM clocks sampled during the timed region.
+
+--impl reference times the FP64 oracle itself (on a bounded sample of
+directions per step) with the same metric.  Multi-GPU: independent replicas
+(the work shards by measurement; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+N_SAMPLES, N_DIRS, N_MICS = 16384, 2048, 32
+METRIC = "energyscapes/s at 32ch x 16384 samples x 2048 dirs; error vs FP64 oracle"
+WORKLOAD = "hemisphere: 32 mics (12 cm square, seeded), 16384 samples @ 450 kHz, 2048 Fibonacci half-sphere dirs, " \
+           "20 reflectors 0.3-6 m, 20 dB SNR, int16; time-domain Catmull-Rom DAS, FP32"
+FP32_LANES_PER_SM = 128     # FP32 FMA lanes per SM (4 SMSPs x 32)
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample_time(cfg, n_dirs_sample: int, seed: int = 0):
+    """Seconds the FP64 oracle needs for one energyscape, from a direction sample."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(cfg["dirs"].shape[0], n_dirs_sample, replace=False))
+    t0 = time.perf_counter()
+    a = oracle.matched_filter(cfg["x"], cfg["chirp"], cfg["fs"])
+    t1 = time.perf_counter()
+    delta = oracle.steering_delays(cfg["mic_xyz"], cfg["dirs"][pick], cfg["fs"], cfg["c"])
+    b = oracle.das_td(a, delta)
+    oracle.envelope_decimate(b, oracle.lpf_taps())
+    t2 = time.perf_counter()
+    D = cfg["dirs"].shape[0]
+    return (t1 - t0) + (t2 - t1) * D / n_dirs_sample, (t1 - t0), (t2 - t1)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import synth
+    cfg = synth.hemisphere()
+    n_s = 16
+    for _ in range(args.warmup):
+        oracle_sample_time(cfg, n_s)
+    per = []
+    for k in range(args.steps):
+        per.append(oracle_sample_time(cfg, n_s, seed=k + 1)[0])
+    t = float(np.sum(per))
+    value = args.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "energyscapes/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("FP32", "FP64 oracle"), "parallelism": "single process"},
+        "cpu_baseline": {"value": value, "unit": "energyscapes/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: matched filter on all 32 channels + DAS/envelope on {n_s} of "
+                                   f"{N_DIRS} directions, scaled to {N_DIRS}"},
+        "e2e": {"value": value, "unit": "energyscapes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-dirs", type=int, default=128, help="directions in the oracle's timed sample")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import synth
+    from paper_2208_10839_gb300 import Plan, _native as nat
+    from paper_2208_10839_gb300 import build as _b
+    _b.build()
+
+    cfg = synth.hemisphere(seed_scene=1 + 1000 * rank)
+    dev = torch.device("cuda", local)
+    plan = Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"])
+    x = torch.from_numpy(cfg["x"]).to(dev)
+    a = torch.empty((N_MICS, N_SAMPLES), dtype=torch.complex64, device=dev)
+    E = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    def step():
+        nat.rtis_matched_filter(plan.handle, x, a, None, sh)
+        nat.rtis_beamform_td(plan.handle, a, E, sh)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    assert plan.sync() == 0
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0, e1, e2 = evs[k]
+            e0.record(stream)
+            nat.rtis_matched_filter(plan.handle, x, a, None, sh)
+            e1.record(stream)
+            nat.rtis_beamform_td(plan.handle, a, E, sh)
+            e2.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in evs]
+    das_ms = [e1.elapsed_time(e2) for _, e1, e2 in evs]
+    mf_ms = [e0.elapsed_time(e1) for e0, e1, _ in evs]
+    t_total = sum(step_ms) / 1e3
+    bits = plan.sync()
+    assert bits == 0, f"device status {bits:#x}"
+
+    # end to end through rtis_process: pinned host input -> device -> energyscape -> pinned host
+    xh = torch.from_numpy(cfg["x"]).pin_memory()
+    Eh = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32).pin_memory()
+    xd = torch.empty_like(x)
+    for _ in range(3):
+        xd.copy_(xh, non_blocking=True)
+        nat.rtis_process(plan.handle, xd, E, sh)
+        Eh.copy_(E, non_blocking=True)
+    torch.cuda.synchronize()
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(args.steps // 2, 3)
+    ee0.record(stream)
+    for _ in range(e2e_steps):
+        xd.copy_(xh, non_blocking=True)
+        nat.rtis_process(plan.handle, xd, E, sh)
+        Eh.copy_(E, non_blocking=True)
+    ee1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = ee0.elapsed_time(ee1) / 1e3
+
+    if world > 1:
+        tt = torch.tensor([t_total, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total, t_e2e = float(tt[0]), float(tt[1])
+
+    value = world * args.steps / t_total
+    e2e_value = world * e2e_steps / t_e2e
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel: FP32 FMA pipe (D*N*M*4 taps*2 (re,im) FMAs = 2 flops each)
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    flops = float(N_DIRS) * N_SAMPLES * N_MICS * 4 * 2 * 2
+    das_s = statistics.mean(das_ms) / 1e3
+    achieved = flops / das_s / 1e12
+    peak_tf = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "td_beamform_kernel", "achieved": achieved, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": None,
+                "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {SM_MAX_MHZ_NOMINAL:.0f} MHz",
+                "algorithmic_flops_per_launch": flops, "launch_ms": das_s * 1e3,
+                "mf_ms": statistics.mean(mf_ms)}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_observed_clock"] = achieved / (n_sm * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "energyscapes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_mics": N_MICS, "n_samples": N_SAMPLES, "n_dirs": N_DIRS,
+                   "n_out": plan.n_out, "decim": 10, "batch_per_step": 1,
+                   "l2": "flushed (512 MiB write) between steps, outside the timed events",
+                   "parallelism": f"{world} independent replica(s), one measurement per rank per step"},
+        "e2e": {"value": e2e_value, "unit": "energyscapes/s", "h2d_bytes_per_step": int(x.numel() * 2),
+                "d2h_bytes_per_step": int(E.numel() * 4), "call": "rtis_process"},
+        "gpu_launches": 3 * args.steps,
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_es, t_mf, t_das = oracle_sample_time(cfg, args.cpu_dirs)
+        line["cpu_baseline"] = {"value": 1.0 / t_es, "unit": "energyscapes/s", "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 oracle, one process: matched filter on all 32 channels "
+                                          f"({t_mf:.2f} s) + DAS/envelope on {args.cpu_dirs} of {N_DIRS} "
+                                          f"directions ({t_das:.2f} s), scaled to {N_DIRS} directions"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

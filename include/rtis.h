@@ -1,0 +1,170 @@
+/*
+ * rtis.h -- C ABI of the eRTIS energyscape library (one GB300, sm_103a).
+ *
+ * The library turns one recording of the eRTIS in-air imaging sonar (32
+ * microphones, int16 samples, 450 kHz) into an energyscape: an image of
+ * reflector intensity over range x steering direction.  The processing chain
+ * follows the paper's Fig. 3 and Sec. 4.1 (matched filter against the emitted
+ * broadband FM sweep, delay-and-sum beamforming per direction of interest,
+ * envelope detection with the time axis as range) and Sec. 4.3 (filters as
+ * FFT convolutions with their group delay removed, subsampling after the
+ * envelope, device memory allocated once per fixed configuration).
+ *
+ * Definitions used by every entry point (x: int16 input, s: chirp, M mics,
+ * N samples per mic, D directions, L chirp samples, R decimation):
+ *   F        = smallest power of two >= N + L - 1
+ *   k_lo/hi  = ceil(band_lo F/fs), floor(band_hi F/fs)     (in-band FFT bins)
+ *   a_m[n]   = IFFT_F( 2 FFT_F(x_m/32768) conj(FFT_F(s)) on k_lo..k_hi )[n]
+ *   delta_dm = fs (Delta_m - (p_m . u_d)/c)                 (samples)
+ *   TD:  b_d[n] = sum_m g_m sum_{q=-1..2} w_q(mu) a_m[j+q],  j = floor(n+delta_dm),
+ *        mu = n + delta_dm - j, Catmull-Rom weights, a = 0 outside [0, N)
+ *   FD:  b_d = IFFT_F( sum_m g_m exp(+2 pi i k delta_dm/F) A_m[k] )[0:N)
+ *   E[d][i]  = sum_j h[j] |b_d|[R i + j - (len(h)-1)/2],  i < floor(N/R),
+ *        |b| = 0 outside [0, N)
+ *
+ * Conventions
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; they must
+ *     stay valid until the work queued on `stream` has finished.  Host
+ *     arrays passed to rtis_plan_create are copied; the caller keeps them.
+ *   - Complex arrays are interleaved (re, im) float32 pairs.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Every call except create/destroy/sync is asynchronous and
+ *     stream-ordered; none synchronises the device.
+ *   - No C++ exception crosses this interface.  Arguments are checked before
+ *     any launch; a failing call returns a status != RTIS_OK, launches
+ *     nothing, and leaves a message for rtis_last_error() (thread-local).
+ *   - Device-side checks (a steering delay outside the plan's staged range,
+ *     a bounded wait that ran out) never trap: they set bits in the plan's
+ *     status word, which rtis_plan_sync() reads and clears.
+ *   - A plan is not thread-safe: calls on one plan must not overlap on
+ *     different streams, because they share the plan's workspaces.
+ */
+#ifndef RTIS_H
+#define RTIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rtis_plan rtis_plan;
+
+typedef enum rtis_status {
+    RTIS_OK = 0,
+    RTIS_ERR_INVALID_ARG = 1,   /* null pointer, bad size, misaligned pointer */
+    RTIS_ERR_CUDA = 2,          /* a CUDA runtime call failed (message says which) */
+    RTIS_ERR_OOM = 3,           /* device allocation failed in rtis_plan_create */
+    RTIS_ERR_UNSUPPORTED = 4,   /* valid request outside what this build implements */
+    RTIS_ERR_TIMEOUT = 5,       /* a bounded device wait ran out (status word) */
+    RTIS_ERR_NONFINITE = 6,     /* non-finite geometry, chirp or taps */
+    RTIS_ERR_DEVICE = 7         /* a device-side range check failed (status word) */
+} rtis_status;
+
+/* Device status-word bits reported by rtis_plan_sync(). */
+#define RTIS_DEV_DELAY_RANGE 0x1u   /* |floor(delta)| beyond the plan's staged halo */
+#define RTIS_DEV_TIMEOUT     0x2u   /* a bounded mbarrier wait ran out */
+
+enum { RTIS_PATH_TD = 0, RTIS_PATH_FD = 1 };
+enum { RTIS_PREC_FP32 = 0, RTIS_PREC_BF16 = 1, RTIS_PREC_FP16 = 2 };
+
+typedef struct rtis_options {
+    double c;                    /* speed of sound, m/s (default 343) */
+    int decim;                   /* R, envelope subsampling factor (default 10) */
+    int lpf_len;                 /* odd number of envelope low-pass taps; 0 -> 4R+1 */
+    const float* lpf_taps;       /* host [lpf_len]; NULL -> sinc(t/R) x Hann, sum 1 */
+    double band_lo_hz;           /* matched-filter band (default 20e3) */
+    double band_hi_hz;           /* (default 80e3) */
+    int path;                    /* RTIS_PATH_TD (default) or RTIS_PATH_FD */
+    int precision;               /* FD path operand type (RTIS_PREC_*) */
+    double max_delay_s;          /* bound on |Delta_m| set by calibration (default 10e-6) */
+    double position_slack_m;     /* bound on calibrated mic displacement (default 0.01) */
+} rtis_options;
+
+/* Fills *opt with the defaults listed above. */
+void rtis_options_default(rtis_options* opt);
+
+typedef struct rtis_plan_info {
+    int n_mics, n_samples, n_dirs, chirp_len;
+    int fft_len;                 /* F */
+    int k_lo, k_hi;              /* in-band bins */
+    int decim, lpf_len, n_out;   /* n_out = floor(N/R): energyscape row length */
+    int halo;                    /* staged samples each side of a TD tile */
+    int max_shift;               /* largest |floor(delta)| the TD kernel accepts */
+    size_t workspace_bytes;      /* device memory the plan holds */
+} rtis_plan_info;
+
+/*
+ * rtis_plan_create -- validate the configuration and allocate, once, every
+ * device buffer the chain needs (Sec. 4.3: preallocation for fixed sizes).
+ *   mic_xyz     host float [n_mics][3], metres, array frame (faces +z)
+ *   fs          sampling rate, Hz (> 0)
+ *   chirp       host float [chirp_len], the emitted sweep s[n]
+ *   directions  host float [n_dirs][3], unit steering vectors
+ *   n_samples   N, samples per channel; a multiple of 4, 64 <= N <= 65536
+ *   opt         NULL -> defaults
+ * Limits: 1 <= n_mics <= 32; 1 <= n_dirs; chirp_len >= 1; the in-band bins
+ * must number at most F/4 and lie below F/4.  On success *out owns the plan
+ * (free with rtis_plan_destroy); on failure *out is NULL.  Synchronises the
+ * device once (table upload).
+ */
+rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, double fs,
+                             const float* chirp, int chirp_len, const float* directions,
+                             int n_dirs, int n_samples, const rtis_options* opt);
+
+/* Frees the plan and its device memory (synchronises the device). NULL is a no-op. */
+void rtis_plan_destroy(rtis_plan* plan);
+
+/* Sizes derived at creation. */
+rtis_status rtis_plan_get_info(const rtis_plan* plan, rtis_plan_info* info);
+
+/*
+ * rtis_process -- whole chain for one recording (Fig. 3): matched filter,
+ * delay-and-sum on the plan's path (TD or FD), envelope, low-pass, subsample.
+ *   d_in   device int16 [n_mics][n_samples], 8-byte aligned
+ *   d_out  device float [n_dirs][n_out]
+ */
+rtis_status rtis_process(rtis_plan* plan, const int16_t* d_in, float* d_out, void* stream);
+
+/*
+ * rtis_matched_filter -- the matched-filter stage alone (Sec. 4.1/4.3).
+ *   d_in   device int16 [n_mics][n_samples]
+ *   d_a    device complex float [n_mics][n_samples]: a_m[n] as defined above
+ * d_a may be NULL when only the band spectrum is wanted.
+ *   d_A    device complex float [n_mics][k_hi-k_lo+1]: A_m[k] = 2 X_m[k] conj(S[k])/F
+ *          (already divided by F; NULL to skip)
+ */
+rtis_status rtis_matched_filter(rtis_plan* plan, const int16_t* d_in, float* d_a, float* d_A,
+                                void* stream);
+
+/*
+ * rtis_beamform_td -- time-domain delay-and-sum with the fused envelope,
+ * low-pass and subsampling epilogue, from a matched-filter output.
+ *   d_a    device complex float [n_mics][n_samples], 16-byte aligned
+ *   d_out  device float [n_dirs][n_out]
+ */
+rtis_status rtis_beamform_td(rtis_plan* plan, const float* d_a, float* d_out, void* stream);
+
+/*
+ * rtis_steering_table -- the plan's per-(direction, mic) fractional-delay
+ * table, computed on the device in FP64 from the current geometry:
+ *   d_shift   device int32 [n_dirs][n_mics]  floor(delta_dm)
+ *   d_weight  device float [n_dirs][n_mics][4]  g_m w_q(mu), q = -1..2
+ */
+rtis_status rtis_steering_table(rtis_plan* plan, int32_t* d_shift, float* d_weight, void* stream);
+
+/*
+ * rtis_plan_sync -- waits for the device, then reads and clears the plan's
+ * device status word.  Returns RTIS_ERR_DEVICE / RTIS_ERR_TIMEOUT if a
+ * device-side check fired since the last sync (bits in *bits if non-NULL).
+ */
+rtis_status rtis_plan_sync(rtis_plan* plan, unsigned* bits);
+
+const char* rtis_status_string(rtis_status s);
+const char* rtis_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTIS_H */

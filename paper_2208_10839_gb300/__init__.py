@@ -1,0 +1,11 @@
+"""eRTIS in-air imaging sonar energyscape chain on one GB300 (sm_103a).
+
+Matched filter -> delay-and-sum beamforming -> envelope/low-pass/subsample,
+as hand-written CUDA kernels behind a C ABI (include/rtis.h, librtis.so).
+This package is the thin Python binding of that ABI.
+"""
+from . import _native  # noqa: F401
+from ._native import RtisError, lib  # noqa: F401
+from .plan import Plan  # noqa: F401
+
+__all__ = ["Plan", "RtisError", "lib"]

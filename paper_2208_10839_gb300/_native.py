@@ -1,0 +1,182 @@
+"""ctypes binding of the C ABI in include/rtis.h (librtis.so).
+
+Argument marshalling only: every step of the energyscape chain runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams; tensors
+are passed by ``data_ptr()``.  There is no CPU fallback: if the library is
+missing, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librtis.so")
+
+RTIS_OK = 0
+RTIS_ERR_INVALID_ARG = 1
+RTIS_ERR_CUDA = 2
+RTIS_ERR_OOM = 3
+RTIS_ERR_UNSUPPORTED = 4
+RTIS_ERR_TIMEOUT = 5
+RTIS_ERR_NONFINITE = 6
+RTIS_ERR_DEVICE = 7
+RTIS_DEV_DELAY_RANGE = 0x1
+RTIS_DEV_TIMEOUT = 0x2
+RTIS_PATH_TD, RTIS_PATH_FD = 0, 1
+RTIS_PREC_FP32, RTIS_PREC_BF16, RTIS_PREC_FP16 = 0, 1, 2
+
+
+class rtis_options(C.Structure):
+    _fields_ = [
+        ("c", C.c_double),
+        ("decim", C.c_int),
+        ("lpf_len", C.c_int),
+        ("lpf_taps", C.POINTER(C.c_float)),
+        ("band_lo_hz", C.c_double),
+        ("band_hi_hz", C.c_double),
+        ("path", C.c_int),
+        ("precision", C.c_int),
+        ("max_delay_s", C.c_double),
+        ("position_slack_m", C.c_double),
+    ]
+
+
+class rtis_plan_info(C.Structure):
+    _fields_ = [
+        ("n_mics", C.c_int), ("n_samples", C.c_int), ("n_dirs", C.c_int), ("chirp_len", C.c_int),
+        ("fft_len", C.c_int), ("k_lo", C.c_int), ("k_hi", C.c_int),
+        ("decim", C.c_int), ("lpf_len", C.c_int), ("n_out", C.c_int),
+        ("halo", C.c_int), ("max_shift", C.c_int), ("workspace_bytes", C.c_size_t),
+    ]
+
+
+class RtisError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status} ({message})")
+        self.status = status
+
+
+_VP = C.c_void_p
+_PROTOS = {
+    "rtis_options_default": (None, [C.POINTER(rtis_options)]),
+    "rtis_plan_create": (C.c_int, [C.POINTER(_VP), C.POINTER(C.c_float), C.c_int, C.c_double, C.POINTER(C.c_float),
+                                   C.c_int, C.POINTER(C.c_float), C.c_int, C.c_int, C.POINTER(rtis_options)]),
+    "rtis_plan_destroy": (None, [_VP]),
+    "rtis_plan_get_info": (C.c_int, [_VP, C.POINTER(rtis_plan_info)]),
+    "rtis_process": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "rtis_matched_filter": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "rtis_beamform_td": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "rtis_steering_table": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "rtis_plan_sync": (C.c_int, [_VP, C.POINTER(C.c_uint)]),
+    "rtis_status_string": (C.c_char_p, [C.c_int]),
+    "rtis_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded librtis.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"librtis.so not built ({LIB_PATH}); run paper_2208_10839_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _PROTOS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().rtis_last_error().decode()
+
+
+def check(status: int, where: str):
+    if status != RTIS_OK:
+        raise RtisError(status, where, last_error())
+
+
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def ptr(t) -> int | None:
+    """Device address of a tensor (or an int address, or None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def stream_handle(stream=None) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def default_options() -> rtis_options:
+    o = rtis_options()
+    lib().rtis_options_default(C.byref(o))
+    return o
+
+
+def rtis_plan_create(mic_xyz, fs, chirp, directions, n_samples, options: rtis_options | None = None):
+    """Returns an opaque plan handle (int); see include/rtis.h."""
+    mic = np.ascontiguousarray(mic_xyz, dtype=np.float32)
+    ch = np.ascontiguousarray(chirp, dtype=np.float32)
+    dirs = np.ascontiguousarray(directions, dtype=np.float32)
+    h = _VP()
+    st = lib().rtis_plan_create(C.byref(h), _fptr(mic), int(mic.shape[0]), float(fs), _fptr(ch), int(ch.shape[0]),
+                                _fptr(dirs), int(dirs.shape[0]), int(n_samples),
+                                C.byref(options) if options is not None else None)
+    check(st, "rtis_plan_create")
+    return h.value
+
+
+def rtis_plan_destroy(plan):
+    lib().rtis_plan_destroy(plan)
+
+
+def rtis_plan_get_info(plan) -> rtis_plan_info:
+    info = rtis_plan_info()
+    check(lib().rtis_plan_get_info(plan, C.byref(info)), "rtis_plan_get_info")
+    return info
+
+
+def rtis_process(plan, d_in, d_out, stream=None):
+    check(lib().rtis_process(plan, ptr(d_in), ptr(d_out), stream_handle(stream)), "rtis_process")
+
+
+def rtis_matched_filter(plan, d_in, d_a, d_A=None, stream=None):
+    check(lib().rtis_matched_filter(plan, ptr(d_in), ptr(d_a), ptr(d_A), stream_handle(stream)),
+          "rtis_matched_filter")
+
+
+def rtis_beamform_td(plan, d_a, d_out, stream=None):
+    check(lib().rtis_beamform_td(plan, ptr(d_a), ptr(d_out), stream_handle(stream)), "rtis_beamform_td")
+
+
+def rtis_steering_table(plan, d_shift, d_weight, stream=None):
+    check(lib().rtis_steering_table(plan, ptr(d_shift), ptr(d_weight), stream_handle(stream)), "rtis_steering_table")
+
+
+def rtis_plan_sync(plan) -> int:
+    bits = C.c_uint(0)
+    st = lib().rtis_plan_sync(plan, C.byref(bits))
+    if st not in (RTIS_OK, RTIS_ERR_DEVICE, RTIS_ERR_TIMEOUT):
+        check(st, "rtis_plan_sync")
+    return bits.value
+
+
+def rtis_status_string(status: int) -> str:
+    return lib().rtis_status_string(status).decode()

@@ -1,0 +1,420 @@
+// Host side of the C ABI declared in include/rtis.h: argument checks, the
+// plan (tables and workspaces allocated once, paper Sec. 4.3), and the
+// launch sequence of each entry point.  No C++ exception leaves this file.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "rtis_internal.h"
+
+namespace rtis {
+
+namespace {
+thread_local std::string g_last_error;
+
+bool all_finite(const float* v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+template <typename T>
+cudaError_t dev_alloc(T** ptr, size_t count, size_t* total) {
+    *total += count * sizeof(T);
+    return cudaMalloc(reinterpret_cast<void**>(ptr), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+void free_plan_buffers(Plan& p) {
+    void* bufs[] = {p.d_mic, p.d_dirs, p.d_gain, p.d_delay, p.d_tw, p.d_C, p.d_h,
+                    p.d_shift, p.d_wt, p.d_Z, p.d_a, p.d_status};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+}
+
+bool aligned(const void* ptr, size_t a) { return (reinterpret_cast<uintptr_t>(ptr) % a) == 0; }
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+rtis_status fail(rtis_status s, const std::string& msg) {
+    set_error(msg);
+    return s;
+}
+
+rtis_status cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return RTIS_ERR_CUDA;
+}
+
+bool encode_tmap_2d_u64(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                        uint32_t box_rows, std::string* err) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (encode == nullptr) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || fn == nullptr) {
+            *err = "cuTensorMapEncodeTiled entry point not available";
+            return false;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * 8};
+    cuuint32_t box[2] = {box_cols, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *err = "cuTensorMapEncodeTiled failed with CUresult " + std::to_string(static_cast<int>(r));
+        return false;
+    }
+    return true;
+}
+
+}  // namespace rtis
+
+using rtis::Plan;
+using rtis::fail;
+using rtis::cuda_fail;
+
+extern "C" {
+
+void rtis_options_default(rtis_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->c = 343.0;
+    opt->decim = 10;
+    opt->lpf_len = 0;
+    opt->lpf_taps = nullptr;
+    opt->band_lo_hz = 20e3;
+    opt->band_hi_hz = 80e3;
+    opt->path = RTIS_PATH_TD;
+    opt->precision = RTIS_PREC_FP32;
+    opt->max_delay_s = 10e-6;
+    opt->position_slack_m = 0.01;
+}
+
+const char* rtis_status_string(rtis_status s) {
+    switch (s) {
+        case RTIS_OK: return "ok";
+        case RTIS_ERR_INVALID_ARG: return "invalid argument";
+        case RTIS_ERR_CUDA: return "CUDA error";
+        case RTIS_ERR_OOM: return "out of device memory";
+        case RTIS_ERR_UNSUPPORTED: return "unsupported configuration";
+        case RTIS_ERR_TIMEOUT: return "device wait timed out";
+        case RTIS_ERR_NONFINITE: return "non-finite input";
+        case RTIS_ERR_DEVICE: return "device-side check failed";
+    }
+    return "unknown status";
+}
+
+const char* rtis_last_error(void) { return rtis::g_last_error.c_str(); }
+
+rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, double fs, const float* chirp,
+                             int chirp_len, const float* directions, int n_dirs, int n_samples,
+                             const rtis_options* opt_in) {
+    if (!out) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: out is NULL");
+    *out = nullptr;
+    if (!mic_xyz || !chirp || !directions)
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: mic_xyz, chirp and directions must be non-NULL");
+    rtis_options opt;
+    rtis_options_default(&opt);
+    if (opt_in) opt = *opt_in;
+    if (n_mics < 1 || n_mics > rtis::kMaxMics)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: n_mics must be in [1, 32]");
+    if (n_dirs < 1) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: n_dirs must be >= 1");
+    if (chirp_len < 1) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: chirp_len must be >= 1");
+    if (n_samples < 64 || n_samples % 4 != 0)
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: n_samples must be a multiple of 4 and >= 64");
+    if (!(fs > 0.0) || !std::isfinite(fs)) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: fs must be > 0");
+    if (!(opt.c > 0.0) || !std::isfinite(opt.c)) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: c must be > 0");
+    if (opt.decim < 1) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: decim must be >= 1");
+    const int lpf_len = opt.lpf_len ? opt.lpf_len : 4 * opt.decim + 1;
+    if (lpf_len < 1 || lpf_len % 2 == 0 || lpf_len > rtis::kTdWarpSamples - 1)
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: lpf_len must be odd and < 992");
+    if (opt.lpf_len == 0 && opt.lpf_taps != nullptr)
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: lpf_taps given without lpf_len");
+    if (!(opt.band_lo_hz >= 0.0) || !(opt.band_hi_hz > opt.band_lo_hz))
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: need 0 <= band_lo_hz < band_hi_hz");
+    if (!(opt.max_delay_s >= 0.0) || !(opt.position_slack_m >= 0.0))
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: max_delay_s and position_slack_m must be >= 0");
+    if (opt.path != RTIS_PATH_TD && opt.path != RTIS_PATH_FD)
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: unknown path");
+    if (!rtis::all_finite(mic_xyz, 3 * static_cast<size_t>(n_mics)) ||
+        !rtis::all_finite(directions, 3 * static_cast<size_t>(n_dirs)) ||
+        !rtis::all_finite(chirp, chirp_len) || (opt.lpf_taps && !rtis::all_finite(opt.lpf_taps, lpf_len)))
+        return fail(RTIS_ERR_NONFINITE, "rtis_plan_create: non-finite geometry, chirp or taps");
+
+    int64_t F = 1;
+    while (F < static_cast<int64_t>(n_samples) + chirp_len - 1) F *= 2;
+    if (F > 65536 || F < 256)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: FFT length must be in [256, 65536] (N + L - 1 too large)");
+    const int k_lo = static_cast<int>(std::ceil(opt.band_lo_hz * F / fs));
+    const int k_hi = static_cast<int>(std::floor(opt.band_hi_hz * F / fs));
+    if (k_hi < k_lo) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: band holds no FFT bin");
+    if (k_hi >= F / 4)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: band must lie below fs/4");
+    if (n_samples / opt.decim < 1) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: decim larger than N");
+
+    rtis_plan* plan = new (std::nothrow) rtis_plan();
+    if (!plan) return fail(RTIS_ERR_OOM, "rtis_plan_create: host allocation failed");
+    Plan& p = plan->p;
+    p.opt = opt;
+    p.M = n_mics;
+    p.N = n_samples;
+    p.D = n_dirs;
+    p.L = chirp_len;
+    p.F = static_cast<int>(F);
+    p.P = p.F / 4;
+    p.logP = 0;
+    while ((1 << p.logP) < p.P) ++p.logP;
+    p.k_lo = k_lo;
+    p.k_hi = k_hi;
+    p.Kb = k_hi - k_lo + 1;
+    p.R = opt.decim;
+    p.lpf_len = lpf_len;
+    p.n_out = n_samples / opt.decim;
+    p.fs = fs;
+    p.c = opt.c;
+
+    // largest |delta| the geometry (plus calibration slack) can produce
+    double pmax = 0.0, umax = 0.0;
+    for (int m = 0; m < n_mics; ++m) {
+        const double x = mic_xyz[3 * m], y = mic_xyz[3 * m + 1], z = mic_xyz[3 * m + 2];
+        pmax = std::max(pmax, std::sqrt(x * x + y * y + z * z));
+    }
+    for (int d = 0; d < n_dirs; ++d) {
+        const double x = directions[3 * d], y = directions[3 * d + 1], z = directions[3 * d + 2];
+        umax = std::max(umax, std::sqrt(x * x + y * y + z * z));
+    }
+    const double dmax = fs * ((pmax + opt.position_slack_m) * umax / opt.c + opt.max_delay_s);
+    int H = static_cast<int>(std::ceil(dmax)) + 3;
+    H = (H + 3) & ~3;
+    p.H = H;
+    p.Jlim = H - 2;
+    p.td_nbox = (2 * H + rtis::kTdWarpSamples + 2 + rtis::kTdBox - 1) / rtis::kTdBox;
+    p.td_row = p.td_nbox * rtis::kTdBox;
+    p.td_bins_per_tile = (rtis::kTdWarpSamples - lpf_len) / p.R + 1;
+    if (rtis::td_smem_bytes(p) > 227 * 1024) {
+        delete plan;
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: steering delays too large for the staged halo");
+    }
+
+    // ---- host tables (FP64, rounded to float once) ----
+    std::vector<double> cs(F), sn(F);
+    for (int64_t j = 0; j < F; ++j) {
+        const double ang = 2.0 * M_PI * static_cast<double>(j) / static_cast<double>(F);
+        cs[j] = std::cos(ang);
+        sn[j] = -std::sin(ang);
+    }
+    std::vector<float2> tw(F);
+    for (int64_t j = 0; j < F; ++j) tw[j] = make_float2(static_cast<float>(cs[j]), static_cast<float>(sn[j]));
+    // C[k'] = 2 conj(S[k]) / F, S[k] = sum_l s[l] exp(-2 pi i k l / F)
+    std::vector<float2> C(p.Kb);
+    for (int kp = 0; kp < p.Kb; ++kp) {
+        const int64_t k = k_lo + kp;
+        double re = 0.0, im = 0.0;
+        for (int l = 0; l < chirp_len; ++l) {
+            const int64_t idx = (k * l) & (F - 1);
+            re += chirp[l] * cs[idx];
+            im += chirp[l] * sn[idx];
+        }
+        C[kp] = make_float2(static_cast<float>(2.0 * re / F), static_cast<float>(-2.0 * im / F));
+    }
+    std::vector<float> h(lpf_len);
+    if (opt.lpf_taps) {
+        for (int j = 0; j < lpf_len; ++j) h[j] = opt.lpf_taps[j];
+    } else {
+        const int half = (lpf_len - 1) / 2;
+        std::vector<double> hd(lpf_len);
+        double sum = 0.0;
+        for (int j = 0; j < lpf_len; ++j) {
+            const double t = j - half;
+            const double x = t / p.R;
+            const double sinc = (t == 0) ? 1.0 : std::sin(M_PI * x) / (M_PI * x);
+            hd[j] = sinc * 0.5 * (1.0 + std::cos(M_PI * t / (half + 1)));
+            sum += hd[j];
+        }
+        for (int j = 0; j < lpf_len; ++j) h[j] = static_cast<float>(hd[j] / sum);
+    }
+    std::vector<float> ones(n_mics, 1.0f), zeros(n_mics, 0.0f);
+
+    // ---- device buffers, allocated once ----
+    size_t total = 0;
+    cudaError_t e = cudaSuccess;
+#define RTIS_ALLOC(ptr, count)                                   \
+    if (e == cudaSuccess) e = rtis::dev_alloc(&(ptr), (count), &total);
+    RTIS_ALLOC(p.d_mic, 3 * n_mics)
+    RTIS_ALLOC(p.d_dirs, 3 * static_cast<size_t>(n_dirs))
+    RTIS_ALLOC(p.d_gain, n_mics)
+    RTIS_ALLOC(p.d_delay, n_mics)
+    RTIS_ALLOC(p.d_tw, F)
+    RTIS_ALLOC(p.d_C, p.Kb)
+    RTIS_ALLOC(p.d_h, lpf_len)
+    RTIS_ALLOC(p.d_shift, static_cast<size_t>(n_dirs) * n_mics)
+    RTIS_ALLOC(p.d_wt, static_cast<size_t>(n_dirs) * n_mics)
+    RTIS_ALLOC(p.d_Z, static_cast<size_t>(n_mics) * 2 * p.P)
+    RTIS_ALLOC(p.d_a, static_cast<size_t>(n_mics) * n_samples)
+    RTIS_ALLOC(p.d_status, 1)
+#undef RTIS_ALLOC
+    p.bytes = total;
+    if (e != cudaSuccess) {
+        rtis::free_plan_buffers(p);
+        delete plan;
+        cudaGetLastError();
+        return (e == cudaErrorMemoryAllocation) ? fail(RTIS_ERR_OOM, "rtis_plan_create: cudaMalloc failed")
+                                                : cuda_fail(e, "rtis_plan_create: cudaMalloc");
+    }
+#define RTIS_UP(dst, src, bytes) \
+    if (e == cudaSuccess) e = cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice);
+    RTIS_UP(p.d_mic, mic_xyz, 3 * n_mics * sizeof(float))
+    RTIS_UP(p.d_dirs, directions, 3 * static_cast<size_t>(n_dirs) * sizeof(float))
+    RTIS_UP(p.d_gain, ones.data(), n_mics * sizeof(float))
+    RTIS_UP(p.d_delay, zeros.data(), n_mics * sizeof(float))
+    RTIS_UP(p.d_tw, tw.data(), F * sizeof(float2))
+    RTIS_UP(p.d_C, C.data(), p.Kb * sizeof(float2))
+    RTIS_UP(p.d_h, h.data(), lpf_len * sizeof(float))
+#undef RTIS_UP
+    if (e == cudaSuccess) e = cudaMemset(p.d_status, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = rtis::td_configure(p);
+    if (e == cudaSuccess) e = rtis::launch_steering_table(p, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        rtis::free_plan_buffers(p);
+        delete plan;
+        return cuda_fail(e, "rtis_plan_create: table upload");
+    }
+    std::string err;
+    if (!rtis::encode_tmap_2d_u64(&p.tmap_a, p.d_a, static_cast<uint64_t>(n_samples), static_cast<uint64_t>(n_mics),
+                                  rtis::kTdBox, 1, &err)) {
+        rtis::free_plan_buffers(p);
+        delete plan;
+        return fail(RTIS_ERR_CUDA, "rtis_plan_create: " + err);
+    }
+    unsigned bits = 0;
+    cudaMemcpy(&bits, p.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (bits & RTIS_DEV_DELAY_RANGE) {
+        rtis::free_plan_buffers(p);
+        delete plan;
+        return fail(RTIS_ERR_DEVICE, "rtis_plan_create: a steering delay exceeds the staged halo");
+    }
+    *out = plan;
+    return RTIS_OK;
+}
+
+void rtis_plan_destroy(rtis_plan* plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    rtis::free_plan_buffers(plan->p);
+    delete plan;
+}
+
+rtis_status rtis_plan_get_info(const rtis_plan* plan, rtis_plan_info* info) {
+    if (!plan || !info) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_get_info: NULL argument");
+    const Plan& p = plan->p;
+    info->n_mics = p.M;
+    info->n_samples = p.N;
+    info->n_dirs = p.D;
+    info->chirp_len = p.L;
+    info->fft_len = p.F;
+    info->k_lo = p.k_lo;
+    info->k_hi = p.k_hi;
+    info->decim = p.R;
+    info->lpf_len = p.lpf_len;
+    info->n_out = p.n_out;
+    info->halo = p.H;
+    info->max_shift = p.Jlim;
+    info->workspace_bytes = p.bytes;
+    return RTIS_OK;
+}
+
+static rtis_status ensure_table(Plan& p, cudaStream_t st) {
+    if (!p.table_dirty) return RTIS_OK;
+    cudaError_t e = rtis::launch_steering_table(p, st);
+    return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "steering table launch");
+}
+
+rtis_status rtis_matched_filter(rtis_plan* plan, const int16_t* d_in, float* d_a, float* d_A, void* stream) {
+    if (!plan || !d_in) return fail(RTIS_ERR_INVALID_ARG, "rtis_matched_filter: NULL plan or input");
+    if (!rtis::aligned(d_in, 8)) return fail(RTIS_ERR_INVALID_ARG, "rtis_matched_filter: d_in must be 8-byte aligned");
+    if ((d_a && !rtis::aligned(d_a, 8)) || (d_A && !rtis::aligned(d_A, 8)))
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_matched_filter: outputs must be 8-byte aligned");
+    Plan& p = plan->p;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = rtis::launch_mf_forward(p, d_in, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rtis_matched_filter: forward launch");
+    e = rtis::launch_mf_inverse(p, reinterpret_cast<float2*>(d_a), reinterpret_cast<float2*>(d_A), st);
+    if (e != cudaSuccess) return cuda_fail(e, "rtis_matched_filter: inverse launch");
+    return RTIS_OK;
+}
+
+rtis_status rtis_beamform_td(rtis_plan* plan, const float* d_a, float* d_out, void* stream) {
+    if (!plan || !d_a || !d_out) return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_td: NULL argument");
+    if (!rtis::aligned(d_a, 16)) return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_td: d_a must be 16-byte aligned");
+    if (!rtis::aligned(d_out, 4)) return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_td: d_out must be 4-byte aligned");
+    Plan& p = plan->p;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUtensorMap map;
+    std::string err;
+    if (!rtis::encode_tmap_2d_u64(&map, d_a, p.N, p.M, rtis::kTdBox, 1, &err))
+        return fail(RTIS_ERR_CUDA, "rtis_beamform_td: " + err);
+    rtis_status s = ensure_table(p, st);
+    if (s != RTIS_OK) return s;
+    cudaError_t e = rtis::launch_td_beamform(p, map, d_out, st);
+    return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_beamform_td: launch");
+}
+
+rtis_status rtis_process(rtis_plan* plan, const int16_t* d_in, float* d_out, void* stream) {
+    if (!plan || !d_in || !d_out) return fail(RTIS_ERR_INVALID_ARG, "rtis_process: NULL argument");
+    if (!rtis::aligned(d_in, 8)) return fail(RTIS_ERR_INVALID_ARG, "rtis_process: d_in must be 8-byte aligned");
+    if (!rtis::aligned(d_out, 4)) return fail(RTIS_ERR_INVALID_ARG, "rtis_process: d_out must be 4-byte aligned");
+    Plan& p = plan->p;
+    if (p.opt.path != RTIS_PATH_TD)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_process: frequency-domain path not built");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rtis_status s = ensure_table(p, st);
+    if (s != RTIS_OK) return s;
+    cudaError_t e = rtis::launch_mf_forward(p, d_in, st);
+    if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, p.d_a, nullptr, st);
+    if (e == cudaSuccess) e = rtis::launch_td_beamform(p, p.tmap_a, d_out, st);
+    return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_process: launch");
+}
+
+rtis_status rtis_steering_table(rtis_plan* plan, int32_t* d_shift, float* d_weight, void* stream) {
+    if (!plan || !d_shift || !d_weight) return fail(RTIS_ERR_INVALID_ARG, "rtis_steering_table: NULL argument");
+    if (!rtis::aligned(d_weight, 16) || !rtis::aligned(d_shift, 4))
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_steering_table: d_weight must be 16-byte aligned");
+    Plan& p = plan->p;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rtis_status s = ensure_table(p, st);
+    if (s != RTIS_OK) return s;
+    const size_t n = static_cast<size_t>(p.D) * p.M;
+    cudaError_t e = cudaMemcpyAsync(d_shift, p.d_shift, n * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_weight, p.d_wt, n * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_steering_table: copy");
+}
+
+rtis_status rtis_plan_sync(rtis_plan* plan, unsigned* bits_out) {
+    if (!plan) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_sync: NULL plan");
+    Plan& p = plan->p;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "rtis_plan_sync: synchronize");
+    unsigned bits = 0;
+    e = cudaMemcpy(&bits, p.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p.d_status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "rtis_plan_sync: status word");
+    if (bits_out) *bits_out = bits;
+    if (bits & RTIS_DEV_TIMEOUT) return fail(RTIS_ERR_TIMEOUT, "rtis_plan_sync: a bounded device wait ran out");
+    if (bits & RTIS_DEV_DELAY_RANGE)
+        return fail(RTIS_ERR_DEVICE, "rtis_plan_sync: a steering delay exceeded the staged halo");
+    return RTIS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+"""Pythonic wrapper around one rtis_plan (device tensors in, device tensors out)."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native as nat
+
+_PATHS = {"td": nat.RTIS_PATH_TD, "fd": nat.RTIS_PATH_FD}
+_PRECS = {"fp32": nat.RTIS_PREC_FP32, "bf16": nat.RTIS_PREC_BF16, "fp16": nat.RTIS_PREC_FP16}
+
+
+class Plan:
+    """A fixed configuration of the chain with its device buffers (allocated once).
+
+    mic_xyz [M][3] (m), chirp [L], directions [D][3] (unit), n_samples N.
+    """
+
+    def __init__(self, mic_xyz, fs, chirp, directions, n_samples, *, c=343.0, decim=10, lpf_taps=None,
+                 band=(20e3, 80e3), path="td", precision="fp32", max_delay_s=10e-6, position_slack_m=0.01):
+        import torch  # device memory and streams only
+        self._torch = torch
+        o = nat.default_options()
+        o.c = float(c)
+        o.decim = int(decim)
+        self._taps = None
+        if lpf_taps is not None:
+            self._taps = np.ascontiguousarray(lpf_taps, dtype=np.float32)
+            o.lpf_len = int(self._taps.shape[0])
+            o.lpf_taps = self._taps.ctypes.data_as(C.POINTER(C.c_float))
+        o.band_lo_hz, o.band_hi_hz = float(band[0]), float(band[1])
+        o.path = _PATHS[path]
+        o.precision = _PRECS[precision]
+        o.max_delay_s = float(max_delay_s)
+        o.position_slack_m = float(position_slack_m)
+        self.handle = nat.rtis_plan_create(mic_xyz, fs, chirp, directions, n_samples, o)
+        self.info = nat.rtis_plan_get_info(self.handle)
+        self.M, self.N, self.D = self.info.n_mics, self.info.n_samples, self.info.n_dirs
+        self.n_out = self.info.n_out
+        self.Kb = self.info.k_hi - self.info.k_lo + 1
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "handle", None):
+            nat.rtis_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- entry points -------------------------------------------------------
+    def _dev(self):
+        return self._torch.device("cuda", self._torch.cuda.current_device())
+
+    def process(self, x, out=None, stream=None):
+        """int16 [M][N] device tensor -> energyscape float32 [D][n_out]."""
+        if out is None:
+            out = self._torch.empty((self.D, self.n_out), dtype=self._torch.float32, device=x.device)
+        nat.rtis_process(self.handle, x, out, stream)
+        return out
+
+    def matched_filter(self, x, want_a=True, want_spectrum=False, stream=None):
+        t = self._torch
+        a = t.empty((self.M, self.N), dtype=t.complex64, device=x.device) if want_a else None
+        A = t.empty((self.M, self.Kb), dtype=t.complex64, device=x.device) if want_spectrum else None
+        nat.rtis_matched_filter(self.handle, x, a, A, stream)
+        return a, A
+
+    def beamform_td(self, a, out=None, stream=None):
+        if out is None:
+            out = self._torch.empty((self.D, self.n_out), dtype=self._torch.float32, device=a.device)
+        nat.rtis_beamform_td(self.handle, a, out, stream)
+        return out
+
+    def steering_table(self, stream=None):
+        t = self._torch
+        dev = self._dev()
+        shift = t.empty((self.D, self.M), dtype=t.int32, device=dev)
+        weight = t.empty((self.D, self.M, 4), dtype=t.float32, device=dev)
+        nat.rtis_steering_table(self.handle, shift, weight, stream)
+        return shift, weight
+
+    def sync(self) -> int:
+        """Waits for the device; returns (and clears) the device status bits."""
+        return nat.rtis_plan_sync(self.handle)

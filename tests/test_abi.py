@@ -1,0 +1,106 @@
+"""The C ABI library loads on a machine without a GPU, exports every entry
+point include/rtis.h declares, and rejects bad arguments before touching the
+device.  CPU only (no compute calls)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nat():
+    from paper_2208_10839_gb300 import build
+    build.build()
+    from paper_2208_10839_gb300 import _native
+    _native.lib()
+    return _native
+
+
+def declared_entry_points():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(rtis_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_entry_points()
+    for required in ("rtis_plan_create", "rtis_process", "rtis_plan_destroy", "rtis_matched_filter",
+                     "rtis_beamform_td", "rtis_plan_sync", "rtis_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(nat):
+    lib = C.CDLL(nat.LIB_PATH)
+    missing = [n for n in declared_entry_points() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_abi(nat):
+    for n in declared_entry_points():
+        if n in ("rtis_options_default", "rtis_last_error"):
+            continue
+        assert hasattr(nat, n), n
+
+
+def test_options_default(nat):
+    o = nat.default_options()
+    assert o.c == 343.0 and o.decim == 10 and o.lpf_len == 0
+    assert o.band_lo_hz == 20e3 and o.band_hi_hz == 80e3
+    assert o.path == nat.RTIS_PATH_TD and o.precision == nat.RTIS_PREC_FP32
+
+
+def _args():
+    return synth.mic_array(0), synth.chirp().astype(np.float32), synth.azimuth_fan(11)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(n_samples=8190), 1),            # not a multiple of 4
+    (dict(n_samples=32), 1),              # too short
+    (dict(n_samples=70000), 4),           # FFT longer than 65536
+    (dict(fs=-1.0), 1),
+    (dict(mics=40), 4),                   # more than 32 mics
+    (dict(dirs=0), 1),
+    (dict(nan_mic=True), 6),
+    (dict(decim=0), 1),
+    (dict(band=(80e3, 20e3)), 1),
+    (dict(band=(20e3, 150e3)), 4),        # band above fs/4
+])
+def test_plan_create_rejects(nat, kw, status):
+    mic, ch, dirs = _args()
+    if "mics" in kw:
+        mic = np.zeros((kw["mics"], 3), np.float32)
+    if kw.get("nan_mic"):
+        mic = mic.copy()
+        mic[3, 1] = np.nan
+    if "dirs" in kw:
+        dirs = dirs[:kw["dirs"]]
+    o = nat.default_options()
+    if "decim" in kw:
+        o.decim = kw["decim"]
+    if "band" in kw:
+        o.band_lo_hz, o.band_hi_hz = kw["band"]
+    with pytest.raises(nat.RtisError) as ei:
+        nat.rtis_plan_create(mic, kw.get("fs", 450e3), ch, dirs, kw.get("n_samples", 4096), o)
+    assert ei.value.status == status
+    assert nat.last_error()
+
+
+def test_null_arguments(nat):
+    lib = nat.lib()
+    assert lib.rtis_plan_create(None, None, 32, 450e3, None, 900, None, 10, 4096, None) == nat.RTIS_ERR_INVALID_ARG
+    assert lib.rtis_process(None, None, None, None) == nat.RTIS_ERR_INVALID_ARG
+    assert lib.rtis_matched_filter(None, None, None, None, None) == nat.RTIS_ERR_INVALID_ARG
+    assert lib.rtis_beamform_td(None, None, None, None) == nat.RTIS_ERR_INVALID_ARG
+    assert lib.rtis_plan_sync(None, None) == nat.RTIS_ERR_INVALID_ARG
+    lib.rtis_plan_destroy(None)
+    assert nat.rtis_status_string(0) == "ok"
