@@ -19,7 +19,7 @@
 namespace rtis {
 namespace {
 
-__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }  // bank-skew padding
+__host__ __device__ __forceinline__ constexpr int spad(int i) { return i + (i >> 4); }  // bank-skew padding
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
