@@ -161,6 +161,39 @@ rtis_status rtis_steering_table(rtis_plan* plan, int32_t* d_shift, float* d_weig
  */
 rtis_status rtis_plan_sync(rtis_plan* plan, unsigned* bits);
 
+/*
+ * rtis_matched_filter_noalloc -- the matched filter of rtis_matched_filter
+ * for callers that may not allocate device memory: code that runs where
+ * cudaMalloc is not allowed or not wanted (a real-time loop that must never
+ * block in the allocator, a host framework that owns all device memory and
+ * only lends buffers, a process without a plan created beforehand).  The
+ * paper has no counterpart; it allocates once per configuration instead.
+ *
+ * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ * The twiddle table, the chirp spectrum and the half-size spectra live in
+ * one static device array of RTIS_NOALLOC_SCRATCH_BYTES, which every GPU
+ * that loads this library holds until the process exits.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each call
+ * rewrites everything it reads), so calls whose work overlaps on the GPU --
+ * on different streams, or from different threads -- race and corrupt each
+ * other's results: serialise them.
+ *   d_in       device int16 [n_mics][n_samples], 8-byte aligned
+ *   d_chirp    device float [chirp_len], the emitted sweep
+ *   band_*_hz  matched-filter band (the plan default is 20e3 .. 80e3)
+ *   d_a        device complex float [n_mics][n_samples] (or NULL), as rtis_matched_filter
+ *   d_A        device complex float [n_mics][k_hi-k_lo+1] (or NULL), as rtis_matched_filter
+ * Sizes needing more than RTIS_NOALLOC_SCRATCH_BYTES
+ * (8 F + 8 ceil256(K_b) + 16 n_mics F/4 bytes, F = nextpow2(N + L - 1)) are
+ * rejected with RTIS_ERR_INVALID_ARG before anything is launched; 32 mics
+ * with N + L - 1 <= 32768 fit.
+ */
+#define RTIS_NOALLOC_SCRATCH_BYTES (8u << 20)
+rtis_status rtis_matched_filter_noalloc(const int16_t* d_in, int n_mics, int n_samples, const float* d_chirp,
+                                        int chirp_len, double fs, double band_lo_hz, double band_hi_hz,
+                                        float* d_a, float* d_A, void* stream);
+
 const char* rtis_status_string(rtis_status s);
 const char* rtis_last_error(void);
 

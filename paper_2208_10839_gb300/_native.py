@@ -71,6 +71,8 @@ _PROTOS = {
     "rtis_beamform_td": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_steering_table": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_plan_sync": (C.c_int, [_VP, C.POINTER(C.c_uint)]),
+    "rtis_matched_filter_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, C.c_double, C.c_double,
+                                              C.c_double, _VP, _VP, _VP]),
     "rtis_status_string": (C.c_char_p, [C.c_int]),
     "rtis_last_error": (C.c_char_p, []),
 }
@@ -168,6 +170,14 @@ def rtis_beamform_td(plan, d_a, d_out, stream=None):
 
 def rtis_steering_table(plan, d_shift, d_weight, stream=None):
     check(lib().rtis_steering_table(plan, ptr(d_shift), ptr(d_weight), stream_handle(stream)), "rtis_steering_table")
+
+
+def rtis_matched_filter_noalloc(d_in, n_mics, n_samples, d_chirp, chirp_len, fs, band_lo_hz, band_hi_hz,
+                                d_a, d_A=None, stream=None):
+    """Matched filter with no device allocation (static scratch; see include/rtis.h)."""
+    check(lib().rtis_matched_filter_noalloc(ptr(d_in), int(n_mics), int(n_samples), ptr(d_chirp), int(chirp_len),
+                                            float(fs), float(band_lo_hz), float(band_hi_hz), ptr(d_a), ptr(d_A),
+                                            stream_handle(stream)), "rtis_matched_filter_noalloc")
 
 
 def rtis_plan_sync(plan) -> int:
