@@ -10,17 +10,20 @@
 // W = g_m * Catmull-Rom weights of mu = delta_dm - floor(delta_dm) and
 // J = floor(delta_dm) come from a per-(direction, mic) table built in FP64.
 //
-// Tiling (one CTA = 8 directions x 992 consecutive samples, one warp per
-// direction, each lane 31 consecutive samples):
-//   * the channel rows a_m[x0 .. x0 + 992 + 2H) of 4 mics at a time are
-//     staged into shared memory by TMA (2-stage mbarrier ring; samples outside
-//     [0, N) arrive as zeros from the TMA out-of-bounds fill);
-//   * each lane walks its 31 samples with a 4-tap sliding window in
-//     registers: one 8-byte shared load and 8 FMAs per sample and mic, the
-//     per-mic steering values broadcast across the warp by shuffles;
+// Tiling (one CTA = 8 directions x 960 consecutive samples, one warp per
+// direction, each lane 30 consecutive samples):
+//   * the channel rows a_m[x0 .. x0 + 960 + 2H) of 2 mics at a time are
+//     staged into shared memory by TMA (4-deep mbarrier ring; samples outside
+//     [0, N) arrive as zeros from the TMA out-of-bounds fill).  A buffer is
+//     refilled by the last warp of the CTA to finish with it, so warps never
+//     meet at a CTA barrier inside the mic loop;
+//   * each lane loads its 34-sample window as 16-byte pairs (lane stride of
+//     30 samples keeps quarter-warps conflict-free) and accumulates the four
+//     taps with packed (re, im) FP32 FMAs; per-mic steering values are
+//     broadcast across the warp by shuffles;
 //   * the epilogue writes |b| for the tile to shared memory and each warp
 //     filters and subsamples its own direction, storing E coalesced.
-// The tile's 992 samples cover bins_per_tile output bins plus the low-pass
+// The tile's 960 samples cover bins_per_tile output bins plus the low-pass
 // halo, so no beam sample ever goes to global memory.
 #include "ptx.cuh"
 #include "rtis_internal.h"
@@ -71,16 +74,70 @@ struct TdArgs {
     int M, N, D, R, lpf_len, n_out, H, row, nbox, bins_per_tile;
 };
 
+// packed pair helpers: a 64-bit register holding (re, im) of one complex sample
+__device__ __forceinline__ uint64_t pack2(float x, float y) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(uint64_t v) {
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+    return make_float2(x, y);
+}
+// acc += (w, w) * v   -- one packed FP32 FMA on (re, im)
+__device__ __forceinline__ void fma2(uint64_t& acc, uint64_t ww, uint64_t v) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(ww), "l"(v));
+}
+
+// One mic's contribution to a lane's T samples.  `p` points at the 16-byte
+// aligned pair holding the first tap (or the sample before it when ODD).
+template <bool ODD>
+__device__ __forceinline__ void td_mic(uint64_t (&acc)[kTdOutPerThread], const ulonglong2* __restrict__ p,
+                                       uint64_t w0, uint64_t w1, uint64_t w2, uint64_t w3) {
+    constexpr int T = kTdOutPerThread;
+    constexpr int NP = (T + 4) / 2;  // pairs covering T + 3 taps from an even start
+    uint64_t v[2 * NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const ulonglong2 q = p[k];
+        v[2 * k] = q.x;
+        v[2 * k + 1] = q.y;
+    }
+    // blocks of TB outputs: consecutive FMAs hit different accumulators, and
+    // the window is consumed in the order its loads were issued
+    constexpr int TB = 6;
+    static_assert(T % TB == 0, "T must be a multiple of the FMA block");
+#pragma unroll
+    for (int tb = 0; tb < T; tb += TB) {
+#pragma unroll
+        for (int t = tb; t < tb + TB; ++t) fma2(acc[t], w0, v[t + ODD]);
+#pragma unroll
+        for (int t = tb; t < tb + TB; ++t) fma2(acc[t], w1, v[t + 1 + ODD]);
+#pragma unroll
+        for (int t = tb; t < tb + TB; ++t) fma2(acc[t], w2, v[t + 2 + ODD]);
+#pragma unroll
+        for (int t = tb; t < tb + TB; ++t) fma2(acc[t], w3, v[t + 3 + ODD]);
+    }
+}
+
+// Stages are released without CTA barriers: after a warp finishes a stage it
+// bumps that buffer's counter, and the last of the CTA's warps to do so
+// issues the TMA refill.  Waits are bounded; a timeout sets the status word,
+// stops this thread's compute, and the CTA drains its copies before exit.
 __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
     td_beamform_kernel(const __grid_constant__ CUtensorMap tmap, const TdArgs args) {
     constexpr int NT = 32 * kTdDirsPerCta;
     constexpr int MS = kTdMicsPerStage;
+    constexpr int NS = kTdStages;
     constexpr int T = kTdOutPerThread;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int row = args.row;
     float2* stage = reinterpret_cast<float2*>(smem_raw);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + static_cast<size_t>(kTdStages) * MS * row * 8);
-    float* hs = reinterpret_cast<float*>(bar + kTdStages);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + static_cast<size_t>(NS) * MS * row * 8);
+    int* done = reinterpret_cast<int*>(bar + NS);
+    int* issued = done + NS;
+    float* hs = reinterpret_cast<float*>(issued + NS);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int d = blockIdx.x * kTdDirsPerCta + warp;
@@ -92,26 +149,31 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
     const int nstages = (M + MS - 1) / MS;
     const uint32_t stage_bytes = static_cast<uint32_t>(MS * args.nbox * kTdBox * 8);
 
-    auto issue = [&](int s) {
-        const int b = s % kTdStages;
+    auto issue = [&](int st) {
+        const int b = st % NS;
+        issued[b] += 1;
         ptx::mbar_arrive_expect_tx(&bar[b], stage_bytes);
         for (int mi = 0; mi < MS; ++mi) {
             float2* dst = stage + static_cast<size_t>(b * MS + mi) * row;
             for (int bx = 0; bx < args.nbox; ++bx)
-                ptx::tma_load_2d(dst + bx * kTdBox, &tmap, x0 + bx * kTdBox, s * MS + mi, &bar[b]);
+                ptx::tma_load_2d(dst + bx * kTdBox, &tmap, x0 + bx * kTdBox, st * MS + mi, &bar[b]);
         }
     };
 
     if (threadIdx.x == 0) {
         ptx::prefetch_tmap(&tmap);
-        for (int s = 0; s < kTdStages; ++s) ptx::mbar_init(&bar[s], 1);
+        for (int b = 0; b < NS; ++b) {
+            ptx::mbar_init(&bar[b], 1);
+            done[b] = 0;
+            issued[b] = 0;
+        }
         ptx::fence_mbar_init();
         ptx::fence_proxy_async();
     }
     for (int j = threadIdx.x; j < args.lpf_len; j += NT) hs[j] = args.h[j];
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kTdStages && s < nstages; ++s) issue(s);
+        for (int st = 0; st < NS && st < nstages; ++st) issue(st);
     }
 
     // lane m of each warp holds the steering entry of mic m for this warp's direction
@@ -123,63 +185,62 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
         my_w = __ldg(args.wt + static_cast<size_t>(d) * M + lane);
     }
 
-    float2 acc[T];
+    uint64_t acc[T];
 #pragma unroll
-    for (int t = 0; t < T; ++t) acc[t] = make_float2(0.f, 0.f);
+    for (int t = 0; t < T; ++t) acc[t] = 0ull;
     const int lane_base = n_start - x0 + lane * T - 1;  // smem index of a[n_start + lane*T - 1]
 
-    int s = 0;
     bool timed_out = false;
-    for (; s < nstages; ++s) {
-        const int b = s % kTdStages;
-        const uint32_t par = static_cast<uint32_t>((s / kTdStages) & 1);
-        const bool ok = ptx::mbar_wait_bounded(&bar[b], par, kWaitPolls);
-        if (__syncthreads_or(!ok)) {
-            timed_out = true;
-            break;
+    for (int st = 0; st < nstages; ++st) {
+        const int b = st % NS;
+        if (!timed_out) {
+            const uint32_t par = static_cast<uint32_t>((st / NS) & 1);
+            if (!ptx::mbar_wait_bounded(&bar[b], par, kWaitPolls)) {
+                timed_out = true;
+                atomicOr(args.status, RTIS_DEV_TIMEOUT);
+            }
         }
-        if (dir_ok) {
+        if (dir_ok && !__any_sync(0xffffffffu, timed_out)) {
 #pragma unroll 1
             for (int mi = 0; mi < MS; ++mi) {
-                const int m = s * MS + mi;
+                const int m = st * MS + mi;
                 if (m >= M) break;
                 const int J = __shfl_sync(0xffffffffu, my_shift, m);
-                const float w0 = __shfl_sync(0xffffffffu, my_w.x, m);
-                const float w1 = __shfl_sync(0xffffffffu, my_w.y, m);
-                const float w2 = __shfl_sync(0xffffffffu, my_w.z, m);
-                const float w3 = __shfl_sync(0xffffffffu, my_w.w, m);
-                const float2* rp = stage + static_cast<size_t>(b * MS + mi) * row + lane_base + J;
-                float2 v0 = rp[0], v1 = rp[1], v2 = rp[2];
-#pragma unroll
-                for (int t = 0; t < T; ++t) {
-                    const float2 v3 = rp[t + 3];
-                    float ax = acc[t].x, ay = acc[t].y;
-                    ax = fmaf(w0, v0.x, ax);
-                    ay = fmaf(w0, v0.y, ay);
-                    ax = fmaf(w1, v1.x, ax);
-                    ay = fmaf(w1, v1.y, ay);
-                    ax = fmaf(w2, v2.x, ax);
-                    ay = fmaf(w2, v2.y, ay);
-                    ax = fmaf(w3, v3.x, ax);
-                    ay = fmaf(w3, v3.y, ay);
-                    acc[t] = make_float2(ax, ay);
-                    v0 = v1;
-                    v1 = v2;
-                    v2 = v3;
+                const float f0 = __shfl_sync(0xffffffffu, my_w.x, m);
+                const float f1 = __shfl_sync(0xffffffffu, my_w.y, m);
+                const float f2 = __shfl_sync(0xffffffffu, my_w.z, m);
+                const float f3 = __shfl_sync(0xffffffffu, my_w.w, m);
+                const int s0 = lane_base + J;  // parity is warp-uniform (T even)
+                const ulonglong2* p =
+                    reinterpret_cast<const ulonglong2*>(stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
+                if (s0 & 1)
+                    td_mic<true>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+                else
+                    td_mic<false>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+            }
+        }
+        // release buffer b; the CTA's last warp to get here refills it
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            const int prev = atomicAdd(&done[b], 1);
+            if (prev == kTdDirsPerCta - 1) {
+                done[b] = 0;
+                __threadfence_block();
+                if (st + NS < nstages) {
+                    ptx::fence_proxy_async();
+                    issue(st + NS);
                 }
             }
         }
-        __syncthreads();  // buffer b fully consumed
-        if (threadIdx.x == 0 && s + kTdStages < nstages) issue(s + kTdStages);
     }
 
-    if (timed_out) {
-        // report, then give copies still in flight a bounded chance to land
+    if (__syncthreads_or(timed_out)) {
+        // give copies still in flight a bounded chance to land, then leave
         if (threadIdx.x == 0) {
-            atomicOr(args.status, RTIS_DEV_TIMEOUT);
-            for (int r = s; r < nstages && r < s + kTdStages; ++r)
-                ptx::mbar_wait_bounded(&bar[r % kTdStages], static_cast<uint32_t>((r / kTdStages) & 1),
-                                       kWaitPolls);
+            for (int b = 0; b < NS; ++b)
+                if (issued[b] > 0)
+                    ptx::mbar_wait_bounded(&bar[b], static_cast<uint32_t>((issued[b] - 1) & 1), kWaitPolls);
         }
         __syncthreads();
         return;
@@ -190,8 +251,8 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
 #pragma unroll
     for (int t = 0; t < T; ++t) {
         const int n = n_start + lane * T + t;
-        const float e = (n >= 0 && n < args.N) ? sqrtf(acc[t].x * acc[t].x + acc[t].y * acc[t].y) : 0.f;
-        env[lane * T + t] = e;
+        const float2 v = unpack2(acc[t]);
+        env[lane * T + t] = (n >= 0 && n < args.N) ? sqrtf(v.x * v.x + v.y * v.y) : 0.f;
     }
     __syncwarp();
     if (dir_ok) {
@@ -221,7 +282,7 @@ cudaError_t launch_steering_table(Plan& p, cudaStream_t st) {
 }
 
 size_t td_smem_bytes(const Plan& p) {
-    return static_cast<size_t>(kTdStages) * kTdMicsPerStage * p.td_row * 8 + kTdStages * 8 +
+    return static_cast<size_t>(kTdStages) * kTdMicsPerStage * p.td_row * 8 + kTdStages * (8 + 4 + 4) +
            static_cast<size_t>(p.lpf_len) * 4;
 }
 

@@ -199,7 +199,8 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     H = (H + 3) & ~3;
     p.H = H;
     p.Jlim = H - 2;
-    p.td_nbox = (2 * H + rtis::kTdWarpSamples + 2 + rtis::kTdBox - 1) / rtis::kTdBox;
+    // a lane reads pairs from an even index up to lane_base + Jlim + T + 3
+    p.td_nbox = (H + p.Jlim + rtis::kTdWarpSamples + 4 + rtis::kTdBox - 1) / rtis::kTdBox;
     p.td_row = p.td_nbox * rtis::kTdBox;
     p.td_bins_per_tile = (rtis::kTdWarpSamples - lpf_len) / p.R + 1;
     if (rtis::td_smem_bytes(p) > 227 * 1024) {

@@ -15,11 +15,11 @@ namespace rtis {
 // ----------------------------------------------------------------------------
 // time-domain beamformer tiling (kernels_das.cu)
 // ----------------------------------------------------------------------------
-constexpr int kTdOutPerThread = 31;                   // odd: conflict-free smem rows
+constexpr int kTdOutPerThread = 30;                   // even: 16-byte pair loads, conflict-free
 constexpr int kTdWarpSamples = 32 * kTdOutPerThread;  // samples one warp beamforms
 constexpr int kTdDirsPerCta = 8;                      // one warp per direction
-constexpr int kTdMicsPerStage = 4;                    // mics per TMA stage
-constexpr int kTdStages = 2;                          // smem ring depth
+constexpr int kTdMicsPerStage = 2;                    // mics per TMA stage
+constexpr int kTdStages = 4;                          // smem ring depth
 constexpr int kTdBox = 256;                           // TMA box width (8-byte elements)
 constexpr int kMaxMics = 32;                          // lanes hold per-mic steering
 
