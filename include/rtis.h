@@ -162,6 +162,35 @@ rtis_status rtis_steering_table(rtis_plan* plan, int32_t* d_shift, float* d_weig
 rtis_status rtis_plan_sync(rtis_plan* plan, unsigned* bits);
 
 /*
+ * Frequency-domain delay-and-sum as a batched complex GEMM (the phase-ramp
+ * form of the paper's delay-and-sum, Fig. 3 / Sec. 4.1, evaluated per
+ * frequency), on the tcgen05 tensor cores:
+ *
+ *   Y[k][d][t] = sum_m W[k][d][m] X[k][m][t],
+ *   W[k][d][m] = g_m exp(+2 pi i f_k tau_dm),  tau_dm = Delta_m - (p_m . u_d)/c
+ *
+ * The steering matrix W is generated on the device (phase in compensated
+ * FP32) and never stored.  precision: RTIS_PREC_BF16 or RTIS_PREC_FP16
+ * operands with FP32 accumulation and per-channel power-of-two scaling, or
+ * RTIS_PREC_FP32 (three BF16 products hi.hi + hi.lo + lo.hi).
+ *
+ * rtis_fd_gemm_create
+ *   mic_xyz    host float [n_mics][3] (n_mics <= 32), directions host float [n_dirs][3]
+ *   freqs_hz   host double [n_bins], bin frequencies f_k
+ *   n_frames   T, 1 <= T <= 64
+ *   gain, delay_s  host float [n_mics] or NULL (1 and 0)
+ * rtis_fd_gemm_run
+ *   d_X  device complex float [n_bins][n_mics][n_frames], 8-byte aligned
+ *   d_Y  device complex float [n_bins][n_dirs][n_frames], 16-byte aligned
+ */
+typedef struct rtis_fd_gemm rtis_fd_gemm;
+rtis_status rtis_fd_gemm_create(rtis_fd_gemm** out, const float* mic_xyz, int n_mics, const float* directions,
+                                int n_dirs, const double* freqs_hz, int n_bins, int n_frames, double c,
+                                const float* gain, const float* delay_s, int precision);
+rtis_status rtis_fd_gemm_run(rtis_fd_gemm* g, const float* d_X, float* d_Y, void* stream);
+void rtis_fd_gemm_destroy(rtis_fd_gemm* g);
+
+/*
  * rtis_matched_filter_noalloc -- the matched filter of rtis_matched_filter
  * for callers that may not allocate device memory: code that runs where
  * cudaMalloc is not allowed or not wanted (a real-time loop that must never

@@ -73,6 +73,11 @@ _PROTOS = {
     "rtis_plan_sync": (C.c_int, [_VP, C.POINTER(C.c_uint)]),
     "rtis_matched_filter_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, C.c_double, C.c_double,
                                               C.c_double, _VP, _VP, _VP]),
+    "rtis_fd_gemm_create": (C.c_int, [C.POINTER(_VP), C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_float), C.c_int,
+                                      C.POINTER(C.c_double), C.c_int, C.c_int, C.c_double, C.POINTER(C.c_float),
+                                      C.POINTER(C.c_float), C.c_int]),
+    "rtis_fd_gemm_run": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "rtis_fd_gemm_destroy": (None, [_VP]),
     "rtis_status_string": (C.c_char_p, [C.c_int]),
     "rtis_last_error": (C.c_char_p, []),
 }
@@ -178,6 +183,31 @@ def rtis_matched_filter_noalloc(d_in, n_mics, n_samples, d_chirp, chirp_len, fs,
     check(lib().rtis_matched_filter_noalloc(ptr(d_in), int(n_mics), int(n_samples), ptr(d_chirp), int(chirp_len),
                                             float(fs), float(band_lo_hz), float(band_hi_hz), ptr(d_a), ptr(d_A),
                                             stream_handle(stream)), "rtis_matched_filter_noalloc")
+
+
+def rtis_fd_gemm_create(mic_xyz, directions, freqs_hz, n_frames, c=343.0, gain=None, delay_s=None,
+                        precision=RTIS_PREC_FP32):
+    """Frequency-domain beamforming GEMM plan (see include/rtis.h); returns a handle."""
+    mic = np.ascontiguousarray(mic_xyz, dtype=np.float32)
+    dirs = np.ascontiguousarray(directions, dtype=np.float32)
+    fr = np.ascontiguousarray(freqs_hz, dtype=np.float64)
+    g = None if gain is None else np.ascontiguousarray(gain, dtype=np.float32)
+    dl = None if delay_s is None else np.ascontiguousarray(delay_s, dtype=np.float32)
+    h = _VP()
+    st = lib().rtis_fd_gemm_create(C.byref(h), _fptr(mic), int(mic.shape[0]), _fptr(dirs), int(dirs.shape[0]),
+                                   fr.ctypes.data_as(C.POINTER(C.c_double)), int(fr.shape[0]), int(n_frames),
+                                   float(c), None if g is None else _fptr(g), None if dl is None else _fptr(dl),
+                                   int(precision))
+    check(st, "rtis_fd_gemm_create")
+    return h.value
+
+
+def rtis_fd_gemm_run(g, d_X, d_Y, stream=None):
+    check(lib().rtis_fd_gemm_run(g, ptr(d_X), ptr(d_Y), stream_handle(stream)), "rtis_fd_gemm_run")
+
+
+def rtis_fd_gemm_destroy(g):
+    lib().rtis_fd_gemm_destroy(g)
 
 
 def rtis_plan_sync(plan) -> int:

@@ -51,8 +51,8 @@ rtis_status cuda_fail(cudaError_t e, const char* what) {
     return RTIS_ERR_CUDA;
 }
 
-bool encode_tmap_2d_u64(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols,
-                        uint32_t box_rows, std::string* err) {
+bool encode_tmap(CUtensorMap* map, CUtensorMapDataType dtype, uint32_t rank, const void* base, const uint64_t* dims,
+                 const uint64_t* strides, const uint32_t* box, CUtensorMapSwizzle swizzle, std::string* err) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (encode == nullptr) {
         void* fn = nullptr;
@@ -64,18 +64,31 @@ bool encode_tmap_2d_u64(CUtensorMap* map, const void* base, uint64_t cols, uint6
         }
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    cuuint64_t dims[2] = {cols, rows};
-    cuuint64_t strides[1] = {cols * 8};
-    cuuint32_t box[2] = {box_cols, box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    cuuint64_t d[5];
+    cuuint64_t st[4];
+    cuuint32_t bx[5], es[5];
+    for (uint32_t i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        bx[i] = box[i];
+        es[i] = 1;
+        if (i + 1 < rank) st[i] = strides[i];
+    }
+    CUresult r = encode(map, dtype, rank, const_cast<void*>(base), d, st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         *err = "cuTensorMapEncodeTiled failed with CUresult " + std::to_string(static_cast<int>(r));
         return false;
     }
     return true;
+}
+
+bool encode_tmap_2d_u64(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                        uint32_t box_rows, std::string* err) {
+    const uint64_t dims[2] = {cols, rows};
+    const uint64_t strides[1] = {cols * 8};
+    const uint32_t box[2] = {box_cols, box_rows};
+    return encode_tmap(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       err);
 }
 
 }  // namespace rtis
@@ -400,6 +413,108 @@ rtis_status rtis_steering_table(rtis_plan* plan, int32_t* d_shift, float* d_weig
     cudaError_t e = cudaMemcpyAsync(d_shift, p.d_shift, n * sizeof(int), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_weight, p.d_wt, n * sizeof(float4), cudaMemcpyDeviceToDevice, st);
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_steering_table: copy");
+}
+
+rtis_status rtis_fd_gemm_create(rtis_fd_gemm** out, const float* mic_xyz, int n_mics, const float* directions,
+                                int n_dirs, const double* freqs_hz, int n_bins, int n_frames, double c,
+                                const float* gain, const float* delay_s, int precision) {
+    if (!out) return fail(RTIS_ERR_INVALID_ARG, "rtis_fd_gemm_create: out is NULL");
+    *out = nullptr;
+    if (!mic_xyz || !directions || !freqs_hz)
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_fd_gemm_create: mic_xyz, directions and freqs_hz must be non-NULL");
+    if (n_mics < 1 || n_mics > rtis::kMaxMics)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_fd_gemm_create: n_mics must be in [1, 32]");
+    if (n_dirs < 1 || n_bins < 1) return fail(RTIS_ERR_INVALID_ARG, "rtis_fd_gemm_create: n_dirs and n_bins must be >= 1");
+    if (n_frames < 1 || n_frames > rtis::kFdMaxFrames)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_fd_gemm_create: n_frames must be in [1, 64]");
+    if (!(c > 0.0) || !std::isfinite(c)) return fail(RTIS_ERR_INVALID_ARG, "rtis_fd_gemm_create: c must be > 0");
+    if (precision != RTIS_PREC_FP32 && precision != RTIS_PREC_BF16 && precision != RTIS_PREC_FP16)
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_fd_gemm_create: unknown precision");
+    if (!rtis::all_finite(mic_xyz, 3 * static_cast<size_t>(n_mics)) ||
+        !rtis::all_finite(directions, 3 * static_cast<size_t>(n_dirs)) ||
+        (gain && !rtis::all_finite(gain, n_mics)) || (delay_s && !rtis::all_finite(delay_s, n_mics)))
+        return fail(RTIS_ERR_NONFINITE, "rtis_fd_gemm_create: non-finite geometry, gain or delay");
+    for (int k = 0; k < n_bins; ++k)
+        if (!std::isfinite(freqs_hz[k])) return fail(RTIS_ERR_NONFINITE, "rtis_fd_gemm_create: non-finite frequency");
+
+    rtis_fd_gemm* plan = new (std::nothrow) rtis_fd_gemm();
+    if (!plan) return fail(RTIS_ERR_OOM, "rtis_fd_gemm_create: host allocation failed");
+    rtis::FdGemmPlan& g = plan->g;
+    g.M = n_mics;
+    g.D = n_dirs;
+    g.K = n_bins;
+    g.T = n_frames;
+    g.precision = precision;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&g.n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) g.n_sm = 1;
+        cudaGetLastError();
+    }
+    // tau_dm in FP64, carried to the device as an unevaluated float pair hi + lo
+    std::vector<float2> tau(static_cast<size_t>(n_dirs) * n_mics), fr(n_bins);
+    for (int d = 0; d < n_dirs; ++d)
+        for (int m = 0; m < n_mics; ++m) {
+            const double dot = static_cast<double>(mic_xyz[3 * m]) * directions[3 * d] +
+                               static_cast<double>(mic_xyz[3 * m + 1]) * directions[3 * d + 1] +
+                               static_cast<double>(mic_xyz[3 * m + 2]) * directions[3 * d + 2];
+            const double t = (delay_s ? static_cast<double>(delay_s[m]) : 0.0) - dot / c;
+            const float hi = static_cast<float>(t);
+            tau[static_cast<size_t>(d) * n_mics + m] = make_float2(hi, static_cast<float>(t - hi));
+        }
+    for (int k = 0; k < n_bins; ++k) {
+        const float hi = static_cast<float>(freqs_hz[k]);
+        fr[k] = make_float2(hi, static_cast<float>(freqs_hz[k] - hi));
+    }
+    std::vector<float> gv(n_mics, 1.0f);
+    if (gain)
+        for (int m = 0; m < n_mics; ++m) gv[m] = gain[m];
+    size_t total = 0;
+    cudaError_t e = rtis::dev_alloc(&g.d_tau, tau.size(), &total);
+    if (e == cudaSuccess) e = rtis::dev_alloc(&g.d_freq, fr.size(), &total);
+    if (e == cudaSuccess) e = rtis::dev_alloc(&g.d_gain, gv.size(), &total);
+    if (e == cudaSuccess) e = rtis::dev_alloc(&g.d_scale, static_cast<size_t>(n_mics), &total);
+    if (e == cudaSuccess) e = rtis::dev_alloc(&g.d_status, 1, &total);
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_tau, tau.data(), tau.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_freq, fr.data(), fr.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_gain, gv.data(), gv.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(g.d_status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        rtis_fd_gemm_destroy(plan);
+        cudaGetLastError();
+        return (e == cudaErrorMemoryAllocation) ? fail(RTIS_ERR_OOM, "rtis_fd_gemm_create: cudaMalloc failed")
+                                                : cuda_fail(e, "rtis_fd_gemm_create: upload");
+    }
+    *out = plan;
+    return RTIS_OK;
+}
+
+rtis_status rtis_fd_gemm_run(rtis_fd_gemm* plan, const float* d_X, float* d_Y, void* stream) {
+    if (!plan || !d_X || !d_Y) return fail(RTIS_ERR_INVALID_ARG, "rtis_fd_gemm_run: NULL argument");
+    if (!rtis::aligned(d_X, 8) || !rtis::aligned(d_Y, 16))
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_fd_gemm_run: d_X must be 8-byte and d_Y 16-byte aligned");
+    rtis::FdGemmPlan& g = plan->g;
+    CUtensorMap ymap;
+    const CUtensorMap* ym = nullptr;
+    if (g.T % 2 == 0 && g.T >= 16) {  // rows of 2T floats: 16-byte strides, at least one 128-byte box
+        std::string err;
+        if (!rtis::fd_gemm_encode_ymap(g, reinterpret_cast<float2*>(d_Y), &ymap, &err))
+            return fail(RTIS_ERR_CUDA, "rtis_fd_gemm_run: " + err);
+        ym = &ymap;
+    }
+    cudaError_t e = rtis::launch_fd_gemm(g, reinterpret_cast<const float2*>(d_X), reinterpret_cast<float2*>(d_Y), ym,
+                                         static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_fd_gemm_run: launch");
+}
+
+void rtis_fd_gemm_destroy(rtis_fd_gemm* plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    rtis::FdGemmPlan& g = plan->g;
+    void* bufs[] = {g.d_tau, g.d_freq, g.d_gain, g.d_scale, g.d_status};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete plan;
 }
 
 rtis_status rtis_plan_sync(rtis_plan* plan, unsigned* bits_out) {

@@ -58,6 +58,24 @@ struct Plan {
 };
 
 // ----------------------------------------------------------------------------
+// frequency-domain beamforming GEMM (kernels_fd.cu)
+// ----------------------------------------------------------------------------
+constexpr int kFdMaxFrames = 64;
+struct FdGemmPlan {
+    int M = 0, D = 0, K = 0, T = 0, precision = 0;
+    int n_sm = 0;               // persistent grid size
+    float2* d_tau = nullptr;    // [D][M] seconds, (hi, lo)
+    float2* d_freq = nullptr;   // [K] Hz, (hi, lo)
+    float* d_gain = nullptr;    // [M]
+    float* d_scale = nullptr;   // [M]
+    unsigned* d_status = nullptr;
+};
+// ymap: TMA view of Y (fd_gemm_encode_ymap) or nullptr for plain stores
+cudaError_t launch_fd_gemm(const FdGemmPlan& g, const float2* d_X, float2* d_Y, const CUtensorMap* ymap,
+                           cudaStream_t st);
+bool fd_gemm_encode_ymap(const FdGemmPlan& g, float2* d_Y, CUtensorMap* map, std::string* err);
+
+// ----------------------------------------------------------------------------
 // error reporting (thread-local last message)
 // ----------------------------------------------------------------------------
 void set_error(const std::string& msg);
@@ -76,9 +94,16 @@ cudaError_t td_configure(const Plan& p);
 
 bool encode_tmap_2d_u64(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows,
                         uint32_t box_cols, uint32_t box_rows, std::string* err);
+// generic tiled tensor map: dims[rank], strides[rank-1] in bytes, box[rank]
+bool encode_tmap(CUtensorMap* map, CUtensorMapDataType dtype, uint32_t rank, const void* base, const uint64_t* dims,
+                 const uint64_t* strides, const uint32_t* box, CUtensorMapSwizzle swizzle, std::string* err);
 
 }  // namespace rtis
 
 struct rtis_plan {
     rtis::Plan p;
+};
+
+struct rtis_fd_gemm {
+    rtis::FdGemmPlan g;
 };

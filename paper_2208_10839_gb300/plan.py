@@ -93,3 +93,42 @@ class Plan:
     def sync(self) -> int:
         """Waits for the device; returns (and clears) the device status bits."""
         return nat.rtis_plan_sync(self.handle)
+
+
+class FdGemm:
+    """Frequency-domain beamforming GEMM: Y[k][d][t] = sum_m W[k][d][m] X[k][m][t] on tcgen05."""
+
+    def __init__(self, mic_xyz, directions, freqs_hz, n_frames, *, c=343.0, gain=None, delay_s=None,
+                 precision="fp32"):
+        import torch
+        self._torch = torch
+        self.handle = nat.rtis_fd_gemm_create(mic_xyz, directions, freqs_hz, n_frames, c, gain, delay_s,
+                                              _PRECS[precision])
+        self.K = len(freqs_hz)
+        self.D = int(np.asarray(directions).shape[0])
+        self.M = int(np.asarray(mic_xyz).shape[0])
+        self.T = int(n_frames)
+
+    def run(self, X, Y=None, stream=None):
+        """X: complex64 [K][M][T] device tensor -> Y complex64 [K][D][T]."""
+        if Y is None:
+            Y = self._torch.empty((self.K, self.D, self.T), dtype=self._torch.complex64, device=X.device)
+        nat.rtis_fd_gemm_run(self.handle, X, Y, stream)
+        return Y
+
+    def close(self):
+        if getattr(self, "handle", None):
+            nat.rtis_fd_gemm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
