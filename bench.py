@@ -2,9 +2,10 @@
 
 A step is one seeded synthetic measurement (32 mics, 16384 int16 samples,
 20 reflectors on the frontal hemisphere, 20 dB SNR) through the whole chain
-on one GPU: matched filter -> time-domain delay-and-sum over 2048 Fibonacci
-half-sphere directions -> envelope, low-pass, subsample -> energyscape
-2048 x 1638 (FP32).  The input sits in HBM when the clock starts; L2 is
+on one GPU: matched filter -> delay-and-sum over 2048 Fibonacci half-sphere
+directions in both forms (time domain with Catmull-Rom fractional delays,
+and frequency domain with exact phase ramps) -> envelope, low-pass,
+subsample -> two energyscapes 2048 x 1638 (FP32).  The input sits in HBM when the clock starts; L2 is
 flushed (a 512 MiB write) between steps, outside the timed events.
 
 Printed (rank 0, one JSON line): value = energyscapes/s over all ranks,
@@ -36,9 +37,12 @@ import numpy as np
 N_SAMPLES, N_DIRS, N_MICS = 16384, 2048, 32
 METRIC = "energyscapes/s at 32ch x 16384 samples x 2048 dirs; error vs FP64 oracle"
 WORKLOAD = "hemisphere: 32 mics (12 cm square, seeded), 16384 samples @ 450 kHz, 2048 Fibonacci half-sphere dirs, " \
-           "20 reflectors 0.3-6 m, 20 dB SNR, int16; time-domain Catmull-Rom DAS, FP32"
+           "20 reflectors 0.3-6 m, 20 dB SNR, int16; matched filter + time-domain and frequency-domain DAS, FP32"
 FP32_LANES_PER_SM = 128     # FP32 FMA lanes per SM (4 SMSPs x 32)
 SM_MAX_MHZ_NOMINAL = 2070.0
+# dram__bytes_read.sum + dram__bytes_write.sum of one td_beamform_kernel launch (ncu capture of this
+# workload, see profiles/); set to None whenever that kernel changes until it is re-captured
+TD_TRAFFIC_BYTES = 5543168
 
 
 def dist_env():
@@ -109,16 +113,18 @@ class ClockSampler:
 
 
 def oracle_sample_time(cfg, n_dirs_sample: int, seed: int = 0):
-    """Seconds the FP64 oracle needs for one energyscape, from a direction sample."""
+    """Seconds the FP64 oracle needs for one step (both energyscapes), from a direction sample."""
     import oracle
     rng = np.random.default_rng(seed)
     pick = np.sort(rng.choice(cfg["dirs"].shape[0], n_dirs_sample, replace=False))
     t0 = time.perf_counter()
     a = oracle.matched_filter(cfg["x"], cfg["chirp"], cfg["fs"])
+    A, k_lo, F = oracle.mf_spectrum(cfg["x"], cfg["chirp"], cfg["fs"])
     t1 = time.perf_counter()
     delta = oracle.steering_delays(cfg["mic_xyz"], cfg["dirs"][pick], cfg["fs"], cfg["c"])
-    b = oracle.das_td(a, delta)
-    oracle.envelope_decimate(b, oracle.lpf_taps())
+    h = oracle.lpf_taps()
+    oracle.envelope_decimate(oracle.das_td(a, delta), h)
+    oracle.envelope_decimate(oracle.das_fd(A, k_lo, F, cfg["n_samples"], delta), h)
     t2 = time.perf_counter()
     D = cfg["dirs"].shape[0]
     return (t1 - t0) + (t2 - t1) * D / n_dirs_sample, (t1 - t0), (t2 - t1)
@@ -143,8 +149,8 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD.replace("FP32", "FP64 oracle"), "parallelism": "single process"},
         "cpu_baseline": {"value": value, "unit": "energyscapes/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step: matched filter on all 32 channels + DAS/envelope on {n_s} of "
-                                   f"{N_DIRS} directions, scaled to {N_DIRS}"},
+                         "sample": f"per step: matched filter on all 32 channels + time- and frequency-domain "
+                                   f"DAS/envelope on {n_s} of {N_DIRS} directions, scaled to {N_DIRS}"},
         "e2e": {"value": value, "unit": "energyscapes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -258,14 +264,28 @@ def main():
     plan = Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"])
     x = torch.from_numpy(cfg["x"]).to(dev)
     a = torch.empty((N_MICS, N_SAMPLES), dtype=torch.complex64, device=dev)
-    E = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32, device=dev)
+    A = torch.empty((N_MICS, plan.Kb), dtype=torch.complex64, device=dev)
+    E_td = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32, device=dev)
+    E_fd = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
+    h = plan.handle
 
-    def step():
-        nat.rtis_matched_filter(plan.handle, x, a, None, sh)
-        nat.rtis_beamform_td(plan.handle, a, E, sh)
+    def step(ev=None):
+        # one measurement -> matched filter (analytic signal and in-band spectra),
+        # time-domain and frequency-domain energyscapes
+        if ev:
+            ev[0].record(stream)
+        nat.rtis_matched_filter(h, x, a, A, sh)
+        if ev:
+            ev[1].record(stream)
+        nat.rtis_beamform_td(h, a, E_td, sh)
+        if ev:
+            ev[2].record(stream)
+        nat.rtis_beamform_fd(h, A, E_fd, sh)
+        if ev:
+            ev[3].record(stream)
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -273,46 +293,48 @@ def main():
     torch.cuda.synchronize()
     assert plan.sync() == 0
 
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.fill_(float(k))
-            e0, e1, e2 = evs[k]
-            e0.record(stream)
-            nat.rtis_matched_filter(plan.handle, x, a, None, sh)
-            e1.record(stream)
-            nat.rtis_beamform_td(plan.handle, a, E, sh)
-            e2.record(stream)
+            step(evs[k])
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in evs]
-    das_ms = [e1.elapsed_time(e2) for _, e1, e2 in evs]
-    mf_ms = [e0.elapsed_time(e1) for e0, e1, _ in evs]
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    mf_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    td_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    fd_ms = [e[2].elapsed_time(e[3]) for e in evs]
     t_total = sum(step_ms) / 1e3
     bits = plan.sync()
     assert bits == 0, f"device status {bits:#x}"
 
-    # end to end through rtis_process: pinned host input -> device -> energyscape -> pinned host
+    # end to end through the public calls: pinned host input -> device -> both
+    # energyscapes -> pinned host
     xh = torch.from_numpy(cfg["x"]).pin_memory()
-    Eh = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32).pin_memory()
+    Eh_td = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32).pin_memory()
+    Eh_fd = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32).pin_memory()
     xd = torch.empty_like(x)
-    for _ in range(3):
+
+    def e2e_step():
         xd.copy_(xh, non_blocking=True)
-        nat.rtis_process(plan.handle, xd, E, sh)
-        Eh.copy_(E, non_blocking=True)
+        nat.rtis_matched_filter(h, xd, a, A, sh)
+        nat.rtis_beamform_td(h, a, E_td, sh)
+        nat.rtis_beamform_fd(h, A, E_fd, sh)
+        Eh_td.copy_(E_td, non_blocking=True)
+        Eh_fd.copy_(E_fd, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
     torch.cuda.synchronize()
     ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_steps = max(args.steps // 2, 3)
     ee0.record(stream)
     for _ in range(e2e_steps):
-        xd.copy_(xh, non_blocking=True)
-        nat.rtis_process(plan.handle, xd, E, sh)
-        Eh.copy_(E, non_blocking=True)
+        e2e_step()
     ee1.record(stream)
     torch.cuda.synchronize()
     t_e2e = ee0.elapsed_time(ee1) / 1e3
@@ -326,18 +348,18 @@ def main():
     e2e_value = world * e2e_steps / t_e2e
     clocks = clk.summary()
 
-    # roofline of the dominant kernel: FP32 FMA pipe (D*N*M*4 taps*2 (re,im) FMAs = 2 flops each)
+    # roofline of the dominant kernel: the time-domain beamformer on the FP32 FMA pipe
+    # (D*N*M*4 taps*2 (re, im) FMAs, 2 flops each)
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     flops = float(N_DIRS) * N_SAMPLES * N_MICS * 4 * 2 * 2
-    das_s = statistics.mean(das_ms) / 1e3
-    achieved = flops / das_s / 1e12
+    td_s = statistics.mean(td_ms) / 1e3
+    achieved = flops / td_s / 1e12
     peak_tf = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": "td_beamform_kernel", "achieved": achieved, "peak": peak_tf,
-                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": TD_TRAFFIC_BYTES,
                 "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {SM_MAX_MHZ_NOMINAL:.0f} MHz",
-                "algorithmic_flops_per_launch": flops, "launch_ms": das_s * 1e3,
-                "mf_ms": statistics.mean(mf_ms)}
+                "algorithmic_flops_per_launch": flops, "launch_ms": td_s * 1e3}
     if clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / (n_sm * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
 
@@ -347,11 +369,18 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_mics": N_MICS, "n_samples": N_SAMPLES, "n_dirs": N_DIRS,
                    "n_out": plan.n_out, "decim": 10, "batch_per_step": 1,
+                   "paths_per_step": "time-domain (Catmull-Rom) and frequency-domain (phase ramp) energyscapes "
+                                     "of the same measurement; value counts measurements",
                    "l2": "flushed (512 MiB write) between steps, outside the timed events",
                    "parallelism": f"{world} independent replica(s), one measurement per rank per step"},
         "e2e": {"value": e2e_value, "unit": "energyscapes/s", "h2d_bytes_per_step": int(x.numel() * 2),
-                "d2h_bytes_per_step": int(E.numel() * 4), "call": "rtis_process"},
-        "gpu_launches": 3 * args.steps,
+                "d2h_bytes_per_step": int(E_td.numel() * 4 + E_fd.numel() * 4),
+                "calls": "rtis_matched_filter, rtis_beamform_td, rtis_beamform_fd"},
+        "gpu_launches": 4 * args.steps,
+        "kernels_ms": {"matched_filter": statistics.mean(mf_ms), "td_beamform": statistics.mean(td_ms),
+                       "fd_energyscape": statistics.mean(fd_ms)},
+        "path_rates": {"td_only_energyscapes_per_s": 1e3 / (statistics.mean(mf_ms) + statistics.mean(td_ms)),
+                       "fd_only_energyscapes_per_s": 1e3 / (statistics.mean(mf_ms) + statistics.mean(fd_ms))},
         "roofline": roofline,
         "clocks": clocks,
     }
@@ -359,8 +388,9 @@ def main():
         t_es, t_mf, t_das = oracle_sample_time(cfg, args.cpu_dirs)
         line["cpu_baseline"] = {"value": 1.0 / t_es, "unit": "energyscapes/s", "cores": 1, "kind": "oracle",
                                 "sample": f"FP64 oracle, one process: matched filter on all 32 channels "
-                                          f"({t_mf:.2f} s) + DAS/envelope on {args.cpu_dirs} of {N_DIRS} "
-                                          f"directions ({t_das:.2f} s), scaled to {N_DIRS} directions"}
+                                          f"({t_mf:.2f} s) + time- and frequency-domain DAS/envelope on "
+                                          f"{args.cpu_dirs} of {N_DIRS} directions ({t_das:.2f} s), scaled to "
+                                          f"{N_DIRS} directions"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -122,6 +122,7 @@ rtis_status rtis_plan_get_info(const rtis_plan* plan, rtis_plan_info* info);
 /*
  * rtis_process -- whole chain for one recording (Fig. 3): matched filter,
  * delay-and-sum on the plan's path (TD or FD), envelope, low-pass, subsample.
+ * The FD path (opt.path = RTIS_PATH_FD) needs F <= 32768.
  *   d_in   device int16 [n_mics][n_samples], 8-byte aligned
  *   d_out  device float [n_dirs][n_out]
  */
@@ -145,6 +146,15 @@ rtis_status rtis_matched_filter(rtis_plan* plan, const int16_t* d_in, float* d_a
  *   d_out  device float [n_dirs][n_out]
  */
 rtis_status rtis_beamform_td(rtis_plan* plan, const float* d_a, float* d_out, void* stream);
+
+/*
+ * rtis_beamform_fd -- frequency-domain delay-and-sum with the envelope,
+ * low-pass and subsampling, from the in-band matched-filter spectra
+ * (rtis_matched_filter's d_A).  Needs F <= 32768.
+ *   d_A    device complex float [n_mics][k_hi-k_lo+1], 8-byte aligned
+ *   d_out  device float [n_dirs][n_out]
+ */
+rtis_status rtis_beamform_fd(rtis_plan* plan, const float* d_A, float* d_out, void* stream);
 
 /*
  * rtis_steering_table -- the plan's per-(direction, mic) fractional-delay

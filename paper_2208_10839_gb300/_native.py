@@ -69,6 +69,7 @@ _PROTOS = {
     "rtis_process": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_matched_filter": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "rtis_beamform_td": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "rtis_beamform_fd": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_steering_table": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_plan_sync": (C.c_int, [_VP, C.POINTER(C.c_uint)]),
     "rtis_matched_filter_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, C.c_double, C.c_double,
@@ -171,6 +172,10 @@ def rtis_matched_filter(plan, d_in, d_a, d_A=None, stream=None):
 
 def rtis_beamform_td(plan, d_a, d_out, stream=None):
     check(lib().rtis_beamform_td(plan, ptr(d_a), ptr(d_out), stream_handle(stream)), "rtis_beamform_td")
+
+
+def rtis_beamform_fd(plan, d_A, d_out, stream=None):
+    check(lib().rtis_beamform_fd(plan, ptr(d_A), ptr(d_out), stream_handle(stream)), "rtis_beamform_fd")
 
 
 def rtis_steering_table(plan, d_shift, d_weight, stream=None):

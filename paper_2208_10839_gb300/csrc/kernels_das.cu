@@ -35,9 +35,9 @@ constexpr uint32_t kWaitPolls = 1u << 22;  // bounded mbarrier wait (~ seconds)
 
 __global__ void steering_table_kernel(const float* __restrict__ mic, const float* __restrict__ dirs,
                                       const float* __restrict__ gain, const float* __restrict__ delay_s,
-                                      int M, int D, double fs, double fs_over_c, int Jlim,
+                                      int M, int D, double fs, double fs_over_c, int Jlim, double inv_F,
                                       int* __restrict__ shift, float4* __restrict__ wt,
-                                      unsigned* __restrict__ status) {
+                                      float2* __restrict__ dphase, unsigned* __restrict__ status) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= M * D) return;
     const int d = idx / M;
@@ -63,6 +63,10 @@ __global__ void steering_table_kernel(const float* __restrict__ mic, const float
     }
     shift[idx] = j;
     wt[idx] = w;
+    // frequency-domain form: delta / F cycles per bin, as an unevaluated pair hi + lo
+    const double dp = delta * inv_F;
+    const float dp_hi = static_cast<float>(dp);
+    dphase[idx] = make_float2(dp_hi, static_cast<float>(dp - dp_hi));
 }
 
 struct TdArgs {
@@ -274,8 +278,8 @@ cudaError_t launch_steering_table(Plan& p, cudaStream_t st) {
     const int total = p.M * p.D;
     const int nt = 256;
     steering_table_kernel<<<(total + nt - 1) / nt, nt, 0, st>>>(p.d_mic, p.d_dirs, p.d_gain, p.d_delay, p.M, p.D,
-                                                              p.fs, p.fs / p.c, p.Jlim, p.d_shift, p.d_wt,
-                                                              p.d_status);
+                                                              p.fs, p.fs / p.c, p.Jlim, 1.0 / p.F, p.d_shift,
+                                                              p.d_wt, p.d_dphase, p.d_status);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) p.table_dirty = false;
     return e;

@@ -1,0 +1,224 @@
+// Frequency-domain delay-and-sum energyscape (the phase-ramp form of the
+// paper's delay-and-sum, Fig. 3 / Sec. 4.1, with the envelope, low-pass and
+// subsampling of Sec. 4.3).  One CTA per direction d:
+//
+//   B_d[k] = sum_m g_m exp(+2 pi i k delta_dm / F) A_m[k],  k = k_lo .. k_hi
+//   b_d[n] = IDFT_F(B_d)[n],  n < N     (A carries the 1/F of the transform)
+//   E[d][i] = sum_j h[j] |b_d[R i + j - half]|
+//
+// B_d: thread t owns the bins k' = t + 256 c (coalesced loads of A); per mic
+// and chunk of 8 bins it anchors the steering phase exactly (compensated FP32
+// product k * delta/F, integer cycles removed) and then advances it with one
+// complex multiply by exp(2 pi i 256 delta/F) per bin.  b_d: with n = 4p + q
+// the band (below F/4) needs four P = F/4 point inverse FFTs of
+// B_d[k_lo + k'] w_F^{k' q}; the remaining factor w_F^{k_lo n} has unit
+// modulus and drops out of |b_d|.  After each phase the low-pass taps that
+// fall on n = q (mod 4) are added to the outputs each thread owns, so the
+// envelope never needs storing.  Twiddles come from two small shared tables
+// (w^j = hi[j >> 8] lo[j & 255]) instead of the F-point table.
+#include "fft.cuh"
+#include "rtis_internal.h"
+
+namespace rtis {
+namespace {
+
+using namespace fft;
+
+constexpr int kFdesThreads = 256;
+constexpr int kFdesChunk = 8;  // bins per thread per anchor
+
+struct FdesArgs {
+    const float2* A;      // [M][Kb] in-band matched-filter spectra (already / F)
+    const float2* dphase; // [D][M] delta_dm / F in cycles per bin, hi + lo
+    const float* gain;    // [M]
+    const float2* tw;     // [F]
+    const float* h;       // [lpf_len]
+    float* E;             // [D][n_out]
+    int M, D, N, F, k_lo, Kb, R, lpf_len, n_out;
+};
+
+// fractional part of k * (hi + lo) in cycles, compensated FP32 (k an exact integer)
+__device__ __forceinline__ float frac_cycles(float k, float2 ph) {
+    const float p = k * ph.x;
+    const float e = fmaf(k, ph.x, -p);
+    const float r = p - rintf(p);
+    return r + fmaf(k, ph.y, e);
+}
+
+struct FdesSmem {
+    int fbuf, B, twhi, twlo, Eacc, hs, step, gs, bytes;
+};
+
+__host__ __device__ inline FdesSmem fdes_layout(int P, int F, int Kb, int n_out, int lpf_len, int M) {
+    FdesSmem L;
+    int o = 0;
+    L.fbuf = o;
+    o += (spad(P - 1) + 1) * 8;
+    L.B = o;
+    o += Kb * 8;
+    L.twhi = o;
+    o += (F / 256) * 8;
+    L.twlo = o;
+    o += 256 * 8;
+    L.step = o;
+    o += M * 8;
+    L.Eacc = o;
+    o += n_out * 4;
+    L.hs = o;
+    o += lpf_len * 4;
+    L.gs = o;
+    o += M * 4;
+    L.bytes = o;
+    return L;
+}
+
+template <int LOGP>
+__global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const FdesArgs a) {
+    constexpr int P = 1 << LOGP;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const FdesSmem L = fdes_layout(P, a.F, a.Kb, a.n_out, a.lpf_len, a.M);
+    float2* fbuf = reinterpret_cast<float2*>(sm + L.fbuf);
+    float2* B = reinterpret_cast<float2*>(sm + L.B);
+    float2* twhi = reinterpret_cast<float2*>(sm + L.twhi);
+    float2* twlo = reinterpret_cast<float2*>(sm + L.twlo);
+    float2* step = reinterpret_cast<float2*>(sm + L.step);  // exp(2 pi i 256 delta/F)
+    float* Eacc = reinterpret_cast<float*>(sm + L.Eacc);
+    float* hs = reinterpret_cast<float*>(sm + L.hs);
+    float* gs = reinterpret_cast<float*>(sm + L.gs);
+
+    const int d = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int M = a.M, Kb = a.Kb;
+    for (int j = tid; j < 256; j += kFdesThreads) twlo[j] = __ldg(a.tw + j);
+    for (int j = tid; j < a.F / 256; j += kFdesThreads) twhi[j] = __ldg(a.tw + j * 256);
+    for (int j = tid; j < a.lpf_len; j += kFdesThreads) hs[j] = a.h[j];
+    for (int i = tid; i < a.n_out; i += kFdesThreads) Eacc[i] = 0.f;
+    if (tid < M) {
+        const float2 ph = __ldg(a.dphase + static_cast<size_t>(d) * M + tid);
+        float s, c;
+        sincospif(2.0f * frac_cycles(static_cast<float>(kFdesThreads), ph), &s, &c);
+        step[tid] = make_float2(c, s);
+        gs[tid] = a.gain[tid];
+    }
+    __syncthreads();
+    const SplitTwiddles tws{twhi, twlo};
+
+    // ---- steered spectrum B_d ------------------------------------------------
+    const float2* dph = a.dphase + static_cast<size_t>(d) * M;
+    for (int c0 = 0; c0 * kFdesThreads < Kb; c0 += kFdesChunk) {
+        const int kp0 = c0 * kFdesThreads + tid;  // bins kp0 + 256 i, i < kFdesChunk
+        float2 acc[kFdesChunk];
+#pragma unroll
+        for (int i = 0; i < kFdesChunk; ++i) acc[i] = make_float2(0.f, 0.f);
+        const float k0 = static_cast<float>(a.k_lo + kp0);
+#pragma unroll 2
+        for (int m = 0; m < M; ++m) {
+            float s, c;
+            __sincosf(6.28318530717958647692f * frac_cycles(k0, __ldg(dph + m)), &s, &c);
+            const float g = gs[m];
+            float2 w = make_float2(g * c, g * s);
+            const float2 st = step[m];
+            const float2* Am = a.A + static_cast<size_t>(m) * Kb;
+#pragma unroll
+            for (int i = 0; i < kFdesChunk; ++i) {
+                const int kp = kp0 + i * kFdesThreads;
+                if (kp < Kb) {
+                    const float2 v = __ldg(Am + kp);
+                    acc[i].x = fmaf(w.x, v.x, fmaf(-w.y, v.y, acc[i].x));
+                    acc[i].y = fmaf(w.x, v.y, fmaf(w.y, v.x, acc[i].y));
+                }
+                w = cmul(w, st);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kFdesChunk; ++i) {
+            const int kp = kp0 + i * kFdesThreads;
+            if (kp < Kb) B[kp] = acc[i];
+        }
+    }
+    __syncthreads();
+
+    // ---- four phase IFFTs, each folded into the low-pass outputs ------------
+    const int half = (a.lpf_len - 1) >> 1;
+    const unsigned fmask = static_cast<unsigned>(a.F - 1);
+    for (int q = 0; q < 4; ++q) {
+        for (int kp = tid; kp < P; kp += kFdesThreads) {
+            float2 g = make_float2(0.f, 0.f);
+            if (kp < Kb) {
+                const float2 v = B[kp];
+                g = (q == 0) ? v : cmul(v, conjf2(tws(static_cast<int>((static_cast<unsigned>(kp) * q) & fmask))));
+            }
+            fbuf[spad(kp)] = g;
+        }
+        __syncthreads();
+        fft_smem<LOGP, true, kFdesThreads>(fbuf, tws, a.F);
+        // envelope of this phase, in place: fbuf[p].x = |b(4p + q)|
+        for (int p = tid; p < P; p += kFdesThreads) {
+            const float2 v = fbuf[spad(p)];
+            fbuf[spad(p)].x = sqrtf(v.x * v.x + v.y * v.y);
+        }
+        __syncthreads();
+        for (int i = tid; i < a.n_out; i += kFdesThreads) {
+            const int n0 = a.R * i - half;          // n = n0 + j
+            const int j0 = ((q - n0) % 4 + 4) & 3;  // first tap with n = q (mod 4)
+            float s = 0.f;
+            for (int j = j0; j < a.lpf_len; j += 4) {
+                const int n = n0 + j;
+                if (n >= 0 && n < a.N) s = fmaf(hs[j], fbuf[spad((n - q) >> 2)].x, s);
+            }
+            Eacc[i] += s;
+        }
+        __syncthreads();
+    }
+    float* Erow = a.E + static_cast<size_t>(d) * a.n_out;
+    for (int i = tid; i < a.n_out; i += kFdesThreads) Erow[i] = Eacc[i];
+}
+
+template <int LOGP>
+cudaError_t fdes_launch_t(const Plan& p, const float2* d_A, float* d_out, cudaStream_t st) {
+    const size_t sm = static_cast<size_t>(fdes_layout(1 << LOGP, p.F, p.Kb, p.n_out, p.lpf_len, p.M).bytes);
+    cudaError_t e = cudaFuncSetAttribute(fd_energyscape_kernel<LOGP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sm));
+    if (e != cudaSuccess) return e;
+    FdesArgs a;
+    a.A = d_A;
+    a.dphase = p.d_dphase;
+    a.gain = p.d_gain;
+    a.tw = p.d_tw;
+    a.h = p.d_h;
+    a.E = d_out;
+    a.M = p.M;
+    a.D = p.D;
+    a.N = p.N;
+    a.F = p.F;
+    a.k_lo = p.k_lo;
+    a.Kb = p.Kb;
+    a.R = p.R;
+    a.lpf_len = p.lpf_len;
+    a.n_out = p.n_out;
+    fd_energyscape_kernel<LOGP><<<p.D, kFdesThreads, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t fdes_smem_bytes(const Plan& p) {
+    if (p.logP < 6 || p.logP > 13) return ~static_cast<size_t>(0);
+    return static_cast<size_t>(fdes_layout(p.P, p.F, p.Kb, p.n_out, p.lpf_len, p.M).bytes);
+}
+
+cudaError_t launch_fd_energyscape(const Plan& p, const float2* d_A, float* d_out, cudaStream_t st) {
+    switch (p.logP) {
+        case 6: return fdes_launch_t<6>(p, d_A, d_out, st);
+        case 7: return fdes_launch_t<7>(p, d_A, d_out, st);
+        case 8: return fdes_launch_t<8>(p, d_A, d_out, st);
+        case 9: return fdes_launch_t<9>(p, d_A, d_out, st);
+        case 10: return fdes_launch_t<10>(p, d_A, d_out, st);
+        case 11: return fdes_launch_t<11>(p, d_A, d_out, st);
+        case 12: return fdes_launch_t<12>(p, d_A, d_out, st);
+        case 13: return fdes_launch_t<13>(p, d_A, d_out, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rtis

@@ -31,7 +31,7 @@ cudaError_t dev_alloc(T** ptr, size_t count, size_t* total) {
 
 void free_plan_buffers(Plan& p) {
     void* bufs[] = {p.d_mic, p.d_dirs, p.d_gain, p.d_delay, p.d_tw, p.d_C, p.d_h,
-                    p.d_shift, p.d_wt, p.d_Z, p.d_a, p.d_status};
+                    p.d_shift, p.d_wt, p.d_dphase, p.d_Z, p.d_a, p.d_A, p.d_status};
     for (void* b : bufs)
         if (b) cudaFree(b);
 }
@@ -220,6 +220,11 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         delete plan;
         return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: steering delays too large for the staged halo");
     }
+    if (opt.path == RTIS_PATH_FD && rtis::fdes_smem_bytes(p) > 227 * 1024) {
+        delete plan;
+        return fail(RTIS_ERR_UNSUPPORTED,
+                    "rtis_plan_create: frequency-domain path needs F <= 32768 and the envelope in shared memory");
+    }
 
     // ---- host tables (FP64, rounded to float once) ----
     std::vector<double> cs(F), sn(F);
@@ -274,6 +279,8 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     RTIS_ALLOC(p.d_h, lpf_len)
     RTIS_ALLOC(p.d_shift, static_cast<size_t>(n_dirs) * n_mics)
     RTIS_ALLOC(p.d_wt, static_cast<size_t>(n_dirs) * n_mics)
+    RTIS_ALLOC(p.d_dphase, static_cast<size_t>(n_dirs) * n_mics)
+    RTIS_ALLOC(p.d_A, static_cast<size_t>(n_mics) * p.Kb)
     RTIS_ALLOC(p.d_Z, static_cast<size_t>(n_mics) * 2 * p.P)
     RTIS_ALLOC(p.d_a, static_cast<size_t>(n_mics) * n_samples)
     RTIS_ALLOC(p.d_status, 1)
@@ -390,15 +397,32 @@ rtis_status rtis_process(rtis_plan* plan, const int16_t* d_in, float* d_out, voi
     if (!rtis::aligned(d_in, 8)) return fail(RTIS_ERR_INVALID_ARG, "rtis_process: d_in must be 8-byte aligned");
     if (!rtis::aligned(d_out, 4)) return fail(RTIS_ERR_INVALID_ARG, "rtis_process: d_out must be 4-byte aligned");
     Plan& p = plan->p;
-    if (p.opt.path != RTIS_PATH_TD)
-        return fail(RTIS_ERR_UNSUPPORTED, "rtis_process: frequency-domain path not built");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rtis_status s = ensure_table(p, st);
     if (s != RTIS_OK) return s;
     cudaError_t e = rtis::launch_mf_forward(p, d_in, st);
-    if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, p.d_a, nullptr, st);
-    if (e == cudaSuccess) e = rtis::launch_td_beamform(p, p.tmap_a, d_out, st);
+    if (p.opt.path == RTIS_PATH_FD) {
+        if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, nullptr, p.d_A, st);
+        if (e == cudaSuccess) e = rtis::launch_fd_energyscape(p, p.d_A, d_out, st);
+    } else {
+        if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, p.d_a, nullptr, st);
+        if (e == cudaSuccess) e = rtis::launch_td_beamform(p, p.tmap_a, d_out, st);
+    }
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_process: launch");
+}
+
+rtis_status rtis_beamform_fd(rtis_plan* plan, const float* d_A, float* d_out, void* stream) {
+    if (!plan || !d_A || !d_out) return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_fd: NULL argument");
+    if (!rtis::aligned(d_A, 8) || !rtis::aligned(d_out, 4))
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_fd: d_A must be 8-byte aligned");
+    Plan& p = plan->p;
+    if (rtis::fdes_smem_bytes(p) > 227 * 1024)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_beamform_fd: needs F <= 32768 and the envelope in shared memory");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rtis_status s = ensure_table(p, st);
+    if (s != RTIS_OK) return s;
+    cudaError_t e = rtis::launch_fd_energyscape(p, reinterpret_cast<const float2*>(d_A), d_out, st);
+    return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_beamform_fd: launch");
 }
 
 rtis_status rtis_steering_table(rtis_plan* plan, int32_t* d_shift, float* d_weight, void* stream) {

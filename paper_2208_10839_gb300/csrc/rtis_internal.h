@@ -47,9 +47,11 @@ struct Plan {
     float* d_h = nullptr;       // [lpf_len]
     int* d_shift = nullptr;     // [D][M]
     float4* d_wt = nullptr;     // [D][M]
+    float2* d_dphase = nullptr; // [D][M] delta / F (hi, lo)
     // device workspaces (owned)
     float2* d_Z = nullptr;      // [M][2][P] half-size spectra
     float2* d_a = nullptr;      // [M][N] analytic matched-filter output
+    float2* d_A = nullptr;      // [M][Kb] in-band matched-filter spectra (frequency-domain path)
     unsigned* d_status = nullptr;
     size_t bytes = 0;
 
@@ -90,6 +92,8 @@ cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStrea
 cudaError_t launch_steering_table(Plan& p, cudaStream_t st);
 cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, float* d_out, cudaStream_t st);
 size_t td_smem_bytes(const Plan& p);
+cudaError_t launch_fd_energyscape(const Plan& p, const float2* d_A, float* d_out, cudaStream_t st);
+size_t fdes_smem_bytes(const Plan& p);
 cudaError_t td_configure(const Plan& p);
 
 bool encode_tmap_2d_u64(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows,

@@ -82,6 +82,13 @@ class Plan:
         nat.rtis_beamform_td(self.handle, a, out, stream)
         return out
 
+    def beamform_fd(self, A, out=None, stream=None):
+        """In-band spectra complex64 [M][Kb] (already / F) -> energyscape via the frequency-domain path."""
+        if out is None:
+            out = self._torch.empty((self.D, self.n_out), dtype=self._torch.float32, device=A.device)
+        nat.rtis_beamform_fd(self.handle, A, out, stream)
+        return out
+
     def steering_table(self, stream=None):
         t = self._torch
         dev = self._dev()

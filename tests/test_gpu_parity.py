@@ -222,3 +222,71 @@ def test_process_hemisphere_full_size_sampled(torch_cuda):
     d_ref, i_ref = np.unravel_index(np.argmax(E_ref), E_ref.shape)
     assert (pick[d_ref], i_ref) == (d_gpu, i_gpu)
     assert abs(E_ref.max() - peak) <= E_TOL * peak
+
+
+# ----------------------------------------------------------------------------- frequency-domain path
+def test_beamform_fd_from_oracle_spectrum(torch_cuda):
+    """The frequency-domain DAS + envelope kernel alone, fed the oracle's in-band spectra."""
+    torch = torch_cuda
+    cfg = synth.single_sensor()
+    A, k_lo, F = orc.mf_spectrum(cfg["x"], cfg["chirp"], cfg["fs"])
+    delta = orc.steering_delays(cfg["mic_xyz"], cfg["dirs"], cfg["fs"], cfg["c"])
+    E_ref = orc.envelope_decimate(orc.das_fd(A, k_lo, F, cfg["n_samples"], delta), orc.lpf_taps())
+    with make_plan(cfg, path="fd") as p:
+        E = p.beamform_fd(to_dev(torch, (A / F).astype(np.complex64)))
+        assert p.sync() == 0
+        rel = assert_energyscape(E.cpu().numpy(), E_ref)
+    assert rel < 1e-5
+
+
+def test_process_fd_single_sensor_config(torch_cuda):
+    torch = torch_cuda
+    cfg = synth.single_sensor()
+    E_ref = orc.energyscape(cfg["x"], cfg["chirp"], cfg["mic_xyz"], cfg["dirs"], cfg["fs"], cfg["c"], path="fd")
+    with make_plan(cfg, path="fd") as p:
+        E = p.process(to_dev(torch, cfg["x"]))
+        assert p.sync() == 0
+        assert_energyscape(E.cpu().numpy(), E_ref)
+
+
+@pytest.mark.parametrize("M,N,D,decim,taps", [
+    (1, 4096, 1, 10, None),
+    (7, 4100, 13, 10, None),
+    (17, 1000, 33, 3, 13),
+    (32, 6000, 9, 7, 29),
+])
+def test_process_fd_edge_shapes(torch_cuda, M, N, D, decim, taps):
+    torch = torch_cuda
+    rng = np.random.default_rng(M * 1000 + N + 7)
+    mic = synth.mic_array(M, M)
+    dirs = synth.fibonacci_hemisphere(D)
+    chirp = synth.chirp().astype(np.float32)
+    x = synth.random_measurement(N + D + 1, M, N, -20000, 20000)
+    h = None if taps is None else rng.uniform(0.0, 1.0, size=taps).astype(np.float32)
+    E_ref = orc.energyscape(x, chirp, mic, dirs, synth.FS, synth.C_SOUND, path="fd", R=decim,
+                            h=None if h is None else h.astype(np.float64))
+    cfg = dict(mic_xyz=mic, fs=synth.FS, chirp=chirp, dirs=dirs, n_samples=N)
+    with make_plan(cfg, decim=decim, lpf_taps=h, path="fd") as p:
+        E = p.process(to_dev(torch, x))
+        assert p.sync() == 0
+        assert_energyscape(E.cpu().numpy(), E_ref)
+
+
+@pytest.mark.slow
+def test_process_fd_hemisphere_full_size_sampled(torch_cuda):
+    torch = torch_cuda
+    cfg = synth.hemisphere()
+    with make_plan(cfg, path="fd") as p:
+        E = p.process(to_dev(torch, cfg["x"]))
+        assert p.sync() == 0
+        E = E.cpu().numpy().astype(np.float64)
+    A, k_lo, F = orc.mf_spectrum(cfg["x"], cfg["chirp"], cfg["fs"])
+    delta = orc.steering_delays(cfg["mic_xyz"], cfg["dirs"], cfg["fs"], cfg["c"])
+    rng = np.random.default_rng(1)
+    top = np.argsort(E.max(axis=1))[-16:]
+    pick = np.unique(np.concatenate([top, rng.choice(E.shape[0], 32, replace=False)]))
+    E_ref = orc.envelope_decimate(orc.das_fd(A, k_lo, F, cfg["n_samples"], delta[pick]), orc.lpf_taps())
+    assert np.max(np.abs(E[pick] - E_ref)) <= E_TOL * E_ref.max()
+    d_gpu, i_gpu = np.unravel_index(np.argmax(E), E.shape)
+    d_ref, i_ref = np.unravel_index(np.argmax(E_ref), E_ref.shape)
+    assert (pick[d_ref], i_ref) == (d_gpu, i_gpu)
