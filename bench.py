@@ -225,6 +225,77 @@ def run_fd_gemm(args, rank, world, local):
     g.close()
 
 
+def run_ring(args, rank, world, local):
+    """8 sensors on a ring, N in {4096..32768}, D in {512..4096}: one batch per step."""
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2208_10839_gb300 import Batch, Plan
+    from paper_2208_10839_gb300 import build as _b
+    _b.build()
+    dev = torch.device("cuda", local)
+    ring = synth.ring_sensors(seed_scene=3 + 1000 * rank)
+    sensors = ring["sensors"]
+    plans = [Plan(s["mic_xyz"], s["fs"], s["chirp"], s["dirs"], s["n_samples"]) for s in sensors]
+    xs = [torch.from_numpy(s["x"]).to(dev) for s in sensors]
+    outs = [torch.empty((p.D, p.n_out), dtype=torch.float32, device=dev) for p in plans]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    batch = Batch(plans)
+    for _ in range(args.warmup):  # the first run autotunes
+        flush.fill_(1.0)
+        batch.run(xs, outs)
+    torch.cuda.synchronize()
+    assert batch.sync() == 0
+    info = batch.info
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            batch.run(xs, outs)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    # the same sensors one rtis_process at a time, for comparison
+    seq = []
+    for k in range(max(3, args.steps // 4)):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for p, x, o in zip(plans, xs, outs):
+            p.process(x, o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq.append(e0.elapsed_time(e1))
+    if world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt[0])
+    n_s = len(sensors)
+    line = {
+        "metric": "energyscapes/s (ring of 8 sensors, ragged N and D, one batch per step)",
+        "value": world * args.steps * n_s / t, "unit": "energyscapes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": ring["name"], "sensors": [(s["n_samples"], int(s["dirs"].shape[0])) for s in sensors],
+                   "l2": "flushed between steps"},
+        "autotune": {"variant": info.variant, "grid": info.grid, "tiles": info.total_tiles,
+                     "beamformer_ms": info.tuned_ms},
+        "sequential_rtis_process_ms": statistics.mean(seq),
+        "gpu_launches": args.steps * (2 * n_s + 1),
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -233,9 +304,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-dirs", type=int, default=128, help="directions in the oracle's timed sample")
-    ap.add_argument("--workload", default="hemisphere", choices=["hemisphere", "fd_gemm"],
+    ap.add_argument("--workload", default="hemisphere", choices=["hemisphere", "fd_gemm", "ring"],
                     help="hemisphere: the energyscape chain (default); fd_gemm: the 1200-bin frequency-domain "
-                         "beamforming GEMM (32 mics x 64 frames -> 2048 directions)")
+                         "beamforming GEMM (32 mics x 64 frames -> 2048 directions); ring: 8 sensors with "
+                         "uneven lengths and direction sets in one autotuned, graph-replayed batch")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--bins", type=int, default=1200, help="fd_gemm: frequency bins (1200 = the full workload)")
     args = ap.parse_args()
@@ -253,6 +325,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if args.workload == "fd_gemm":
         return run_fd_gemm(args, rank, world, local)
+    if args.workload == "ring":
+        return run_ring(args, rank, world, local)
 
     import synth
     from paper_2208_10839_gb300 import Plan, _native as nat

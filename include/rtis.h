@@ -93,6 +93,9 @@ typedef struct rtis_plan_info {
     int halo;                    /* staged samples each side of a TD tile */
     int max_shift;               /* largest |floor(delta)| the TD kernel accepts */
     size_t workspace_bytes;      /* device memory the plan holds */
+    int td_variant;              /* time-domain beamformer stage layout chosen at creation */
+    int td_grid;                 /* and its grid (CTAs) */
+    float td_tuned_ms;           /* its time on this device when tuned */
 } rtis_plan_info;
 
 /*
@@ -107,7 +110,9 @@ typedef struct rtis_plan_info {
  * Limits: 1 <= n_mics <= 32; 1 <= n_dirs; chirp_len >= 1; the in-band bins
  * must number at most F/4 and lie below F/4.  On success *out owns the plan
  * (free with rtis_plan_destroy); on failure *out is NULL.  Synchronises the
- * device once (table upload).
+ * device (table upload) and autotunes the time-domain beamformer's stage
+ * layout and grid by timing the candidates on the plan's zeroed workspace
+ * (a few ms).
  */
 rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, double fs,
                              const float* chirp, int chirp_len, const float* directions,
@@ -170,6 +175,43 @@ rtis_status rtis_steering_table(rtis_plan* plan, int32_t* d_shift, float* d_weig
  * device-side check fired since the last sync (bits in *bits if non-NULL).
  */
 rtis_status rtis_plan_sync(rtis_plan* plan, unsigned* bits);
+
+/*
+ * Many sensors at once (the paper's multi-sensor network, Sec. 3; several
+ * sensors on one GPU, Sec. 5): plans with their own geometry, record length
+ * and direction set, processed on the time-domain path.  Every sensor's
+ * matched filter runs, then ONE persistent beamformer launch walks the tiles
+ * of all sensors (at most 16 plans per batch).
+ *
+ * rtis_process_batch -- plain launches on `stream`; allocates nothing.
+ *   plans  [n] plans (not owned); d_in [n] device int16 [M_s][N_s];
+ *   d_out [n] device float [D_s][n_out_s].
+ *   Device-side checks report into plans[0]'s status word.
+ *
+ * rtis_batch_create / rtis_batch_run / rtis_batch_destroy -- a reusable
+ * batch.  The first run autotunes the beamformer (three stage layouts x three
+ * grids: 1 or 2 persistent CTAs per SM, or one CTA per tile, each timed on
+ * the real inputs; the outputs are
+ * written several times); every run replays the batch as a CUDA graph on an
+ * internal stream, ordered after and before `stream` with events.  A new set
+ * of input/output pointers re-captures the graph.  The plans must outlive
+ * the batch; rtis_batch_sync waits for it and reads its status word.
+ */
+typedef struct rtis_batch rtis_batch;
+typedef struct rtis_batch_info {
+    int n_sensors, total_tiles;
+    int tuned;        /* 1 once the first run has autotuned */
+    int variant;      /* beamformer stage layout: 0 = 2 mics x 4 stages, 1 = 4 x 2, 2 = 1 x 8 */
+    int grid;         /* beamformer CTAs */
+    float tuned_ms;   /* beamformer time of the chosen candidate */
+} rtis_batch_info;
+rtis_status rtis_process_batch(rtis_plan* const* plans, int n, const int16_t* const* d_in, float* const* d_out,
+                               void* stream);
+rtis_status rtis_batch_create(rtis_batch** out, rtis_plan* const* plans, int n);
+rtis_status rtis_batch_run(rtis_batch* b, const int16_t* const* d_in, float* const* d_out, void* stream);
+rtis_status rtis_batch_get_info(const rtis_batch* b, rtis_batch_info* info);
+rtis_status rtis_batch_sync(rtis_batch* b, unsigned* bits);
+void rtis_batch_destroy(rtis_batch* b);
 
 /*
  * Frequency-domain delay-and-sum as a batched complex GEMM (the phase-ramp

@@ -50,7 +50,13 @@ class rtis_plan_info(C.Structure):
         ("fft_len", C.c_int), ("k_lo", C.c_int), ("k_hi", C.c_int),
         ("decim", C.c_int), ("lpf_len", C.c_int), ("n_out", C.c_int),
         ("halo", C.c_int), ("max_shift", C.c_int), ("workspace_bytes", C.c_size_t),
+        ("td_variant", C.c_int), ("td_grid", C.c_int), ("td_tuned_ms", C.c_float),
     ]
+
+
+class rtis_batch_info(C.Structure):
+    _fields_ = [("n_sensors", C.c_int), ("total_tiles", C.c_int), ("tuned", C.c_int), ("variant", C.c_int),
+                ("grid", C.c_int), ("tuned_ms", C.c_float)]
 
 
 class RtisError(RuntimeError):
@@ -79,6 +85,12 @@ _PROTOS = {
                                       C.POINTER(C.c_float), C.c_int]),
     "rtis_fd_gemm_run": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_fd_gemm_destroy": (None, [_VP]),
+    "rtis_process_batch": (C.c_int, [C.POINTER(_VP), C.c_int, C.POINTER(_VP), C.POINTER(_VP), _VP]),
+    "rtis_batch_create": (C.c_int, [C.POINTER(_VP), C.POINTER(_VP), C.c_int]),
+    "rtis_batch_run": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP), _VP]),
+    "rtis_batch_get_info": (C.c_int, [_VP, C.POINTER(rtis_batch_info)]),
+    "rtis_batch_sync": (C.c_int, [_VP, C.POINTER(C.c_uint)]),
+    "rtis_batch_destroy": (None, [_VP]),
     "rtis_status_string": (C.c_char_p, [C.c_int]),
     "rtis_last_error": (C.c_char_p, []),
 }
@@ -213,6 +225,47 @@ def rtis_fd_gemm_run(g, d_X, d_Y, stream=None):
 
 def rtis_fd_gemm_destroy(g):
     lib().rtis_fd_gemm_destroy(g)
+
+
+def _vp_array(items):
+    arr = (_VP * len(items))()
+    for i, it in enumerate(items):
+        arr[i] = ptr(it)
+    return arr
+
+
+def rtis_process_batch(plans, d_in, d_out, stream=None):
+    """Several plans' recordings -> energyscapes, one batched beamformer launch (no graph)."""
+    check(lib().rtis_process_batch(_vp_array(plans), len(plans), _vp_array(d_in), _vp_array(d_out),
+                                   stream_handle(stream)), "rtis_process_batch")
+
+
+def rtis_batch_create(plans):
+    h = _VP()
+    check(lib().rtis_batch_create(C.byref(h), _vp_array(plans), len(plans)), "rtis_batch_create")
+    return h.value
+
+
+def rtis_batch_run(b, d_in, d_out, stream=None):
+    check(lib().rtis_batch_run(b, _vp_array(d_in), _vp_array(d_out), stream_handle(stream)), "rtis_batch_run")
+
+
+def rtis_batch_get_info(b) -> rtis_batch_info:
+    info = rtis_batch_info()
+    check(lib().rtis_batch_get_info(b, C.byref(info)), "rtis_batch_get_info")
+    return info
+
+
+def rtis_batch_sync(b) -> int:
+    bits = C.c_uint(0)
+    st = lib().rtis_batch_sync(b, C.byref(bits))
+    if st not in (RTIS_OK, RTIS_ERR_TIMEOUT):
+        check(st, "rtis_batch_sync")
+    return bits.value
+
+
+def rtis_batch_destroy(b):
+    lib().rtis_batch_destroy(b)
 
 
 def rtis_plan_sync(plan) -> int:

@@ -25,6 +25,9 @@
 //     filters and subsamples its own direction, storing E coalesced.
 // The tile's 960 samples cover bins_per_tile output bins plus the low-pass
 // halo, so no beam sample ever goes to global memory.
+#include <algorithm>
+#include <cstring>
+
 #include "ptx.cuh"
 #include "rtis_internal.h"
 
@@ -68,15 +71,6 @@ __global__ void steering_table_kernel(const float* __restrict__ mic, const float
     const float dp_hi = static_cast<float>(dp);
     dphase[idx] = make_float2(dp_hi, static_cast<float>(dp - dp_hi));
 }
-
-struct TdArgs {
-    const int* shift;
-    const float4* wt;
-    const float* h;
-    float* E;
-    unsigned* status;
-    int M, N, D, R, lpf_len, n_out, H, row, nbox, bins_per_tile;
-};
 
 // packed pair helpers: a 64-bit register holding (re, im) of one complex sample
 __device__ __forceinline__ uint64_t pack2(float x, float y) {
@@ -125,47 +119,28 @@ __device__ __forceinline__ void td_mic(uint64_t (&acc)[kTdOutPerThread], const u
     }
 }
 
+// Persistent over a flat list of tiles that may span several sensors (each
+// with its own geometry, record length and direction set).  Tile t of sensor
+// s covers 8 directions (direction group t % n_dgroups) x one range tile.
 // Stages are released without CTA barriers: after a warp finishes a stage it
 // bumps that buffer's counter, and the last of the CTA's warps to do so
-// issues the TMA refill.  Waits are bounded; a timeout sets the status word,
-// stops this thread's compute, and the CTA drains its copies before exit.
+// issues the TMA refill.  Barrier phases run on across tiles.  Waits are
+// bounded; a timeout sets the status word, stops the CTA's compute, and the
+// CTA drains its copies before exit.
+template <int MS, int NS>
 __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
-    td_beamform_kernel(const __grid_constant__ CUtensorMap tmap, const TdArgs args) {
+    td_beamform_kernel(const __grid_constant__ TdMaps maps, const __grid_constant__ TdBatch bt) {
     constexpr int NT = 32 * kTdDirsPerCta;
-    constexpr int MS = kTdMicsPerStage;
-    constexpr int NS = kTdStages;
     constexpr int T = kTdOutPerThread;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int row = args.row;
     float2* stage = reinterpret_cast<float2*>(smem_raw);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + static_cast<size_t>(NS) * MS * row * 8);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + static_cast<size_t>(NS) * MS * bt.row_max * 8);
     int* done = reinterpret_cast<int*>(bar + NS);
     int* issued = done + NS;
     float* hs = reinterpret_cast<float*>(issued + NS);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int d = blockIdx.x * kTdDirsPerCta + warp;
-    const int i0 = blockIdx.y * args.bins_per_tile;
-    const int half = (args.lpf_len - 1) >> 1;
-    const int n_start = args.R * i0 - half;
-    const int x0 = (n_start - args.H) & ~1;  // even: 16-byte aligned TMA x coordinate
-    const int M = args.M;
-    const int nstages = (M + MS - 1) / MS;
-    const uint32_t stage_bytes = static_cast<uint32_t>(MS * args.nbox * kTdBox * 8);
-
-    auto issue = [&](int st) {
-        const int b = st % NS;
-        issued[b] += 1;
-        ptx::mbar_arrive_expect_tx(&bar[b], stage_bytes);
-        for (int mi = 0; mi < MS; ++mi) {
-            float2* dst = stage + static_cast<size_t>(b * MS + mi) * row;
-            for (int bx = 0; bx < args.nbox; ++bx)
-                ptx::tma_load_2d(dst + bx * kTdBox, &tmap, x0 + bx * kTdBox, st * MS + mi, &bar[b]);
-        }
-    };
-
     if (threadIdx.x == 0) {
-        ptx::prefetch_tmap(&tmap);
         for (int b = 0; b < NS; ++b) {
             ptx::mbar_init(&bar[b], 1);
             done[b] = 0;
@@ -174,67 +149,122 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
         ptx::fence_mbar_init();
         ptx::fence_proxy_async();
     }
-    for (int j = threadIdx.x; j < args.lpf_len; j += NT) hs[j] = args.h[j];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < NS && st < nstages; ++st) issue(st);
-    }
 
-    // lane m of each warp holds the steering entry of mic m for this warp's direction
-    const bool dir_ok = d < args.D;
-    int my_shift = 0;
-    float4 my_w = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (dir_ok && lane < M) {
-        my_shift = __ldg(args.shift + static_cast<size_t>(d) * M + lane);
-        my_w = __ldg(args.wt + static_cast<size_t>(d) * M + lane);
-    }
-
-    uint64_t acc[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) acc[t] = 0ull;
-    const int lane_base = n_start - x0 + lane * T - 1;  // smem index of a[n_start + lane*T - 1]
-
+    int g0 = 0;  // stages consumed by this CTA before the current tile
     bool timed_out = false;
-    for (int st = 0; st < nstages; ++st) {
-        const int b = st % NS;
-        if (!timed_out) {
-            const uint32_t par = static_cast<uint32_t>((st / NS) & 1);
-            if (!ptx::mbar_wait_bounded(&bar[b], par, kWaitPolls)) {
-                timed_out = true;
-                atomicOr(args.status, RTIS_DEV_TIMEOUT);
-            }
-        }
-        if (dir_ok && !__any_sync(0xffffffffu, timed_out)) {
-#pragma unroll 1
+    for (int tile = blockIdx.x; tile < bt.total_tiles; tile += gridDim.x) {
+        int si = 0;
+        while (si + 1 < bt.n_sensors && tile >= bt.s[si + 1].tile_base) ++si;
+        const TdSensor& S = bt.s[si];
+        const CUtensorMap* tmap = &maps.m[si];
+        const int local = tile - S.tile_base;
+        const int dg = local % S.n_dgroups;
+        const int d = dg * kTdDirsPerCta + warp;
+        const int i0 = (local / S.n_dgroups) * S.bins_per_tile;
+        const int half = (S.lpf_len - 1) >> 1;
+        const int n_start = S.R * i0 - half;
+        const int x0 = (n_start - S.H) & ~1;  // even: 16-byte aligned TMA x coordinate
+        const int M = S.M, row = S.row;
+        const int nstages = (M + MS - 1) / MS;
+        const uint32_t stage_bytes = static_cast<uint32_t>(MS * S.nbox * kTdBox * 8);
+
+        auto issue = [&](int st) {
+            const int b = (g0 + st) % NS;
+            issued[b] += 1;
+            ptx::mbar_arrive_expect_tx(&bar[b], stage_bytes);
             for (int mi = 0; mi < MS; ++mi) {
-                const int m = st * MS + mi;
-                if (m >= M) break;
-                const int J = __shfl_sync(0xffffffffu, my_shift, m);
-                const float f0 = __shfl_sync(0xffffffffu, my_w.x, m);
-                const float f1 = __shfl_sync(0xffffffffu, my_w.y, m);
-                const float f2 = __shfl_sync(0xffffffffu, my_w.z, m);
-                const float f3 = __shfl_sync(0xffffffffu, my_w.w, m);
-                const int s0 = lane_base + J;  // parity is warp-uniform (T even)
-                const ulonglong2* p =
-                    reinterpret_cast<const ulonglong2*>(stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
-                if (s0 & 1)
-                    td_mic<true>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
-                else
-                    td_mic<false>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+                float2* dst = stage + static_cast<size_t>(b * MS + mi) * row;
+                for (int bx = 0; bx < S.nbox; ++bx)
+                    ptx::tma_load_2d(dst + bx * kTdBox, tmap, x0 + bx * kTdBox, st * MS + mi, &bar[b]);
+            }
+        };
+
+        __syncthreads();  // the previous tile's epilogue is done with the stage buffers and taps
+        if (threadIdx.x == 0) {
+            ptx::prefetch_tmap(tmap);
+            for (int st = 0; st < NS && st < nstages; ++st) issue(st);
+        }
+        for (int j = threadIdx.x; j < S.lpf_len; j += NT) hs[j] = S.h[j];
+
+        // lane m of each warp holds the steering entry of mic m for this warp's direction
+        const bool dir_ok = d < S.D;
+        int my_shift = 0;
+        float4 my_w = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (dir_ok && lane < M) {
+            my_shift = __ldg(S.shift + static_cast<size_t>(d) * M + lane);
+            my_w = __ldg(S.wt + static_cast<size_t>(d) * M + lane);
+        }
+
+        uint64_t acc[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) acc[t] = 0ull;
+        const int lane_base = n_start - x0 + lane * T - 1;  // smem index of a[n_start + lane*T - 1]
+
+        for (int st = 0; st < nstages; ++st) {
+            const int b = (g0 + st) % NS;
+            if (!timed_out) {
+                const uint32_t par = static_cast<uint32_t>(((g0 + st) / NS) & 1);
+                if (!ptx::mbar_wait_bounded(&bar[b], par, kWaitPolls)) {
+                    timed_out = true;
+                    atomicOr(bt.status, RTIS_DEV_TIMEOUT);
+                }
+            }
+            if (dir_ok && !__any_sync(0xffffffffu, timed_out)) {
+#pragma unroll 1
+                for (int mi = 0; mi < MS; ++mi) {
+                    const int m = st * MS + mi;
+                    if (m >= M) break;
+                    const int J = __shfl_sync(0xffffffffu, my_shift, m);
+                    const float f0 = __shfl_sync(0xffffffffu, my_w.x, m);
+                    const float f1 = __shfl_sync(0xffffffffu, my_w.y, m);
+                    const float f2 = __shfl_sync(0xffffffffu, my_w.z, m);
+                    const float f3 = __shfl_sync(0xffffffffu, my_w.w, m);
+                    const int s0 = lane_base + J;  // parity is warp-uniform (T even)
+                    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
+                        stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
+                    if (s0 & 1)
+                        td_mic<true>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+                    else
+                        td_mic<false>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+                }
+            }
+            // release buffer b; the CTA's last warp to get here refills it
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                const int prev = atomicAdd(&done[b], 1);
+                if (prev == kTdDirsPerCta - 1) {
+                    done[b] = 0;
+                    __threadfence_block();
+                    if (st + NS < nstages) {
+                        ptx::fence_proxy_async();
+                        issue(st + NS);
+                    }
+                }
             }
         }
-        // release buffer b; the CTA's last warp to get here refills it
+        g0 += nstages;
+
+        if (__syncthreads_or(timed_out)) break;  // uniform: leave the tile loop, drain below
+
+        // epilogue: envelope of this warp's beam over the tile, then low-pass + subsample
+        float* env = reinterpret_cast<float*>(smem_raw) + warp * kTdWarpSamples;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int n = n_start + lane * T + t;
+            const float2 v = unpack2(acc[t]);
+            env[lane * T + t] = (n >= 0 && n < S.N) ? sqrtf(v.x * v.x + v.y * v.y) : 0.f;
+        }
         __syncwarp();
-        if (lane == 0) {
-            __threadfence_block();
-            const int prev = atomicAdd(&done[b], 1);
-            if (prev == kTdDirsPerCta - 1) {
-                done[b] = 0;
-                __threadfence_block();
-                if (st + NS < nstages) {
-                    ptx::fence_proxy_async();
-                    issue(st + NS);
-                }
+        if (dir_ok) {
+            float* Erow = S.E + static_cast<size_t>(d) * S.n_out;
+            for (int il = lane; il < S.bins_per_tile; il += 32) {
+                const int i = i0 + il;
+                if (i >= S.n_out) break;
+                const float* e = env + S.R * il;
+                float acc_e = 0.f;
+                for (int j = 0; j < S.lpf_len; ++j) acc_e = fmaf(hs[j], e[j], acc_e);
+                Erow[i] = acc_e;
             }
         }
     }
@@ -247,28 +277,6 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
                     ptx::mbar_wait_bounded(&bar[b], static_cast<uint32_t>((issued[b] - 1) & 1), kWaitPolls);
         }
         __syncthreads();
-        return;
-    }
-
-    // epilogue: envelope of this warp's beam over the tile, then low-pass + subsample
-    float* env = reinterpret_cast<float*>(smem_raw) + warp * kTdWarpSamples;
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int n = n_start + lane * T + t;
-        const float2 v = unpack2(acc[t]);
-        env[lane * T + t] = (n >= 0 && n < args.N) ? sqrtf(v.x * v.x + v.y * v.y) : 0.f;
-    }
-    __syncwarp();
-    if (dir_ok) {
-        float* Erow = args.E + static_cast<size_t>(d) * args.n_out;
-        for (int il = lane; il < args.bins_per_tile; il += 32) {
-            const int i = i0 + il;
-            if (i >= args.n_out) break;
-            const float* e = env + args.R * il;
-            float acc_e = 0.f;
-            for (int j = 0; j < args.lpf_len; ++j) acc_e = fmaf(hs[j], e[j], acc_e);
-            Erow[i] = acc_e;
-        }
     }
 }
 
@@ -285,37 +293,120 @@ cudaError_t launch_steering_table(Plan& p, cudaStream_t st) {
     return e;
 }
 
-size_t td_smem_bytes(const Plan& p) {
-    return static_cast<size_t>(kTdStages) * kTdMicsPerStage * p.td_row * 8 + kTdStages * (8 + 4 + 4) +
-           static_cast<size_t>(p.lpf_len) * 4;
+size_t td_smem_bytes(int row_max, int lpf_max) {
+    // stage ring (the same bytes for every (mics per stage, stages) variant), then
+    // barriers and counters for up to 8 stages, then the low-pass taps
+    return static_cast<size_t>(kTdStages) * kTdMicsPerStage * row_max * 8 + 8 * (8 + 4 + 4) +
+           static_cast<size_t>(lpf_max) * 4;
+}
+size_t td_smem_bytes(const Plan& p) { return td_smem_bytes(p.td_row, p.lpf_len); }
+
+namespace {
+template <int MS, int NS>
+cudaError_t td_launch_t(const TdMaps& maps, const TdBatch& bt, int grid, size_t smem, cudaStream_t st) {
+    static_assert(MS * NS == kTdMicsPerStage * kTdStages, "variants share one shared-memory size");
+    cudaError_t e = cudaFuncSetAttribute(td_beamform_kernel<MS, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    td_beamform_kernel<MS, NS><<<grid, 32 * kTdDirsPerCta, smem, st>>>(maps, bt);
+    return cudaGetLastError();
+}
+}  // namespace
+
+void td_fill_sensor(const Plan& p, float* d_out, int tile_base, TdSensor* s) {
+    s->shift = p.d_shift;
+    s->wt = p.d_wt;
+    s->h = p.d_h;
+    s->E = d_out;
+    s->M = p.M;
+    s->N = p.N;
+    s->D = p.D;
+    s->R = p.R;
+    s->lpf_len = p.lpf_len;
+    s->n_out = p.n_out;
+    s->H = p.H;
+    s->row = p.td_row;
+    s->nbox = p.td_nbox;
+    s->bins_per_tile = p.td_bins_per_tile;
+    s->n_dgroups = (p.D + kTdDirsPerCta - 1) / kTdDirsPerCta;
+    s->tile_base = tile_base;
 }
 
-cudaError_t td_configure(const Plan& p) {
-    return cudaFuncSetAttribute(td_beamform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(td_smem_bytes(p)));
+int td_tiles(const Plan& p) {
+    return ((p.D + kTdDirsPerCta - 1) / kTdDirsPerCta) * ((p.n_out + p.td_bins_per_tile - 1) / p.td_bins_per_tile);
+}
+
+cudaError_t launch_td_batch(const TdMaps& maps, const TdBatch& bt, int variant, int grid, cudaStream_t st) {
+    const size_t smem = td_smem_bytes(bt.row_max, bt.lpf_max);
+    switch (variant) {
+        case 0: return td_launch_t<2, 4>(maps, bt, grid, smem, st);
+        case 1: return td_launch_t<4, 2>(maps, bt, grid, smem, st);
+        case 2: return td_launch_t<1, 8>(maps, bt, grid, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Times every stage layout with one CTA per tile and with two persistent CTAs
+// per SM on the plan's own workspace (the timing does not depend on the data)
+// and keeps the fastest.
+cudaError_t td_autotune(Plan& p, float* d_scratch_out) {
+    TdMaps maps;
+    maps.m[0] = p.tmap_a;
+    TdBatch bt;
+    std::memset(&bt, 0, sizeof(bt));
+    td_fill_sensor(p, d_scratch_out, 0, &bt.s[0]);
+    bt.n_sensors = 1;
+    bt.total_tiles = td_tiles(p);
+    bt.row_max = p.td_row;
+    bt.lpf_max = p.lpf_len;
+    bt.status = p.d_status;
+    int n_sm = 1, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 1;
+    const int grids[2] = {bt.total_tiles, std::min(bt.total_tiles, 2 * n_sm)};
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return e;
+    float best = 1e30f;
+    for (int v = 0; v < kTdVariants && e == cudaSuccess; ++v) {
+        for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
+            e = launch_td_batch(maps, bt, v, grids[gi], 0);  // warm-up
+            float total = 0.f;
+            for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+                cudaEventRecord(e0, 0);
+                e = launch_td_batch(maps, bt, v, grids[gi], 0);
+                cudaEventRecord(e1, 0);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                total += ms;
+            }
+            if (e == cudaSuccess && total < best) {
+                best = total;
+                p.td_variant = v;
+                p.td_grid = grids[gi];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p.td_tuned_ms = best / 2.f;
+    return e;
 }
 
 cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, float* d_out, cudaStream_t st) {
-    TdArgs a;
-    a.shift = p.d_shift;
-    a.wt = p.d_wt;
-    a.h = p.d_h;
-    a.E = d_out;
-    a.status = p.d_status;
-    a.M = p.M;
-    a.N = p.N;
-    a.D = p.D;
-    a.R = p.R;
-    a.lpf_len = p.lpf_len;
-    a.n_out = p.n_out;
-    a.H = p.H;
-    a.row = p.td_row;
-    a.nbox = p.td_nbox;
-    a.bins_per_tile = p.td_bins_per_tile;
-    const dim3 grid((p.D + kTdDirsPerCta - 1) / kTdDirsPerCta,
-                    (p.n_out + p.td_bins_per_tile - 1) / p.td_bins_per_tile);
-    td_beamform_kernel<<<grid, 32 * kTdDirsPerCta, td_smem_bytes(p), st>>>(tmap, a);
-    return cudaGetLastError();
+    TdMaps maps;
+    maps.m[0] = tmap;
+    TdBatch bt;
+    std::memset(&bt, 0, sizeof(bt));
+    td_fill_sensor(p, d_out, 0, &bt.s[0]);
+    bt.n_sensors = 1;
+    bt.total_tiles = td_tiles(p);
+    bt.row_max = p.td_row;
+    bt.lpf_max = p.lpf_len;
+    bt.status = p.d_status;
+    return launch_td_batch(maps, bt, p.td_variant, p.td_grid > 0 ? p.td_grid : bt.total_tiles, st);
 }
 
 }  // namespace rtis

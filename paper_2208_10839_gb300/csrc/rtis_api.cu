@@ -304,7 +304,6 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     RTIS_UP(p.d_h, h.data(), lpf_len * sizeof(float))
 #undef RTIS_UP
     if (e == cudaSuccess) e = cudaMemset(p.d_status, 0, sizeof(unsigned));
-    if (e == cudaSuccess) e = rtis::td_configure(p);
     if (e == cudaSuccess) e = rtis::launch_steering_table(p, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -321,6 +320,26 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     }
     unsigned bits = 0;
     cudaMemcpy(&bits, p.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (!(bits & RTIS_DEV_DELAY_RANGE)) {
+        // autotune the beamformer on the zeroed workspace with a scratch output
+        float* scratch = nullptr;
+        e = cudaMemset(p.d_a, 0, static_cast<size_t>(n_mics) * n_samples * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc(&scratch, static_cast<size_t>(n_dirs) * p.n_out * sizeof(float));
+        if (e == cudaSuccess) e = rtis::td_autotune(p, scratch);
+        if (scratch) cudaFree(scratch);
+        if (e == cudaSuccess) e = cudaMemcpy(&bits, p.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            rtis::free_plan_buffers(p);
+            delete plan;
+            cudaGetLastError();
+            return cuda_fail(e, "rtis_plan_create: beamformer autotune");
+        }
+        if (bits & RTIS_DEV_TIMEOUT) {
+            rtis::free_plan_buffers(p);
+            delete plan;
+            return fail(RTIS_ERR_TIMEOUT, "rtis_plan_create: beamformer autotune timed out");
+        }
+    }
     if (bits & RTIS_DEV_DELAY_RANGE) {
         rtis::free_plan_buffers(p);
         delete plan;
@@ -353,6 +372,9 @@ rtis_status rtis_plan_get_info(const rtis_plan* plan, rtis_plan_info* info) {
     info->halo = p.H;
     info->max_shift = p.Jlim;
     info->workspace_bytes = p.bytes;
+    info->td_variant = p.td_variant;
+    info->td_grid = p.td_grid;
+    info->td_tuned_ms = p.td_tuned_ms;
     return RTIS_OK;
 }
 

@@ -34,6 +34,8 @@ struct Plan {
     int R = 0, lpf_len = 0, n_out = 0;
     int H = 0, Jlim = 0;              // TD staging halo and accepted |shift|
     int td_bins_per_tile = 0, td_row = 0, td_nbox = 0;
+    int td_variant = 0, td_grid = 0;  // beamformer stage layout and grid, autotuned at creation
+    float td_tuned_ms = 0.f;
     double fs = 0, c = 0;
     rtis_options opt{};
 
@@ -92,9 +94,33 @@ cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStrea
 cudaError_t launch_steering_table(Plan& p, cudaStream_t st);
 cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, float* d_out, cudaStream_t st);
 size_t td_smem_bytes(const Plan& p);
+size_t td_smem_bytes(int row_max, int lpf_max);
 cudaError_t launch_fd_energyscape(const Plan& p, const float2* d_A, float* d_out, cudaStream_t st);
 size_t fdes_smem_bytes(const Plan& p);
-cudaError_t td_configure(const Plan& p);
+
+// persistent multi-sensor time-domain beamformer
+constexpr int kTdMaxSensors = 16;
+constexpr int kTdVariants = 3;  // (mics per stage, stages): (2, 4), (4, 2), (1, 8)
+struct TdSensor {
+    const int* shift;
+    const float4* wt;
+    const float* h;
+    float* E;
+    int M, N, D, R, lpf_len, n_out, H, row, nbox, bins_per_tile;
+    int n_dgroups, tile_base;  // tiles: n_dgroups x range tiles, from tile_base on
+};
+struct TdBatch {
+    TdSensor s[kTdMaxSensors];
+    int n_sensors, total_tiles, row_max, lpf_max;
+    unsigned* status;
+};
+struct TdMaps {
+    CUtensorMap m[kTdMaxSensors];
+};
+void td_fill_sensor(const Plan& p, float* d_out, int tile_base, TdSensor* s);
+int td_tiles(const Plan& p);
+cudaError_t td_autotune(Plan& p, float* d_scratch_out);
+cudaError_t launch_td_batch(const TdMaps& maps, const TdBatch& bt, int variant, int grid, cudaStream_t st);
 
 bool encode_tmap_2d_u64(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows,
                         uint32_t box_cols, uint32_t box_rows, std::string* err);

@@ -139,3 +139,54 @@ class FdGemm:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Several plans processed together: one batched beamformer launch, autotuned on
+    the first run and replayed from a CUDA graph afterwards."""
+
+    def __init__(self, plans):
+        import torch
+        self._torch = torch
+        self.plans = list(plans)
+        self.handle = nat.rtis_batch_create([p.handle for p in self.plans])
+
+    @property
+    def info(self):
+        return nat.rtis_batch_get_info(self.handle)
+
+    def run(self, xs, outs=None, stream=None):
+        t = self._torch
+        if outs is None:
+            outs = [t.empty((p.D, p.n_out), dtype=t.float32, device=x.device) for p, x in zip(self.plans, xs)]
+        nat.rtis_batch_run(self.handle, list(xs), list(outs), stream)
+        return outs
+
+    def sync(self) -> int:
+        return nat.rtis_batch_sync(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            nat.rtis_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def process_batch(plans, xs, outs=None, stream=None):
+    """One-shot batched processing without a graph (allocates nothing in the library)."""
+    import torch
+    if outs is None:
+        outs = [torch.empty((p.D, p.n_out), dtype=torch.float32, device=x.device) for p, x in zip(plans, xs)]
+    nat.rtis_process_batch([p.handle for p in plans], list(xs), list(outs), stream)
+    return outs
