@@ -37,7 +37,8 @@ import math
 import numpy as np
 
 __all__ = [
-    "fft_length", "band_bins", "to_float", "mf_spectrum", "matched_filter", "catmull_rom",
+    "fft_length", "band_bins", "to_float", "mf_spectrum", "matched_filter", "catmull_rom", "catmull_rom_deriv",
+    "lpf_adjoint", "energyscape_vjp",
     "steering_delays", "das_td", "das_td_bruteforce", "das_fd", "lpf_taps", "envelope_decimate",
     "energyscape", "steering_matrix", "fd_gemm", "DEFAULT_BAND", "DEFAULT_DECIM",
 ]
@@ -136,6 +137,14 @@ def catmull_rom(mu):
     w_1 = 0.5 * (-3.0 * mu3 + 4.0 * mu2 + mu)
     w_2 = 0.5 * (mu3 - mu2)
     return w_m1, w_0, w_1, w_2
+
+
+def catmull_rom_deriv(mu):
+    """d/dmu of the Catmull-Rom weights (taps j-1, j, j+1, j+2)."""
+    mu = np.asarray(mu, dtype=np.float64)
+    mu2 = mu * mu
+    return (0.5 * (-3.0 * mu2 + 4.0 * mu - 1.0), 0.5 * (9.0 * mu2 - 10.0 * mu),
+            0.5 * (-9.0 * mu2 + 8.0 * mu + 1.0), 0.5 * (3.0 * mu2 - 2.0 * mu))
 
 
 def steering_delays(mic_xyz, dirs, fs: float, c: float, delay_s=None):
@@ -261,6 +270,75 @@ def envelope_decimate(b, h, R: int = DEFAULT_DECIM):
     for j in range(h.shape[0]):
         E += h[j] * ep[:, j:j + R * n_out:R]
     return E
+
+
+def lpf_adjoint(G, h, R: int, n_samples: int):
+    """Transpose of envelope_decimate's low-pass + subsampling (linear in |b|):
+    G_env[d][n] = sum_i G[d][i] h[n - R i + half], n in [0, N)."""
+    G = np.asarray(G, dtype=np.float64)
+    h = np.asarray(h, dtype=np.float64)
+    D, n_out = G.shape
+    half = (h.shape[0] - 1) // 2
+    out = np.zeros((D, n_samples + 2 * half + R))
+    for j in range(h.shape[0]):
+        out[:, j:j + R * n_out:R] += h[j] * G
+    return out[:, half:half + n_samples]
+
+
+def energyscape_vjp(x_int16, chirp, mic_xyz, dirs, fs: float, c: float, G, gain=None, delay_s=None,
+                    R: int = DEFAULT_DECIM, h=None, band=DEFAULT_BAND, chunk: int = 32):
+    """Time-domain energyscape E and the gradient of <G, E> with respect to the
+    mic positions, gains and delays (hand-derived reverse pass, FP64).
+
+    With t = n + delta_dm, I = sum_q w_q(mu) a[j+q] and I' = dI/dt:
+      G_env = lpf_adjoint(G);  G_b = G_env b / |b|  (0 where b = 0)
+      dL/d delta_dm = g_m sum_n Re(conj(G_b) I'),  dL/d g_m = sum_{d,n} Re(conj(G_b) I)
+      dL/d Delta_m = fs sum_d dL/d delta_dm,  dL/d p_m = -(fs/c) sum_d dL/d delta_dm u_d
+    Returns (E, grad_xyz [M][3], grad_gain [M], grad_delay [M] (per second)).
+    """
+    a = matched_filter(x_int16, chirp, fs, band)
+    M, N = a.shape
+    u = np.asarray(dirs, dtype=np.float64)
+    D = u.shape[0]
+    g = np.ones(M) if gain is None else np.asarray(gain, dtype=np.float64)
+    delta = steering_delays(mic_xyz, dirs, fs, c, delay_s)
+    h = lpf_taps(R) if h is None else np.asarray(h, dtype=np.float64)
+    pad = int(math.ceil(np.max(np.abs(delta)))) + 4
+    ap = _zero_padded(a, pad)
+    n = np.arange(N, dtype=np.float64)
+    b = np.zeros((D, N), dtype=np.complex128)
+    for d0 in range(0, D, chunk):
+        dd = delta[d0:d0 + chunk]
+        for m in range(M):
+            t = n[None, :] + dd[:, m:m + 1]
+            j = np.floor(t)
+            w = catmull_rom(t - j)
+            idx = j.astype(np.int64) + pad
+            b[d0:d0 + chunk] += g[m] * sum(w[q] * ap[m][idx + q - 1] for q in range(4))
+    E = envelope_decimate(b, h, R)
+    G_env = lpf_adjoint(G, h, R, N)
+    mag = np.abs(b)
+    G_b = np.where(mag > 0, G_env / np.where(mag > 0, mag, 1.0), 0.0) * b
+    d_delta = np.zeros((D, M))
+    grad_gain = np.zeros(M)
+    for d0 in range(0, D, chunk):
+        dd = delta[d0:d0 + chunk]
+        gb = G_b[d0:d0 + chunk]
+        for m in range(M):
+            t = n[None, :] + dd[:, m:m + 1]
+            j = np.floor(t)
+            mu = t - j
+            w = catmull_rom(mu)
+            wd = catmull_rom_deriv(mu)
+            idx = j.astype(np.int64) + pad
+            taps = [ap[m][idx + q - 1] for q in range(4)]
+            I = sum(w[q] * taps[q] for q in range(4))
+            Id = sum(wd[q] * taps[q] for q in range(4))
+            d_delta[d0:d0 + chunk, m] = g[m] * np.sum(np.real(np.conj(gb) * Id), axis=1)
+            grad_gain[m] += np.sum(np.real(np.conj(gb) * I))
+    grad_delay = fs * np.sum(d_delta, axis=0)
+    grad_xyz = -(fs / c) * (d_delta.T @ u)
+    return E, grad_xyz, grad_gain, grad_delay
 
 
 def energyscape(x_int16, chirp, mic_xyz, dirs, fs: float, c: float, path: str = "td",

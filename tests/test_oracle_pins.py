@@ -285,3 +285,76 @@ def test_fd_gemm_bruteforce():
                 for m in range(M):
                     acc += W[k, d, m] * X[k, m, t]
                 assert abs(Y[k, d, t] - acc) < 1e-12
+
+
+# -------------------------------------------------------------- adjoint
+def test_lpf_adjoint_dot_product():
+    rng = np.random.default_rng(12)
+    R, N = 7, 301
+    h = rng.normal(size=29)
+    b = rng.normal(size=(3, N))          # a nonnegative "envelope" is not needed: the map is linear in |b|
+    env = np.abs(b)
+    G = rng.normal(size=(3, N // R))
+    lhs = np.sum(orc.envelope_decimate(env, h, R) * G)
+    rhs = np.sum(env * orc.lpf_adjoint(G, h, R, N))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_catmull_rom_derivative_matches_difference():
+    mu = np.linspace(0.02, 0.98, 25)
+    eps = 1e-6
+    for wq, dq in zip(zip(*[orc.catmull_rom(mu + s) for s in (eps, -eps)]), orc.catmull_rom_deriv(mu)):
+        np.testing.assert_allclose((wq[0] - wq[1]) / (2 * eps), dq, atol=1e-8)
+
+
+def _tiny_calibration_case():
+    rng = np.random.default_rng(21)
+    M, N, D = 4, 600, 5
+    s = synth.chirp()[:200]
+    mic = rng.uniform(-0.05, 0.05, size=(M, 3))
+    mic[:, 2] = 0.0
+    dirs = synth.fibonacci_hemisphere(D).astype(np.float64)
+    x = np.zeros((M, N), dtype=np.int16)
+    for m in range(M):
+        x[m, 150 + 3 * m:150 + 3 * m + s.size] = np.rint(s * 12000).astype(np.int16)
+    x = (x + rng.integers(-300, 300, size=(M, N))).astype(np.int16)
+    gain = rng.uniform(0.8, 1.2, size=M)
+    delay = rng.uniform(-2e-6, 2e-6, size=M)
+    G = rng.normal(size=(D, N // orc.DEFAULT_DECIM))
+    return x, s, mic, dirs, gain, delay, G
+
+
+def test_adjoint_matches_central_differences():
+    x, s, mic, dirs, gain, delay, G = _tiny_calibration_case()
+    fs, c = synth.FS, synth.C_SOUND
+    E, gx, gg, gd = orc.energyscape_vjp(x, s, mic, dirs, fs, c, G, gain, delay)
+    np.testing.assert_allclose(E, orc.energyscape(x, s, mic, dirs, fs, c, gain=gain, delay_s=delay), rtol=1e-12)
+    loss = lambda mic_, g_, d_: np.sum(G * orc.energyscape(x, s, mic_, dirs, fs, c, gain=g_, delay_s=d_))
+    for m in (0, 3):
+        for k in range(3):
+            hstep = 1e-7
+            mp, mm = mic.copy(), mic.copy()
+            mp[m, k] += hstep
+            mm[m, k] -= hstep
+            fd = (loss(mp, gain, delay) - loss(mm, gain, delay)) / (2 * hstep)
+            assert abs(fd - gx[m, k]) <= 1e-5 * (abs(gx[m, k]) + 1e-3 * np.max(np.abs(gx)))
+        hstep = 1e-6
+        gp, gm = gain.copy(), gain.copy()
+        gp[m] += hstep
+        gm[m] -= hstep
+        fd = (loss(mic, gp, delay) - loss(mic, gm, delay)) / (2 * hstep)
+        assert abs(fd - gg[m]) <= 1e-6 * abs(gg[m]) + 1e-9
+        hstep = 1e-9
+        dp, dm = delay.copy(), delay.copy()
+        dp[m] += hstep
+        dm[m] -= hstep
+        fd = (loss(mic, gain, dp) - loss(mic, gain, dm)) / (2 * hstep)
+        assert abs(fd - gd[m]) <= 1e-5 * (abs(gd[m]) + 1e-3 * np.max(np.abs(gd)))
+
+
+def test_adjoint_gain_gradient_is_exact_for_linear_scaling():
+    # E is positively homogeneous in the common gain: sum_m g_m dE/dg_m = E, so
+    # <G, E> = sum_m g_m dL/dg_m
+    x, s, mic, dirs, gain, delay, G = _tiny_calibration_case()
+    E, gx, gg, gd = orc.energyscape_vjp(x, s, mic, dirs, synth.FS, synth.C_SOUND, G, gain, delay)
+    np.testing.assert_allclose(np.sum(gain * gg), np.sum(G * E), rtol=1e-10)
