@@ -296,6 +296,154 @@ def run_ring(args, rank, world, local):
         p.close()
 
 
+def run_calibration(args, rank, world, local):
+    """Self-calibration gradient: 32 perturbed mics x 16384 samples x 2048 directions,
+    10 known reflectors; a step = energyscape + L2 loss + adjoint w.r.t. xyz/gain/delay."""
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2208_10839_gb300 import Calibrator, Plan, _native as nat
+    from paper_2208_10839_gb300 import build as _b
+    _b.build()
+    dev = torch.device("cuda", local)
+    cfg = synth.calibration(seed=4 + 1000 * rank)
+    plan = Plan(cfg["mic_nominal"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"], c=cfg["c"])
+    x = torch.from_numpy(cfg["x"]).to(dev)
+    E_ref = plan.process(torch.from_numpy(cfg["x_ref"]).to(dev)).clone()
+    cal = Calibrator(plan, cfg["mic_nominal"])
+    for _ in range(3):  # a few descent steps so the estimate is off nominal
+        cal.step(x, E_ref)
+    p_, g_, d_ = cal.params()
+    plan.set_calibration(p_, g_, d_)
+    M, N, D = plan.M, plan.N, plan.D
+    h = plan.handle
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    E = torch.empty((D, plan.n_out), dtype=torch.float32, device=dev)
+    G = torch.empty_like(E)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    gx = torch.empty((M, 3), dtype=torch.float32, device=dev)
+    gg = torch.empty(M, dtype=torch.float32, device=dev)
+    gd = torch.empty(M, dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(xin, ev=None):
+        if ev:
+            ev[0].record(stream)
+        nat.rtis_set_calibration(h, p_, g_, d_, sh)
+        nat.rtis_process(h, xin, E, sh)
+        nat.rtis_loss_l2(h, E, E_ref, G, loss, sh)
+        if ev:
+            ev[1].record(stream)
+        nat.rtis_backward(h, xin, G, gx, gg, gd, sh)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step(x)
+    torch.cuda.synchronize()
+    assert plan.sync() == 0
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            step(x, evs[k])
+        torch.cuda.synchronize()
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    bwd_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    t = sum(step_ms) / 1e3
+    # the matched filter alone (rtis_backward recomputes it first), to split the backward time
+    a_buf = torch.empty((M, N), dtype=torch.complex64, device=dev)
+    mf = []
+    for k in range(max(3, args.steps // 4)):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nat.rtis_matched_filter(h, x, a_buf, None, sh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mf.append(e0.elapsed_time(e1))
+    assert plan.sync() == 0
+
+    # end to end: pinned host recording in, gradients and loss out
+    xh = torch.from_numpy(cfg["x"]).pin_memory()
+    xd = torch.empty_like(x)
+    gh = [torch.empty(v.shape, dtype=torch.float32).pin_memory() for v in (gx, gg, gd, loss)]
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        step(xd)
+        for hv, dv in zip(gh, (gx, gg, gd, loss)):
+            hv.copy_(dv, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    n_e2e = max(args.steps // 2, 3)
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ee0.record(stream)
+    for _ in range(n_e2e):
+        e2e_step()
+    ee1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = ee0.elapsed_time(ee1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t, t_e2e = float(tt[0]), float(tt[1])
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    peak_tf = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    # adjoint: recomputed beams (4 taps x 2 FMAs) + tap correlations (4 taps x 2 FMAs) per (d, n, m)
+    flops = float(D) * N * M * 16 * 2
+    adj_s = (statistics.mean(bwd_ms) - statistics.mean(mf)) / 1e3
+    line = {
+        "metric": "calibration gradients/s (energyscape + L2 loss + adjoint wrt mic xyz, gain, delay; "
+                  "32ch x 16384 samples x 2048 dirs)",
+        "value": world * args.steps / t, "unit": "gradients/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "calibration: 32 mics perturbed by N(0, 1 mm), gains U(0.8, 1.2), delays "
+                               "U(-2, 2) us; 16384 samples, 2048 Fibonacci half-sphere dirs, 10 known reflectors",
+                   "l2": "flushed (512 MiB write) between steps, outside the timed events"},
+        "e2e": {"value": world * n_e2e / t_e2e, "unit": "gradients/s", "h2d_bytes_per_step": int(x.numel() * 2),
+                "d2h_bytes_per_step": int(4 * (gx.numel() + gg.numel() + gd.numel() + 1))},
+        "gpu_launches": 10 * args.steps,
+        "kernels_ms": {"forward_and_loss": statistics.mean(fwd_ms), "backward": statistics.mean(bwd_ms),
+                       "matched_filter": statistics.mean(mf),
+                       "adjoint_and_reduce": statistics.mean(bwd_ms) - statistics.mean(mf)},
+        "roofline": {"bound": "alu", "kernel": "td_adjoint_kernel (+ adj_reduce_kernel)",
+                     "achieved": flops / adj_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": flops / adj_s / 1e12 / peak_tf, "traffic": None,
+                     "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x "
+                                   f"{SM_MAX_MHZ_NOMINAL:.0f} MHz",
+                     "algorithmic_flops_per_launch": flops, "launch_ms": adj_s * 1e3},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        rng = np.random.default_rng(0)
+        pick = np.sort(rng.choice(D, 32, replace=False))
+        Gs = G.cpu().numpy()[pick].astype(np.float64)
+        pn, gn, dn = (v.cpu().numpy().astype(np.float64) for v in (p_, g_, d_))
+        t0 = time.perf_counter()
+        oracle.energyscape_vjp(cfg["x"], cfg["chirp"], pn, cfg["dirs"][pick], cfg["fs"], cfg["c"], Gs, gain=gn,
+                               delay_s=dn)
+        t_or = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 32.0 / D / t_or, "unit": "gradients/s", "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 oracle energyscape_vjp on 32 of {D} directions "
+                                          f"({t_or:.2f} s), scaled to {D}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,10 +452,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-dirs", type=int, default=128, help="directions in the oracle's timed sample")
-    ap.add_argument("--workload", default="hemisphere", choices=["hemisphere", "fd_gemm", "ring"],
+    ap.add_argument("--workload", default="hemisphere", choices=["hemisphere", "fd_gemm", "ring", "calibration"],
                     help="hemisphere: the energyscape chain (default); fd_gemm: the 1200-bin frequency-domain "
                          "beamforming GEMM (32 mics x 64 frames -> 2048 directions); ring: 8 sensors with "
-                         "uneven lengths and direction sets in one autotuned, graph-replayed batch")
+                         "uneven lengths and direction sets in one autotuned, graph-replayed batch; calibration: "
+                         "energyscape + L2 loss + adjoint of a perturbed 32-mic array")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--bins", type=int, default=1200, help="fd_gemm: frequency bins (1200 = the full workload)")
     args = ap.parse_args()
@@ -327,6 +476,8 @@ def main():
         return run_fd_gemm(args, rank, world, local)
     if args.workload == "ring":
         return run_ring(args, rank, world, local)
+    if args.workload == "calibration":
+        return run_calibration(args, rank, world, local)
 
     import synth
     from paper_2208_10839_gb300 import Plan, _native as nat

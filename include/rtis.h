@@ -170,6 +170,48 @@ rtis_status rtis_beamform_fd(rtis_plan* plan, const float* d_A, float* d_out, vo
 rtis_status rtis_steering_table(rtis_plan* plan, int32_t* d_shift, float* d_weight, void* stream);
 
 /*
+ * rtis_set_calibration -- replaces the array calibration the plan steers
+ * with (positions p_m, gains g_m, per-mic delays Delta_m in seconds); each
+ * pointer is a device array ([n_mics][3], [n_mics], [n_mics]) or NULL to
+ * keep the current values (initially: the create-time positions, gains 1,
+ * delays 0).  Stream-ordered; the steering tables are rebuilt on `stream`.
+ * Delays beyond opt.max_delay_s or positions moved by more than
+ * opt.position_slack_m can exceed the staged halo: the affected entries
+ * then contribute nothing and rtis_plan_sync reports RTIS_ERR_DEVICE.
+ */
+rtis_status rtis_set_calibration(rtis_plan* plan, const float* d_mic_xyz, const float* d_gain,
+                                 const float* d_delay_s, void* stream);
+
+/*
+ * rtis_backward -- reverse pass of the time-domain energyscape with respect
+ * to the calibration (not in the paper, which has no gradient): given the
+ * cotangent G = dL/dE it returns
+ *   d_grad_xyz [n_mics][3] = dL/dp_m,  d_grad_gain [n_mics] = dL/dg_m,
+ *   d_grad_delay [n_mics] = dL/dDelta_m (per second)
+ * (any of them may be NULL).  With t = n + delta_dm and Catmull-Rom value
+ * and slope weights: dL/d delta_dm = g_m sum_n Re(conj(G_b) I'), where
+ * G_b = (transposed low-pass of G) * b / |b| (0 where b = 0).  The matched
+ * filter and the beams are recomputed from d_in; nothing per direction is
+ * stored.  Reductions run in a fixed order (deterministic).
+ *   d_in        device int16 [n_mics][n_samples]
+ *   d_grad_out  device float [n_dirs][n_out]
+ */
+rtis_status rtis_backward(rtis_plan* plan, const int16_t* d_in, const float* d_grad_out, float* d_grad_xyz,
+                          float* d_grad_gain, float* d_grad_delay, void* stream);
+
+/*
+ * rtis_loss_l2 -- the self-calibration objective (not in the paper): with E
+ * the energyscape of a recording and E_ref that of the known scene,
+ *   *d_loss = sum_{d,i} (E[d][i] - E_ref[d][i])^2,  d_grad_out = 2 (E - E_ref)
+ * (d_grad_out may be NULL).  d_E, d_E_ref, d_grad_out: device float
+ * [n_dirs][n_out]; d_loss: one device float.  The sum runs in a fixed order
+ * (deterministic).  Uses the plan's adjoint scratch: do not overlap with
+ * rtis_backward on another stream.
+ */
+rtis_status rtis_loss_l2(rtis_plan* plan, const float* d_E, const float* d_E_ref, float* d_grad_out, float* d_loss,
+                         void* stream);
+
+/*
  * rtis_plan_sync -- waits for the device, then reads and clears the plan's
  * device status word.  Returns RTIS_ERR_DEVICE / RTIS_ERR_TIMEOUT if a
  * device-side check fired since the last sync (bits in *bits if non-NULL).

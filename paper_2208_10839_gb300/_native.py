@@ -78,6 +78,9 @@ _PROTOS = {
     "rtis_beamform_fd": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_steering_table": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_plan_sync": (C.c_int, [_VP, C.POINTER(C.c_uint)]),
+    "rtis_set_calibration": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "rtis_backward": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "rtis_loss_l2": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "rtis_matched_filter_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, C.c_double, C.c_double,
                                               C.c_double, _VP, _VP, _VP]),
     "rtis_fd_gemm_create": (C.c_int, [C.POINTER(_VP), C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_float), C.c_int,
@@ -266,6 +269,21 @@ def rtis_batch_sync(b) -> int:
 
 def rtis_batch_destroy(b):
     lib().rtis_batch_destroy(b)
+
+
+def rtis_set_calibration(plan, d_mic_xyz=None, d_gain=None, d_delay_s=None, stream=None):
+    check(lib().rtis_set_calibration(plan, ptr(d_mic_xyz), ptr(d_gain), ptr(d_delay_s), stream_handle(stream)),
+          "rtis_set_calibration")
+
+
+def rtis_backward(plan, d_in, d_grad_out, d_grad_xyz=None, d_grad_gain=None, d_grad_delay=None, stream=None):
+    check(lib().rtis_backward(plan, ptr(d_in), ptr(d_grad_out), ptr(d_grad_xyz), ptr(d_grad_gain), ptr(d_grad_delay),
+                              stream_handle(stream)), "rtis_backward")
+
+
+def rtis_loss_l2(plan, d_E, d_E_ref, d_grad_out, d_loss, stream=None):
+    check(lib().rtis_loss_l2(plan, ptr(d_E), ptr(d_E_ref), ptr(d_grad_out), ptr(d_loss), stream_handle(stream)),
+          "rtis_loss_l2")
 
 
 def rtis_plan_sync(plan) -> int:

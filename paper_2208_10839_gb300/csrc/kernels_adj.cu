@@ -1,0 +1,427 @@
+// Reverse pass of the time-domain energyscape with respect to the array's
+// calibration: microphone positions p_m, per-channel gains g_m and delays
+// Delta_m (the delay-and-sum of the paper's Fig. 3 / Sec. 4.1 and the
+// envelope / low-pass / subsampling of Sec. 4.3, differentiated by hand).
+//
+// With t = n + delta_dm, I = sum_q w_q(mu) a_m[j+q] and I' = dI/dt, and G the
+// cotangent of the energyscape:
+//   G_env[n] = sum_i G[i] h[n - R i + half]           (transposed low-pass)
+//   G_b[n]   = G_env[n] b[n] / |b[n]|                 (0 where b = 0)
+//   dL/d delta_dm = g_m sum_n Re(conj(G_b) I'),   dL/d g_m = sum_{d,n} Re(conj(G_b) I)
+//   dL/d Delta_m = fs sum_d dL/d delta_dm,        dL/d p_m = -(fs/c) sum_d dL/d delta_dm u_d
+//
+// Nothing per direction is stored between passes: each tile (8 directions x
+// 960 samples, the forward tiling) recomputes its beams from the staged
+// channel rows, turns them into G_b in registers, then streams the rows a
+// second time and forms, per mic, the four tap correlations
+//   C_q = sum_t Re(conj(G_b[t]) a[t + q])
+// from which both sums follow with the value and slope weights (so the
+// second pass costs what the first does).  Each tile owns the samples of its
+// output bins; per-(tile, direction, mic) partials are reduced in a fixed
+// order by a second kernel, so the gradient is deterministic.
+#include <algorithm>
+#include <cstring>
+
+#include "ptx.cuh"
+#include "rtis_internal.h"
+
+namespace rtis {
+namespace {
+
+constexpr uint32_t kAdjPolls = 1u << 22;
+constexpr int kAdjMS = 2, kAdjNS = 4;  // mics per stage, ring depth (the forward's default layout)
+
+struct AdjArgs {
+    const int* shift;
+    const float4* wraw;
+    const float4* wder;
+    const float* gain;
+    const float* h;
+    const float* G;       // [D][n_out] cotangent
+    float2* part;         // [range tiles][D][M]: (dL/d delta, dL/d g) partials
+    unsigned* status;
+    int M, N, D, R, lpf_len, n_out, H, row, nbox, bins_per_tile, seg;
+};
+
+__device__ __forceinline__ uint64_t pack2a(float x, float y) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2a(uint64_t v) {
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+    return make_float2(x, y);
+}
+__device__ __forceinline__ void fma2a(uint64_t& acc, uint64_t ww, uint64_t v) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(ww), "l"(v));
+}
+
+// forward: one mic's contribution to a lane's T samples (as the forward kernel)
+template <bool ODD>
+__device__ __forceinline__ void adj_fwd_mic(uint64_t (&acc)[kTdOutPerThread], const ulonglong2* __restrict__ p,
+                                            uint64_t w0, uint64_t w1, uint64_t w2, uint64_t w3) {
+    constexpr int T = kTdOutPerThread;
+    constexpr int NP = (T + 4) / 2;
+    uint64_t v[2 * NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const ulonglong2 q = p[k];
+        v[2 * k] = q.x;
+        v[2 * k + 1] = q.y;
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        fma2a(acc[t], w0, v[t + ODD]);
+        fma2a(acc[t], w1, v[t + 1 + ODD]);
+        fma2a(acc[t], w2, v[t + 2 + ODD]);
+        fma2a(acc[t], w3, v[t + 3 + ODD]);
+    }
+}
+
+// reverse: C_q = sum_t Re(conj(G_b[t]) a[t + q]), q = 0..3 (taps j-1 .. j+2)
+template <bool ODD>
+__device__ __forceinline__ float4 adj_corr_mic(const uint64_t (&gb)[kTdOutPerThread], const ulonglong2* __restrict__ p) {
+    constexpr int T = kTdOutPerThread;
+    constexpr int NP = (T + 4) / 2;
+    float2 v[2 * NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const ulonglong2 q = p[k];
+        v[2 * k] = unpack2a(q.x);
+        v[2 * k + 1] = unpack2a(q.y);
+    }
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const float2 g = unpack2a(gb[t]);
+        c0 = fmaf(g.x, v[t + ODD].x, fmaf(g.y, v[t + ODD].y, c0));
+        c1 = fmaf(g.x, v[t + 1 + ODD].x, fmaf(g.y, v[t + 1 + ODD].y, c1));
+        c2 = fmaf(g.x, v[t + 2 + ODD].x, fmaf(g.y, v[t + 2 + ODD].y, c2));
+        c3 = fmaf(g.x, v[t + 3 + ODD].x, fmaf(g.y, v[t + 3 + ODD].y, c3));
+    }
+    return make_float4(c0, c1, c2, c3);
+}
+
+__global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
+    td_adjoint_kernel(const __grid_constant__ CUtensorMap tmap, const AdjArgs args) {
+    constexpr int NT = 32 * kTdDirsPerCta;
+    constexpr int T = kTdOutPerThread;
+    constexpr int MS = kAdjMS, NS = kAdjNS;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int row = args.row;
+    float2* stage = reinterpret_cast<float2*>(smem_raw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + static_cast<size_t>(NS) * MS * row * 8);
+    int* done = reinterpret_cast<int*>(bar + NS);
+    int* issued = done + NS;
+    float* hs = reinterpret_cast<float*>(issued + NS);
+    float* gseg = hs + ((args.lpf_len + 3) & ~3);  // [8 warps][seg]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int d = blockIdx.x * kTdDirsPerCta + warp;
+    const int nt = blockIdx.y;
+    const int i0 = nt * args.bins_per_tile;
+    const int half = (args.lpf_len - 1) >> 1;
+    const int n_start = args.R * i0 - half;
+    const int x0 = (n_start - args.H) & ~1;
+    const int M = args.M;
+    const int ngroups = (M + MS - 1) / MS;
+    const int nstages = 2 * ngroups;  // pass A then pass B over the same rows
+    const uint32_t stage_bytes = static_cast<uint32_t>(MS * args.nbox * kTdBox * 8);
+    // samples this tile owns: those of its output bins (the last tile: up to N)
+    const int own_lo = args.R * i0;
+    const bool last_tile = (i0 + args.bins_per_tile >= args.n_out);
+    const int own_hi = last_tile ? args.N : args.R * (i0 + args.bins_per_tile);
+
+    auto issue = [&](int st) {
+        const int b = st % NS;
+        const int grp = st % ngroups;
+        issued[b] += 1;
+        ptx::mbar_arrive_expect_tx(&bar[b], stage_bytes);
+        for (int mi = 0; mi < MS; ++mi) {
+            float2* dst = stage + static_cast<size_t>(b * MS + mi) * row;
+            for (int bx = 0; bx < args.nbox; ++bx)
+                ptx::tma_load_2d(dst + bx * kTdBox, &tmap, x0 + bx * kTdBox, grp * MS + mi, &bar[b]);
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        ptx::prefetch_tmap(&tmap);
+        for (int b = 0; b < NS; ++b) {
+            ptx::mbar_init(&bar[b], 1);
+            done[b] = 0;
+            issued[b] = 0;
+        }
+        ptx::fence_mbar_init();
+        ptx::fence_proxy_async();
+    }
+    for (int j = threadIdx.x; j < args.lpf_len; j += NT) hs[j] = args.h[j];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < NS && st < nstages; ++st) issue(st);
+    }
+
+    const bool dir_ok = d < args.D;
+    int my_shift = 0;
+    float4 my_w = make_float4(0.f, 0.f, 0.f, 0.f), my_wd = my_w;
+    float my_g = 0.f;
+    if (dir_ok && lane < M) {
+        const size_t e = static_cast<size_t>(d) * M + lane;
+        my_shift = __ldg(args.shift + e);
+        my_w = __ldg(args.wraw + e);
+        my_wd = __ldg(args.wder + e);
+        my_g = __ldg(args.gain + lane);
+    }
+    // cotangent segment of this warp's direction, bins [iseg0, iseg0 + seg)
+    const int reach = (half + args.R - 1) / args.R + 1;
+    const int iseg0 = i0 - reach;
+    float* gs = gseg + warp * args.seg;
+    for (int k = lane; k < args.seg; k += 32) {
+        const int i = iseg0 + k;
+        gs[k] = (dir_ok && i >= 0 && i < args.n_out) ? __ldg(args.G + static_cast<size_t>(d) * args.n_out + i) : 0.f;
+    }
+
+    uint64_t acc[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) acc[t] = 0ull;
+    const int lane_base = n_start - x0 + lane * T - 1;
+    float sum_d = 0.f, sum_g = 0.f;  // lane m keeps mic m's totals
+    bool timed_out = false;
+
+    for (int st = 0; st < nstages; ++st) {
+        const int b = st % NS;
+        if (!timed_out) {
+            if (!ptx::mbar_wait_bounded(&bar[b], static_cast<uint32_t>((st / NS) & 1), kAdjPolls)) {
+                timed_out = true;
+                atomicOr(args.status, RTIS_DEV_TIMEOUT);
+            }
+        }
+        const bool pass_b = st >= ngroups;
+        if (dir_ok && !__any_sync(0xffffffffu, timed_out)) {
+#pragma unroll 1
+            for (int mi = 0; mi < MS; ++mi) {
+                const int m = (st % ngroups) * MS + mi;
+                if (m >= M) break;
+                const int J = __shfl_sync(0xffffffffu, my_shift, m);
+                const int s0 = lane_base + J;
+                const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
+                    stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
+                const float w0 = __shfl_sync(0xffffffffu, my_w.x, m), w1 = __shfl_sync(0xffffffffu, my_w.y, m);
+                const float w2 = __shfl_sync(0xffffffffu, my_w.z, m), w3 = __shfl_sync(0xffffffffu, my_w.w, m);
+                if (!pass_b) {
+                    const float g = __shfl_sync(0xffffffffu, my_g, m);
+                    const float f0 = g * w0, f1 = g * w1, f2 = g * w2, f3 = g * w3;
+                    if (s0 & 1)
+                        adj_fwd_mic<true>(acc, p, pack2a(f0, f0), pack2a(f1, f1), pack2a(f2, f2), pack2a(f3, f3));
+                    else
+                        adj_fwd_mic<false>(acc, p, pack2a(f0, f0), pack2a(f1, f1), pack2a(f2, f2), pack2a(f3, f3));
+                } else {
+                    const float4 C = (s0 & 1) ? adj_corr_mic<true>(acc, p) : adj_corr_mic<false>(acc, p);
+                    const float d0 = __shfl_sync(0xffffffffu, my_wd.x, m), d1 = __shfl_sync(0xffffffffu, my_wd.y, m);
+                    const float d2 = __shfl_sync(0xffffffffu, my_wd.z, m), d3 = __shfl_sync(0xffffffffu, my_wd.w, m);
+                    float sg = fmaf(w0, C.x, fmaf(w1, C.y, fmaf(w2, C.z, w3 * C.w)));
+                    float sd = fmaf(d0, C.x, fmaf(d1, C.y, fmaf(d2, C.z, d3 * C.w)));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sg += __shfl_xor_sync(0xffffffffu, sg, o);
+                        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                    }
+                    if (lane == m) {
+                        sum_g = sg;
+                        sum_d = sd;
+                    }
+                }
+            }
+        }
+        if (st == ngroups - 1 && dir_ok && !__any_sync(0xffffffffu, timed_out)) {
+            // beams of this tile are complete: turn them into G_b = G_env b / |b| on owned samples
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const int n = n_start + lane * T + t;
+                float ge = 0.f;
+                if (n >= own_lo && n < own_hi && n >= 0 && n < args.N) {
+                    // bins i with |n - R i| <= half, taken from the segment
+                    const int ilo = (n - half + args.R * reach * 4) / args.R - reach * 4;  // floor((n-half)/R)
+                    for (int i = ilo; i <= ilo + 2 * reach; ++i) {
+                        const int j = n - args.R * i + half;
+                        if (j >= 0 && j < args.lpf_len) ge = fmaf(gs[i - iseg0], hs[j], ge);
+                    }
+                }
+                const float2 v = unpack2a(acc[t]);
+                const float mag = sqrtf(v.x * v.x + v.y * v.y);
+                const float sc = mag > 0.f ? ge / mag : 0.f;
+                acc[t] = pack2a(sc * v.x, sc * v.y);
+            }
+        }
+        // release buffer b; the CTA's last warp to get here refills it
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            const int prev = atomicAdd(&done[b], 1);
+            if (prev == kTdDirsPerCta - 1) {
+                done[b] = 0;
+                __threadfence_block();
+                if (st + NS < nstages) {
+                    ptx::fence_proxy_async();
+                    issue(st + NS);
+                }
+            }
+        }
+    }
+    if (dir_ok && lane < M && !timed_out)
+        args.part[(static_cast<size_t>(nt) * args.D + d) * M + lane] = make_float2(my_g * sum_d, sum_g);
+
+    if (__syncthreads_or(timed_out)) {
+        if (threadIdx.x == 0) {
+            for (int b = 0; b < NS; ++b)
+                if (issued[b] > 0)
+                    ptx::mbar_wait_bounded(&bar[b], static_cast<uint32_t>((issued[b] - 1) & 1), kAdjPolls);
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA per mic: fixed-order sums over range tiles and directions.
+__global__ void adj_reduce_kernel(const float2* __restrict__ part, const float* __restrict__ dirs, int M, int D,
+                                  int n_tiles, double fs, double fs_over_c, float* __restrict__ gxyz,
+                                  float* __restrict__ ggain, float* __restrict__ gdelay) {
+    constexpr int NT = 256;
+    const int m = blockIdx.x;
+    float sd = 0.f, sg = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+    for (int d = threadIdx.x; d < D; d += NT) {
+        float pd = 0.f, pg = 0.f;
+        for (int t = 0; t < n_tiles; ++t) {
+            const float2 v = part[(static_cast<size_t>(t) * D + d) * M + m];
+            pd += v.x;
+            pg += v.y;
+        }
+        sd += pd;
+        sg += pg;
+        sx = fmaf(pd, dirs[3 * d], sx);
+        sy = fmaf(pd, dirs[3 * d + 1], sy);
+        sz = fmaf(pd, dirs[3 * d + 2], sz);
+    }
+    __shared__ float red[5][NT];
+    red[0][threadIdx.x] = sd;
+    red[1][threadIdx.x] = sg;
+    red[2][threadIdx.x] = sx;
+    red[3][threadIdx.x] = sy;
+    red[4][threadIdx.x] = sz;
+    __syncthreads();
+    for (int w = NT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 5; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (gdelay) gdelay[m] = static_cast<float>(fs * red[0][0]);
+        if (ggain) ggain[m] = red[1][0];
+        if (gxyz) {
+            gxyz[3 * m] = static_cast<float>(-fs_over_c * red[2][0]);
+            gxyz[3 * m + 1] = static_cast<float>(-fs_over_c * red[3][0]);
+            gxyz[3 * m + 2] = static_cast<float>(-fs_over_c * red[4][0]);
+        }
+    }
+}
+
+// L2 calibration loss: per-block partial sums of (E - E_ref)^2 (fixed tree), G = 2 (E - E_ref)
+constexpr int kLossThreads = 256, kLossBlocks = 4 * 152;
+
+__global__ void __launch_bounds__(kLossThreads) l2_loss_kernel(const float* __restrict__ E,
+                                                               const float* __restrict__ Eref,
+                                                               float* __restrict__ G, float* __restrict__ part,
+                                                               size_t n) {
+    float s = 0.f;
+    for (size_t i = static_cast<size_t>(blockIdx.x) * kLossThreads + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * kLossThreads) {
+        const float r = E[i] - Eref[i];
+        if (G) G[i] = 2.f * r;
+        s = fmaf(r, r, s);
+    }
+    __shared__ float red[kLossThreads];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kLossThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void l2_final_kernel(const float* __restrict__ part, int nb, float* __restrict__ loss) {
+    __shared__ double red[kLossThreads];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += kLossThreads) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kLossThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = static_cast<float>(red[0]);
+}
+
+int adj_seg(const Plan& p) {
+    const int half = (p.lpf_len - 1) / 2;
+    const int reach = (half + p.R - 1) / p.R + 1;
+    return p.td_bins_per_tile + 3 * reach + 2;
+}
+
+}  // namespace
+
+size_t adj_smem_bytes(const Plan& p) {
+    return static_cast<size_t>(kAdjNS) * kAdjMS * p.td_row * 8 + kAdjNS * (8 + 4 + 4) +
+           static_cast<size_t>((p.lpf_len + 3) & ~3) * 4 + static_cast<size_t>(kTdDirsPerCta) * adj_seg(p) * 4;
+}
+
+cudaError_t launch_td_adjoint(const Plan& p, const float* d_grad_out, float* d_gxyz, float* d_ggain, float* d_gdelay,
+                              cudaStream_t st) {
+    AdjArgs a;
+    a.shift = p.d_shift;
+    a.wraw = p.d_wraw;
+    a.wder = p.d_wder;
+    a.gain = p.d_gain;
+    a.h = p.d_h;
+    a.G = d_grad_out;
+    a.part = p.d_adj;
+    a.status = p.d_status;
+    a.M = p.M;
+    a.N = p.N;
+    a.D = p.D;
+    a.R = p.R;
+    a.lpf_len = p.lpf_len;
+    a.n_out = p.n_out;
+    a.H = p.H;
+    a.row = p.td_row;
+    a.nbox = p.td_nbox;
+    a.bins_per_tile = p.td_bins_per_tile;
+    a.seg = adj_seg(p);
+    const size_t smem = adj_smem_bytes(p);
+    cudaError_t e = cudaFuncSetAttribute(td_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int n_tiles = (p.n_out + p.td_bins_per_tile - 1) / p.td_bins_per_tile;
+    const dim3 grid((p.D + kTdDirsPerCta - 1) / kTdDirsPerCta, n_tiles);
+    td_adjoint_kernel<<<grid, 32 * kTdDirsPerCta, smem, st>>>(p.tmap_a, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    adj_reduce_kernel<<<p.M, 256, 0, st>>>(p.d_adj, p.d_dirs, p.M, p.D, n_tiles, p.fs, p.fs / p.c, d_gxyz, d_ggain,
+                                           d_gdelay);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l2_loss(const Plan& p, const float* d_E, const float* d_Eref, float* d_G, float* d_loss,
+                           cudaStream_t st) {
+    const size_t n = static_cast<size_t>(p.D) * p.n_out;
+    float* part = reinterpret_cast<float*>(p.d_adj);  // the adjoint's partials, free between calls
+    const int nb = static_cast<int>(std::min<size_t>(kLossBlocks, (n + kLossThreads - 1) / kLossThreads));
+    if (nb == 0) return cudaMemsetAsync(d_loss, 0, sizeof(float), st);
+    l2_loss_kernel<<<nb, kLossThreads, 0, st>>>(d_E, d_Eref, d_G, part, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    l2_final_kernel<<<1, kLossThreads, 0, st>>>(part, nb, d_loss);
+    return cudaGetLastError();
+}
+
+}  // namespace rtis

@@ -40,7 +40,8 @@ __global__ void steering_table_kernel(const float* __restrict__ mic, const float
                                       const float* __restrict__ gain, const float* __restrict__ delay_s,
                                       int M, int D, double fs, double fs_over_c, int Jlim, double inv_F,
                                       int* __restrict__ shift, float4* __restrict__ wt,
-                                      float2* __restrict__ dphase, unsigned* __restrict__ status) {
+                                      float2* __restrict__ dphase, float4* __restrict__ wraw,
+                                      float4* __restrict__ wder, unsigned* __restrict__ status) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= M * D) return;
     const int d = idx / M;
@@ -57,15 +58,28 @@ __global__ void steering_table_kernel(const float* __restrict__ mic, const float
                            static_cast<float>(g * (3.0 * mu3 - 5.0 * mu2 + 2.0)),
                            static_cast<float>(g * (-3.0 * mu3 + 4.0 * mu2 + mu)),
                            static_cast<float>(g * (mu3 - mu2)));
+    // gain-free weights and their slopes d/dmu, for the adjoint
+    float4 wr = make_float4(static_cast<float>(0.5 * (-mu3 + 2.0 * mu2 - mu)),
+                            static_cast<float>(0.5 * (3.0 * mu3 - 5.0 * mu2 + 2.0)),
+                            static_cast<float>(0.5 * (-3.0 * mu3 + 4.0 * mu2 + mu)),
+                            static_cast<float>(0.5 * (mu3 - mu2)));
+    float4 wd = make_float4(static_cast<float>(0.5 * (-3.0 * mu2 + 4.0 * mu - 1.0)),
+                            static_cast<float>(0.5 * (9.0 * mu2 - 10.0 * mu)),
+                            static_cast<float>(0.5 * (-9.0 * mu2 + 8.0 * mu + 1.0)),
+                            static_cast<float>(0.5 * (3.0 * mu2 - 2.0 * mu)));
     int j = 0;
     if (fabs(jf) <= static_cast<double>(Jlim)) {
         j = static_cast<int>(jf);
     } else {  // outside the staged halo (or not finite): contribute nothing, report
         atomicOr(status, RTIS_DEV_DELAY_RANGE);
         w = make_float4(0.f, 0.f, 0.f, 0.f);
+        wr = w;
+        wd = w;
     }
     shift[idx] = j;
     wt[idx] = w;
+    wraw[idx] = wr;
+    wder[idx] = wd;
     // frequency-domain form: delta / F cycles per bin, as an unevaluated pair hi + lo
     const double dp = delta * inv_F;
     const float dp_hi = static_cast<float>(dp);
@@ -287,7 +301,7 @@ cudaError_t launch_steering_table(Plan& p, cudaStream_t st) {
     const int nt = 256;
     steering_table_kernel<<<(total + nt - 1) / nt, nt, 0, st>>>(p.d_mic, p.d_dirs, p.d_gain, p.d_delay, p.M, p.D,
                                                               p.fs, p.fs / p.c, p.Jlim, 1.0 / p.F, p.d_shift,
-                                                              p.d_wt, p.d_dphase, p.d_status);
+                                                              p.d_wt, p.d_dphase, p.d_wraw, p.d_wder, p.d_status);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) p.table_dirty = false;
     return e;

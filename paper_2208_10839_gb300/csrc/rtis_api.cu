@@ -31,7 +31,7 @@ cudaError_t dev_alloc(T** ptr, size_t count, size_t* total) {
 
 void free_plan_buffers(Plan& p) {
     void* bufs[] = {p.d_mic, p.d_dirs, p.d_gain, p.d_delay, p.d_tw, p.d_C, p.d_h,
-                    p.d_shift, p.d_wt, p.d_dphase, p.d_Z, p.d_a, p.d_A, p.d_status};
+                    p.d_shift, p.d_wt, p.d_dphase, p.d_wraw, p.d_wder, p.d_adj, p.d_Z, p.d_a, p.d_A, p.d_status};
     for (void* b : bufs)
         if (b) cudaFree(b);
 }
@@ -280,6 +280,11 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     RTIS_ALLOC(p.d_shift, static_cast<size_t>(n_dirs) * n_mics)
     RTIS_ALLOC(p.d_wt, static_cast<size_t>(n_dirs) * n_mics)
     RTIS_ALLOC(p.d_dphase, static_cast<size_t>(n_dirs) * n_mics)
+    RTIS_ALLOC(p.d_wraw, static_cast<size_t>(n_dirs) * n_mics)
+    RTIS_ALLOC(p.d_wder, static_cast<size_t>(n_dirs) * n_mics)
+    // adjoint partials [range tiles][D][M]; also the loss's per-block partials (<= 1024 floats)
+    RTIS_ALLOC(p.d_adj, std::max<size_t>(512, static_cast<size_t>((p.n_out + p.td_bins_per_tile - 1) /
+                                                                   p.td_bins_per_tile) * n_dirs * n_mics))
     RTIS_ALLOC(p.d_A, static_cast<size_t>(n_mics) * p.Kb)
     RTIS_ALLOC(p.d_Z, static_cast<size_t>(n_mics) * 2 * p.P)
     RTIS_ALLOC(p.d_a, static_cast<size_t>(n_mics) * n_samples)
@@ -561,6 +566,52 @@ void rtis_fd_gemm_destroy(rtis_fd_gemm* plan) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete plan;
+}
+
+rtis_status rtis_set_calibration(rtis_plan* plan, const float* d_mic_xyz, const float* d_gain, const float* d_delay_s,
+                                 void* stream) {
+    if (!plan) return fail(RTIS_ERR_INVALID_ARG, "rtis_set_calibration: NULL plan");
+    Plan& p = plan->p;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (d_mic_xyz) e = cudaMemcpyAsync(p.d_mic, d_mic_xyz, 3 * p.M * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && d_gain) e = cudaMemcpyAsync(p.d_gain, d_gain, p.M * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && d_delay_s)
+        e = cudaMemcpyAsync(p.d_delay, d_delay_s, p.M * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rtis_set_calibration: copy");
+    p.table_dirty = true;
+    return ensure_table(p, st);
+}
+
+rtis_status rtis_backward(rtis_plan* plan, const int16_t* d_in, const float* d_grad_out, float* d_grad_xyz,
+                          float* d_grad_gain, float* d_grad_delay, void* stream) {
+    if (!plan || !d_in || !d_grad_out) return fail(RTIS_ERR_INVALID_ARG, "rtis_backward: NULL argument");
+    if (!d_grad_xyz && !d_grad_gain && !d_grad_delay)
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_backward: no gradient requested");
+    if (!rtis::aligned(d_in, 8) || !rtis::aligned(d_grad_out, 4))
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_backward: misaligned pointer");
+    Plan& p = plan->p;
+    // every sample a tile owns must lie inside the window the tile beamforms
+    const int half = (p.lpf_len - 1) / 2;
+    const int n_tiles = (p.n_out + p.td_bins_per_tile - 1) / p.td_bins_per_tile;
+    const int last_start = p.R * (n_tiles - 1) * p.td_bins_per_tile - half;
+    if (p.R * p.td_bins_per_tile + half > rtis::kTdWarpSamples || p.N > last_start + rtis::kTdWarpSamples)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_backward: decimation too coarse for the beamformer tile");
+    if (rtis::adj_smem_bytes(p) > 227 * 1024) return fail(RTIS_ERR_UNSUPPORTED, "rtis_backward: halo too large");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rtis_status s = ensure_table(p, st);
+    if (s != RTIS_OK) return s;
+    cudaError_t e = rtis::launch_mf_forward(p, d_in, st);  // recompute the matched filter
+    if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, p.d_a, nullptr, st);
+    if (e == cudaSuccess) e = rtis::launch_td_adjoint(p, d_grad_out, d_grad_xyz, d_grad_gain, d_grad_delay, st);
+    return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_backward: launch");
+}
+
+rtis_status rtis_loss_l2(rtis_plan* plan, const float* d_E, const float* d_E_ref, float* d_grad_out, float* d_loss,
+                         void* stream) {
+    if (!plan || !d_E || !d_E_ref || !d_loss) return fail(RTIS_ERR_INVALID_ARG, "rtis_loss_l2: NULL argument");
+    cudaError_t e = rtis::launch_l2_loss(plan->p, d_E, d_E_ref, d_grad_out, d_loss, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_loss_l2: launch");
 }
 
 rtis_status rtis_plan_sync(rtis_plan* plan, unsigned* bits_out) {

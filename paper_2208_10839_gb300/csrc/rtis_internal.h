@@ -50,6 +50,9 @@ struct Plan {
     int* d_shift = nullptr;     // [D][M]
     float4* d_wt = nullptr;     // [D][M]
     float2* d_dphase = nullptr; // [D][M] delta / F (hi, lo)
+    float4* d_wraw = nullptr;   // [D][M] Catmull-Rom weights without the gain (adjoint)
+    float4* d_wder = nullptr;   // [D][M] their slopes d/dmu (adjoint)
+    float2* d_adj = nullptr;    // [range tiles][D][M] adjoint partials (d/d delta, d/d gain)
     // device workspaces (owned)
     float2* d_Z = nullptr;      // [M][2][P] half-size spectra
     float2* d_a = nullptr;      // [M][N] analytic matched-filter output
@@ -120,6 +123,11 @@ struct TdMaps {
 void td_fill_sensor(const Plan& p, float* d_out, int tile_base, TdSensor* s);
 int td_tiles(const Plan& p);
 cudaError_t td_autotune(Plan& p, float* d_scratch_out);
+cudaError_t launch_td_adjoint(const Plan& p, const float* d_grad_out, float* d_gxyz, float* d_ggain, float* d_gdelay,
+                              cudaStream_t st);
+cudaError_t launch_l2_loss(const Plan& p, const float* d_E, const float* d_Eref, float* d_G, float* d_loss,
+                           cudaStream_t st);
+size_t adj_smem_bytes(const Plan& p);
 cudaError_t launch_td_batch(const TdMaps& maps, const TdBatch& bt, int variant, int grid, cudaStream_t st);
 
 bool encode_tmap_2d_u64(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows,

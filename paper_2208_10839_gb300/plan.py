@@ -89,6 +89,24 @@ class Plan:
         nat.rtis_beamform_fd(self.handle, A, out, stream)
         return out
 
+    def set_calibration(self, mic_xyz=None, gain=None, delay_s=None, stream=None):
+        """Device float tensors [M][3], [M], [M] (seconds); None keeps the current value."""
+        t = self._torch
+        c = lambda v: None if v is None else v.detach().to(t.float32).contiguous()
+        mic_xyz, gain, delay_s = c(mic_xyz), c(gain), c(delay_s)
+        nat.rtis_set_calibration(self.handle, mic_xyz, gain, delay_s, stream)
+        self._keep = (mic_xyz, gain, delay_s)  # alive until the stream-ordered copies ran
+
+    def backward(self, x, grad_out, stream=None):
+        """dL/dE [D][n_out] -> (dL/dp [M][3], dL/dg [M], dL/dDelta [M]) for the time-domain path."""
+        t = self._torch
+        dev = x.device
+        gx = t.empty((self.M, 3), dtype=t.float32, device=dev)
+        gg = t.empty((self.M,), dtype=t.float32, device=dev)
+        gd = t.empty((self.M,), dtype=t.float32, device=dev)
+        nat.rtis_backward(self.handle, x, grad_out.contiguous(), gx, gg, gd, stream)
+        return gx, gg, gd
+
     def steering_table(self, stream=None):
         t = self._torch
         dev = self._dev()
@@ -190,3 +208,39 @@ def process_batch(plans, xs, outs=None, stream=None):
         outs = [torch.empty((p.D, p.n_out), dtype=torch.float32, device=x.device) for p, x in zip(plans, xs)]
     nat.rtis_process_batch([p.handle for p in plans], list(xs), list(outs), stream)
     return outs
+
+
+def _autograd_function():
+    import torch
+
+    class EnergyscapeFn(torch.autograd.Function):
+        """E = energyscape(x; p, g, Delta) with the hand-written adjoint (rtis_backward)."""
+
+        @staticmethod
+        def forward(ctx, plan, x, mic_xyz, gain, delay_s):
+            plan.set_calibration(mic_xyz, gain, delay_s)
+            E = plan.process(x)
+            ctx.plan = plan
+            ctx.save_for_backward(x, mic_xyz, gain, delay_s)
+            return E
+
+        @staticmethod
+        def backward(ctx, grad_E):
+            x, mic_xyz, gain, delay_s = ctx.saved_tensors
+            plan = ctx.plan
+            plan.set_calibration(mic_xyz, gain, delay_s)
+            gx, gg, gd = plan.backward(x, grad_E)
+            return None, None, gx.to(mic_xyz.dtype), gg.to(gain.dtype), gd.to(delay_s.dtype)
+
+    return EnergyscapeFn
+
+
+_FN = None
+
+
+def energyscape(plan, x, mic_xyz, gain, delay_s):
+    """Differentiable time-domain energyscape with respect to the array calibration."""
+    global _FN
+    if _FN is None:
+        _FN = _autograd_function()
+    return _FN.apply(plan, x, mic_xyz, gain, delay_s)
