@@ -1,5 +1,5 @@
 // Shared-memory FFT building blocks (device code) used by the matched filter
-// and the frequency-domain beamformer: an in-register radix-2/4/8/16 DFT and a
+// and the frequency-domain beamformer: an in-register radix-2 .. 32 DFT and a
 // mixed-radix Stockham autosort FFT over P = 2^LOGP points held in shared
 // memory (1-in-16 padded layout), twiddles from an F-point table
 // tw[j] = exp(-2 pi i j / F) computed in FP64.
@@ -17,39 +17,36 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
-// cos and sin of 2*pi*e/16 for e = 0..7 (folded to constants once unrolled)
-__device__ __forceinline__ float cos16(int e) {
+// cos and sin of 2*pi*e/32 for e = 0..15 (folded to constants once unrolled)
+__device__ __forceinline__ float cos32(int e) {
     switch (e) {
         case 0: return 1.0f;
-        case 1: return 0.92387953251128674f;
-        case 2: return 0.70710678118654752f;
-        case 3: return 0.38268343236508977f;
-        case 4: return 0.0f;
-        case 5: return -0.38268343236508977f;
-        case 6: return -0.70710678118654752f;
-        default: return -0.92387953251128674f;
+        case 1: return 0.98078528040323044913f;
+        case 2: return 0.92387953251128674f;
+        case 3: return 0.83146961230254523708f;
+        case 4: return 0.70710678118654752f;
+        case 5: return 0.55557023301960222474f;
+        case 6: return 0.38268343236508977f;
+        case 7: return 0.19509032201612826785f;
+        case 8: return 0.0f;
+        case 9: return -0.19509032201612826785f;
+        case 10: return -0.38268343236508977f;
+        case 11: return -0.55557023301960222474f;
+        case 12: return -0.70710678118654752f;
+        case 13: return -0.83146961230254523708f;
+        case 14: return -0.92387953251128674f;
+        default: return -0.98078528040323044913f;
     }
 }
-__device__ __forceinline__ float sin16(int e) {
-    switch (e) {
-        case 0: return 0.0f;
-        case 1: return 0.38268343236508977f;
-        case 2: return 0.70710678118654752f;
-        case 3: return 0.92387953251128674f;
-        case 4: return 1.0f;
-        case 5: return 0.92387953251128674f;
-        case 6: return 0.70710678118654752f;
-        default: return 0.38268343236508977f;
-    }
-}
+__device__ __forceinline__ float sin32(int e) { return e <= 8 ? cos32(8 - e) : cos32(e - 8); }
 
-// d * exp(-/+ 2 pi i e / 16)  (forward: minus; inverse: plus)
+// d * exp(-/+ 2 pi i e / 32)  (forward: minus; inverse: plus)
 template <bool INV>
-__device__ __forceinline__ float2 rot16(float2 d, int e) {
+__device__ __forceinline__ float2 rot32(float2 d, int e) {
     if (e == 0) return d;
-    if (e == 4) return INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
-    const float c = cos16(e);
-    const float s = INV ? sin16(e) : -sin16(e);
+    if (e == 8) return INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+    const float c = cos32(e);
+    const float s = INV ? sin32(e) : -sin32(e);
     return make_float2(d.x * c - d.y * s, d.x * s + d.y * c);
 }
 
@@ -63,7 +60,7 @@ __device__ __forceinline__ constexpr int bitrev(int k) {
     return r;
 }
 
-// In-register radix-R DFT (R = 2, 4, 8, 16): decimation-in-frequency
+// In-register radix-R DFT (R = 1, 2, 4, 8, 16, 32): decimation-in-frequency
 // butterflies, then a static bit-reversal reorder.
 template <int R, bool INV>
 __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
@@ -76,7 +73,7 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
             for (int i = 0; i < half; ++i) {
                 const float2 a = v[s + i], b = v[s + i + half];
                 v[s + i] = make_float2(a.x + b.x, a.y + b.y);
-                v[s + i + half] = rot16<INV>(make_float2(a.x - b.x, a.y - b.y), i * (16 / len));
+                v[s + i + half] = rot32<INV>(make_float2(a.x - b.x, a.y - b.y), i * (32 / len));
             }
         }
     }

@@ -79,28 +79,33 @@ __device__ __forceinline__ void adj_fwd_mic(uint64_t (&acc)[kTdOutPerThread], co
     }
 }
 
-// reverse: C_q = sum_t Re(conj(G_b[t]) a[t + q]), q = 0..3 (taps j-1 .. j+2)
+// reverse: C_q = sum_t Re(conj(G_b[t]) a[t + q]), q = 0..3 (taps j-1 .. j+2).
+// (re, im) pairs multiply lane-wise with packed FMAs; the two halves are added
+// at the end.  Even and odd t accumulate separately for more independent chains.
 template <bool ODD>
 __device__ __forceinline__ float4 adj_corr_mic(const uint64_t (&gb)[kTdOutPerThread], const ulonglong2* __restrict__ p) {
     constexpr int T = kTdOutPerThread;
     constexpr int NP = (T + 4) / 2;
-    float2 v[2 * NP];
+    uint64_t v[2 * NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const ulonglong2 q = p[k];
-        v[2 * k] = unpack2a(q.x);
-        v[2 * k + 1] = unpack2a(q.y);
+        v[2 * k] = q.x;
+        v[2 * k + 1] = q.y;
     }
-    float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+    uint64_t c[4][2] = {{0ull, 0ull}, {0ull, 0ull}, {0ull, 0ull}, {0ull, 0ull}};
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        const float2 g = unpack2a(gb[t]);
-        c0 = fmaf(g.x, v[t + ODD].x, fmaf(g.y, v[t + ODD].y, c0));
-        c1 = fmaf(g.x, v[t + 1 + ODD].x, fmaf(g.y, v[t + 1 + ODD].y, c1));
-        c2 = fmaf(g.x, v[t + 2 + ODD].x, fmaf(g.y, v[t + 2 + ODD].y, c2));
-        c3 = fmaf(g.x, v[t + 3 + ODD].x, fmaf(g.y, v[t + 3 + ODD].y, c3));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fma2a(c[q][t & 1], gb[t], v[t + q + ODD]);
     }
-    return make_float4(c0, c1, c2, c3);
+    float r[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 e = unpack2a(c[q][0]), o = unpack2a(c[q][1]);
+        r[q] = (e.x + e.y) + (o.x + o.y);
+    }
+    return make_float4(r[0], r[1], r[2], r[3]);
 }
 
 __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)

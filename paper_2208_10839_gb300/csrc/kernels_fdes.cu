@@ -12,9 +12,13 @@
 // complex multiply by exp(2 pi i 256 delta/F) per bin.  b_d: with n = 4p + q
 // the band (below F/4) needs four P = F/4 point inverse FFTs of
 // B_d[k_lo + k'] w_F^{k' q}; the remaining factor w_F^{k_lo n} has unit
-// modulus and drops out of |b_d|.  After each phase the low-pass taps that
-// fall on n = q (mod 4) are added to the outputs each thread owns, so the
-// envelope never needs storing.  Twiddles come from two small shared tables
+// modulus and drops out of |b_d|.  Each phase IFFT is three Stockham passes
+// of radix P/256, 16, 16 (256 threads, one butterfly or two per thread per
+// pass): the first pass reads the steered spectrum and applies the phase's
+// pre-twiddle in registers (skipping the zero bins above the band), the last
+// writes |b| as floats, only for the samples n < N.  After each phase the
+// low-pass taps that fall on n = q (mod 4) are added to the outputs each
+// thread owns.  Twiddles come from two small shared tables
 // (w^j = hi[j >> 8] lo[j & 255]) instead of the F-point table.
 #include "fft.cuh"
 #include "rtis_internal.h"
@@ -49,11 +53,13 @@ struct FdesSmem {
     int fbuf, B, twhi, twlo, Eacc, hs, step, gs, bytes;
 };
 
+__host__ __device__ constexpr int fpad(int i) { return i + (i >> 5); }  // 1-in-32 bank skew
+
 __host__ __device__ inline FdesSmem fdes_layout(int P, int F, int Kb, int n_out, int lpf_len, int M) {
     FdesSmem L;
     int o = 0;
     L.fbuf = o;
-    o += (spad(P - 1) + 1) * 8;
+    o += (fpad(P - 1) + 1) * 8;
     L.B = o;
     o += Kb * 8;
     L.twhi = o;
@@ -70,6 +76,65 @@ __host__ __device__ inline FdesSmem fdes_layout(int P, int F, int Kb, int n_out,
     o += M * 4;
     L.bytes = o;
     return L;
+}
+
+// One inverse radix-16 Stockham pass over P points (padded layout fpad),
+// Ns = product of the earlier radices.  The last pass (Ns = P/16) writes
+// env[p] = |b(4p + q)| for p < p_need instead of the complex values.
+template <int LOGP, int NS, bool LAST>
+__device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const SplitTwiddles& tws, int F, int p_need) {
+    constexpr int P = 1 << LOGP;
+    constexpr int NB = P / 16;
+    constexpr int BPT = (NB + kFdesThreads - 1) / kFdesThreads;
+    static_assert(!LAST || NS == NB, "the last pass has Ns = P/16");
+    const int tw_scale = F / (NS * 16);
+    float2 v[BPT][16];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = threadIdx.x + b * kFdesThreads;
+        if (NB % kFdesThreads == 0 || j < NB) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[b][r] = buf[fpad(j + r * NB)];
+        }
+    }
+    __syncthreads();
+    // w^r = w^(r - lowbit) w^lowbit from the table values w^1, w^2, w^4, w^8;
+    // when Ns divides the thread count every butterfly of a thread has the same k
+    constexpr bool SHARED_K = (NS <= kFdesThreads);
+    float2 w[16];
+    auto twiddles = [&](int k) {
+#pragma unroll
+        for (int r = 1; r < 16; r <<= 1) w[r] = conjf2(tws(r * k * tw_scale));
+#pragma unroll
+        for (int r = 3; r < 16; ++r)
+            if (r & (r - 1)) w[r] = cmul(w[r & (r - 1)], w[r & -r]);
+    };
+    if (SHARED_K && NS > 1) twiddles(threadIdx.x & (NS - 1));
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = threadIdx.x + b * kFdesThreads;
+        if (NB % kFdesThreads == 0 || j < NB) {
+            const int k = j & (NS - 1);
+            if (NS > 1) {
+                if (!SHARED_K) twiddles(k);
+#pragma unroll
+                for (int r = 1; r < 16; ++r) v[b][r] = cmul(v[b][r], w[r]);
+            }
+            dft_reg<16, true>(v[b]);
+            if constexpr (!LAST) {
+                const int base = (j - k) * 16 + k;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) buf[fpad(base + r * NS)] = v[b][r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const int p = k + r * NS;
+                    if (p < p_need) env[p] = sqrtf(v[b][r].x * v[b][r].x + v[b][r].y * v[b][r].y);
+                }
+            }
+        }
+    }
+    __syncthreads();
 }
 
 template <int LOGP>
@@ -139,32 +204,39 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
     __syncthreads();
 
     // ---- four phase IFFTs, each folded into the low-pass outputs ------------
+    constexpr int R0 = P / kFdesThreads;  // first-pass radix, 1 .. 32
+    static_assert(R0 >= 1 && R0 <= 32, "P = 256 .. 8192");
+    float* env = reinterpret_cast<float*>(fbuf);  // |b(4p + q)|, written by the last pass
     const int half = (a.lpf_len - 1) >> 1;
+    const int p_need = (a.N + 3) >> 2;  // samples n = 4p + q < N
     const unsigned fmask = static_cast<unsigned>(a.F - 1);
     for (int q = 0; q < 4; ++q) {
-        for (int kp = tid; kp < P; kp += kFdesThreads) {
-            float2 g = make_float2(0.f, 0.f);
-            if (kp < Kb) {
-                const float2 v = B[kp];
-                g = (q == 0) ? v : cmul(v, conjf2(tws(static_cast<int>((static_cast<unsigned>(kp) * q) & fmask))));
+        {  // first pass (radix R0, Ns = 1): bins k' = t + 256 r, pre-twiddled by w_F^{-k' q}
+            float2 v[R0];
+#pragma unroll
+            for (int r = 0; r < R0; ++r) {
+                const int kp = tid + r * kFdesThreads;
+                float2 g = make_float2(0.f, 0.f);
+                if (kp < Kb) {
+                    const float2 x = B[kp];
+                    g = (q == 0) ? x : cmul(x, conjf2(tws(static_cast<int>((static_cast<unsigned>(kp) * q) & fmask))));
+                }
+                v[r] = g;
             }
-            fbuf[spad(kp)] = g;
+            dft_reg<R0, true>(v);
+#pragma unroll
+            for (int r = 0; r < R0; ++r) fbuf[fpad(tid * R0 + r)] = v[r];
         }
         __syncthreads();
-        fft_smem<LOGP, true, kFdesThreads>(fbuf, tws, a.F);
-        // envelope of this phase, in place: fbuf[p].x = |b(4p + q)|
-        for (int p = tid; p < P; p += kFdesThreads) {
-            const float2 v = fbuf[spad(p)];
-            fbuf[spad(p)].x = sqrtf(v.x * v.x + v.y * v.y);
-        }
-        __syncthreads();
+        fdes_pass16<LOGP, R0, false>(fbuf, env, tws, a.F, p_need);
+        fdes_pass16<LOGP, 16 * R0, true>(fbuf, env, tws, a.F, p_need);
         for (int i = tid; i < a.n_out; i += kFdesThreads) {
             const int n0 = a.R * i - half;          // n = n0 + j
             const int j0 = ((q - n0) % 4 + 4) & 3;  // first tap with n = q (mod 4)
             float s = 0.f;
             for (int j = j0; j < a.lpf_len; j += 4) {
                 const int n = n0 + j;
-                if (n >= 0 && n < a.N) s = fmaf(hs[j], fbuf[spad((n - q) >> 2)].x, s);
+                if (n >= 0 && n < a.N) s = fmaf(hs[j], env[(n - q) >> 2], s);
             }
             Eacc[i] += s;
         }
@@ -203,14 +275,12 @@ cudaError_t fdes_launch_t(const Plan& p, const float2* d_A, float* d_out, cudaSt
 }  // namespace
 
 size_t fdes_smem_bytes(const Plan& p) {
-    if (p.logP < 6 || p.logP > 13) return ~static_cast<size_t>(0);
+    if (p.logP < 8 || p.logP > 13) return ~static_cast<size_t>(0);
     return static_cast<size_t>(fdes_layout(p.P, p.F, p.Kb, p.n_out, p.lpf_len, p.M).bytes);
 }
 
 cudaError_t launch_fd_energyscape(const Plan& p, const float2* d_A, float* d_out, cudaStream_t st) {
     switch (p.logP) {
-        case 6: return fdes_launch_t<6>(p, d_A, d_out, st);
-        case 7: return fdes_launch_t<7>(p, d_A, d_out, st);
         case 8: return fdes_launch_t<8>(p, d_A, d_out, st);
         case 9: return fdes_launch_t<9>(p, d_A, d_out, st);
         case 10: return fdes_launch_t<10>(p, d_A, d_out, st);
