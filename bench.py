@@ -6,12 +6,13 @@ on one GPU: matched filter -> delay-and-sum over 2048 Fibonacci half-sphere
 directions in both forms (time domain with Catmull-Rom fractional delays,
 and frequency domain with exact phase ramps) -> envelope, low-pass,
 subsample -> two energyscapes 2048 x 1638 (FP32).  The input sits in HBM when the clock starts; L2 is
-flushed (a 512 MiB write) between steps, outside the timed events.
+flushed (a 512 MiB write, then a 256 MiB read so that its write-backs end) between steps, outside the
+timed events.
 
 Printed (rank 0, one JSON line): value = energyscapes/s over all ranks,
 e2e = the same through rtis_process with pinned host buffers (H2D input and
 D2H energyscape inside the timed region), roofline of the dominant kernel
-(the beamformer, FP32-FMA bound), the FP64 oracle timed on the host as
+(whichever beamformer takes longer; both are FP32-FMA bound), the FP64 oracle timed on the host as
 cpu_baseline, and SM clocks sampled during the timed region.
 
 --impl reference times the FP64 oracle itself (on a bounded sample of
@@ -40,9 +41,10 @@ WORKLOAD = "hemisphere: 32 mics (12 cm square, seeded), 16384 samples @ 450 kHz,
            "20 reflectors 0.3-6 m, 20 dB SNR, int16; matched filter + time-domain and frequency-domain DAS, FP32"
 FP32_LANES_PER_SM = 128     # FP32 FMA lanes per SM (4 SMSPs x 32)
 SM_MAX_MHZ_NOMINAL = 2070.0
-# dram__bytes_read.sum + dram__bytes_write.sum of one td_beamform_kernel launch (ncu capture of this
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of each beamformer (ncu capture of this
 # workload, see profiles/); set to None whenever that kernel changes until it is re-captured
-TD_TRAFFIC_BYTES = 5543168
+TD_TRAFFIC_BYTES = 5539584
+FD_TRAFFIC_BYTES = 1736704
 
 
 def dist_env():
@@ -112,6 +114,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class L2Flush:
+    """Between timed steps: write 512 MiB (evicts everything the last step left in
+    the 129 MB L2), then read 256 MiB more, so the dirty lines of that write are
+    written back before the next step's clock starts rather than during it."""
+
+    def __init__(self, dev):
+        import torch
+        self.w = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        self.r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        self.sink = None
+
+    def __call__(self, v=0.0):
+        self.w.fill_(float(v))
+        self.sink = self.r.sum()
+
+
 def oracle_sample_time(cfg, n_dirs_sample: int, seed: int = 0):
     """Seconds the FP64 oracle needs for one step (both energyscapes), from a direction sample."""
     import oracle
@@ -172,10 +190,10 @@ def run_fd_gemm(args, rank, world, local):
     g = FdGemm(cfg["mic_xyz"], cfg["dirs"], cfg["freqs"], T, precision=args.precision)
     X = torch.from_numpy(cfg["X"].astype(np.complex64)).to(dev)
     Y = torch.empty((K, D, T), dtype=torch.complex64, device=dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
-        flush.fill_(1.0)
+        flush(1.0)
         g.run(X, Y)
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -184,7 +202,7 @@ def run_fd_gemm(args, rank, world, local):
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
-            flush.fill_(float(k))
+            flush(float(k))
             evs[k][0].record(stream)
             g.run(X, Y)
             evs[k][1].record(stream)
@@ -211,7 +229,7 @@ def run_fd_gemm(args, rank, world, local):
         "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": cfg["name"], "precision": args.precision, "l2": "flushed between steps"},
+        "config": {"workload": cfg["name"], "precision": args.precision, "l2": "flushed between steps (512 MiB write, then a 256 MiB read so write-backs finish), outside the timed events"},
         "error_vs_fp64_oracle": {"max_abs_over_max": err, "bins_checked": picks},
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "hbm", "kernel": "fd_gemm_kernel", "achieved": bytes_alg / launch_s / 1e9,
@@ -240,11 +258,11 @@ def run_ring(args, rank, world, local):
     plans = [Plan(s["mic_xyz"], s["fs"], s["chirp"], s["dirs"], s["n_samples"]) for s in sensors]
     xs = [torch.from_numpy(s["x"]).to(dev) for s in sensors]
     outs = [torch.empty((p.D, p.n_out), dtype=torch.float32, device=dev) for p in plans]
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
     batch = Batch(plans)
     for _ in range(args.warmup):  # the first run autotunes
-        flush.fill_(1.0)
+        flush(1.0)
         batch.run(xs, outs)
     torch.cuda.synchronize()
     assert batch.sync() == 0
@@ -254,7 +272,7 @@ def run_ring(args, rank, world, local):
         dist.barrier()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
-            flush.fill_(float(k))
+            flush(float(k))
             evs[k][0].record(stream)
             batch.run(xs, outs)
             evs[k][1].record(stream)
@@ -263,7 +281,7 @@ def run_ring(args, rank, world, local):
     # the same sensors one rtis_process at a time, for comparison
     seq = []
     for k in range(max(3, args.steps // 4)):
-        flush.fill_(float(k))
+        flush(float(k))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for p, x, o in zip(plans, xs, outs):
@@ -282,7 +300,7 @@ def run_ring(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": ring["name"], "sensors": [(s["n_samples"], int(s["dirs"].shape[0])) for s in sensors],
-                   "l2": "flushed between steps"},
+                   "l2": "flushed between steps (512 MiB write, then a 256 MiB read so write-backs finish), outside the timed events"},
         "autotune": {"variant": info.variant, "grid": info.grid, "tiles": info.total_tiles,
                      "beamformer_ms": info.tuned_ms},
         "sequential_rtis_process_ms": statistics.mean(seq),
@@ -326,7 +344,7 @@ def run_calibration(args, rank, world, local):
     gx = torch.empty((M, 3), dtype=torch.float32, device=dev)
     gg = torch.empty(M, dtype=torch.float32, device=dev)
     gd = torch.empty(M, dtype=torch.float32, device=dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
 
     def step(xin, ev=None):
         if ev:
@@ -341,7 +359,7 @@ def run_calibration(args, rank, world, local):
             ev[2].record(stream)
 
     for _ in range(args.warmup):
-        flush.fill_(1.0)
+        flush(1.0)
         step(x)
     torch.cuda.synchronize()
     assert plan.sync() == 0
@@ -351,7 +369,7 @@ def run_calibration(args, rank, world, local):
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
-            flush.fill_(float(k))
+            flush(float(k))
             step(x, evs[k])
         torch.cuda.synchronize()
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
@@ -362,7 +380,7 @@ def run_calibration(args, rank, world, local):
     a_buf = torch.empty((M, N), dtype=torch.complex64, device=dev)
     mf = []
     for k in range(max(3, args.steps // 4)):
-        flush.fill_(float(k))
+        flush(float(k))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         nat.rtis_matched_filter(h, x, a_buf, None, sh)
@@ -411,7 +429,7 @@ def run_calibration(args, rank, world, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "calibration: 32 mics perturbed by N(0, 1 mm), gains U(0.8, 1.2), delays "
                                "U(-2, 2) us; 16384 samples, 2048 Fibonacci half-sphere dirs, 10 known reflectors",
-                   "l2": "flushed (512 MiB write) between steps, outside the timed events"},
+                   "l2": "flushed between steps (512 MiB write, then a 256 MiB read so write-backs finish), outside the timed events"},
         "e2e": {"value": world * n_e2e / t_e2e, "unit": "gradients/s", "h2d_bytes_per_step": int(x.numel() * 2),
                 "d2h_bytes_per_step": int(4 * (gx.numel() + gg.numel() + gd.numel() + 1))},
         "gpu_launches": 10 * args.steps,
@@ -492,7 +510,7 @@ def main():
     A = torch.empty((N_MICS, plan.Kb), dtype=torch.complex64, device=dev)
     E_td = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32, device=dev)
     E_fd = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32, device=dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     h = plan.handle
@@ -513,7 +531,7 @@ def main():
             ev[3].record(stream)
 
     for _ in range(args.warmup):
-        flush.fill_(1.0)
+        flush(1.0)
         step()
     torch.cuda.synchronize()
     assert plan.sync() == 0
@@ -524,7 +542,7 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
-            flush.fill_(float(k))
+            flush(float(k))
             step(evs[k])
         torch.cuda.synchronize()
     if world > 1:
@@ -573,20 +591,33 @@ def main():
     e2e_value = world * e2e_steps / t_e2e
     clocks = clk.summary()
 
-    # roofline of the dominant kernel: the time-domain beamformer on the FP32 FMA pipe
-    # (D*N*M*4 taps*2 (re, im) FMAs, 2 flops each)
+    # rooflines of the two beamformers, both bound by the FP32 ALU (FMA pipe); the
+    # JSON's "roofline" is the one that takes longer per step (the dominant kernel)
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
-    flops = float(N_DIRS) * N_SAMPLES * N_MICS * 4 * 2 * 2
-    td_s = statistics.mean(td_ms) / 1e3
-    achieved = flops / td_s / 1e12
     peak_tf = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": "td_beamform_kernel", "achieved": achieved, "peak": peak_tf,
-                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": TD_TRAFFIC_BYTES,
-                "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {SM_MAX_MHZ_NOMINAL:.0f} MHz",
-                "algorithmic_flops_per_launch": flops, "launch_ms": td_s * 1e3}
-    if clocks.get("sm_mhz"):
-        roofline["frac_at_observed_clock"] = achieved / (n_sm * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+    basis = f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {SM_MAX_MHZ_NOMINAL:.0f} MHz"
+    td_s = statistics.mean(td_ms) / 1e3
+    fd_s = statistics.mean(fd_ms) / 1e3
+    P = plan.info.fft_len // 4
+    lpf_len = 4 * 10 + 1
+    td_flops = float(N_DIRS) * N_SAMPLES * N_MICS * 4 * 2 * 2  # 4 taps x (re, im) FMAs per (d, n, m)
+    fd_flops = float(N_DIRS) * (8.0 * plan.Kb * N_MICS                   # steered spectrum: complex MACs
+                                + 4 * 5.0 * P * np.log2(P)                # four P-point inverse FFTs
+                                + 3 * 6.0 * plan.Kb                        # phase pre-twiddles (q = 1..3)
+                                + 3.0 * N_SAMPLES                          # envelope |b|
+                                + 2.0 * lpf_len * plan.n_out)              # low-pass at the output bins
+    rl = {}
+    for name, kern, flops, secs, traffic in (("td", "td_beamform_kernel", td_flops, td_s, TD_TRAFFIC_BYTES),
+                                             ("fd", "fd_energyscape_kernel", fd_flops, fd_s, FD_TRAFFIC_BYTES)):
+        ach = flops / secs / 1e12
+        rl[name] = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": ach / peak_tf, "traffic": traffic, "peak_basis": basis,
+                    "algorithmic_flops_per_launch": flops, "launch_ms": secs * 1e3}
+        if clocks.get("sm_mhz"):
+            rl[name]["frac_at_observed_clock"] = ach / (n_sm * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+    dominant = "fd" if fd_s > td_s else "td"
+    roofline = rl[dominant]
 
     line = {
         "metric": METRIC, "value": value, "unit": "energyscapes/s", "n_gpus": world, "steps": args.steps,
@@ -596,7 +627,7 @@ def main():
                    "n_out": plan.n_out, "decim": 10, "batch_per_step": 1,
                    "paths_per_step": "time-domain (Catmull-Rom) and frequency-domain (phase ramp) energyscapes "
                                      "of the same measurement; value counts measurements",
-                   "l2": "flushed (512 MiB write) between steps, outside the timed events",
+                   "l2": "flushed between steps (512 MiB write, then a 256 MiB read so write-backs finish), outside the timed events",
                    "parallelism": f"{world} independent replica(s), one measurement per rank per step"},
         "e2e": {"value": e2e_value, "unit": "energyscapes/s", "h2d_bytes_per_step": int(x.numel() * 2),
                 "d2h_bytes_per_step": int(E_td.numel() * 4 + E_fd.numel() * 4),
@@ -607,6 +638,7 @@ def main():
         "path_rates": {"td_only_energyscapes_per_s": 1e3 / (statistics.mean(mf_ms) + statistics.mean(td_ms)),
                        "fd_only_energyscapes_per_s": 1e3 / (statistics.mean(mf_ms) + statistics.mean(fd_ms))},
         "roofline": roofline,
+        "roofline_other": rl["td" if dominant == "fd" else "fd"],
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
