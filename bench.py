@@ -255,7 +255,10 @@ def run_ring(args, rank, world, local):
     dev = torch.device("cuda", local)
     ring = synth.ring_sensors(seed_scene=3 + 1000 * rank)
     sensors = ring["sensors"]
-    plans = [Plan(s["mic_xyz"], s["fs"], s["chirp"], s["dirs"], s["n_samples"]) for s in sensors]
+    if args.precision not in ("fp32", "bf16"):
+        raise SystemExit("ring: --precision fp32 or bf16 (storage of the analytic signal)")
+    plans = [Plan(s["mic_xyz"], s["fs"], s["chirp"], s["dirs"], s["n_samples"], precision=args.precision)
+             for s in sensors]
     xs = [torch.from_numpy(s["x"]).to(dev) for s in sensors]
     outs = [torch.empty((p.D, p.n_out), dtype=torch.float32, device=dev) for p in plans]
     flush = L2Flush(dev)
@@ -298,8 +301,9 @@ def run_ring(args, rank, world, local):
         "metric": "energyscapes/s (ring of 8 sensors, ragged N and D, one batch per step)",
         "value": world * args.steps * n_s / t, "unit": "energyscapes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": ring["name"], "sensors": [(s["n_samples"], int(s["dirs"].shape[0])) for s in sensors],
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16 storage, f32 arithmetic",
+        "data": "synthetic",
+        "config": {"workload": ring["name"], "storage": args.precision, "sensors": [(s["n_samples"], int(s["dirs"].shape[0])) for s in sensors],
                    "l2": "flushed between steps (512 MiB write, then a 256 MiB read so write-backs finish), outside the timed events"},
         "autotune": {"variant": info.variant, "grid": info.grid, "tiles": info.total_tiles,
                      "beamformer_ms": info.tuned_ms},

@@ -77,7 +77,10 @@ typedef struct rtis_options {
     double band_lo_hz;           /* matched-filter band (default 20e3) */
     double band_hi_hz;           /* (default 80e3) */
     int path;                    /* RTIS_PATH_TD (default) or RTIS_PATH_FD */
-    int precision;               /* FD path operand type (RTIS_PREC_*) */
+    int precision;               /* storage of the analytic signal a on the TD path:
+                                    RTIS_PREC_FP32 (default) or RTIS_PREC_BF16 (a rounded
+                                    to BF16 pairs, half the staged bytes; products and sums
+                                    stay FP32).  The FD path takes FP32 only. */
     double max_delay_s;          /* bound on |Delta_m| set by calibration (default 10e-6) */
     double position_slack_m;     /* bound on calibrated mic displacement (default 0.01) */
 } rtis_options;
@@ -127,7 +130,9 @@ rtis_status rtis_plan_get_info(const rtis_plan* plan, rtis_plan_info* info);
 /*
  * rtis_process -- whole chain for one recording (Fig. 3): matched filter,
  * delay-and-sum on the plan's path (TD or FD), envelope, low-pass, subsample.
- * The FD path (opt.path = RTIS_PATH_FD) needs F <= 32768.
+ * The FD path (opt.path = RTIS_PATH_FD) needs F <= 32768.  With
+ * opt.precision = RTIS_PREC_BF16 the TD path beamforms from a BF16 copy of a
+ * (relative error ~2^-9 per sample; energyscape within 1e-2 of the peak).
  *   d_in   device int16 [n_mics][n_samples], 8-byte aligned
  *   d_out  device float [n_dirs][n_out]
  */
@@ -146,7 +151,8 @@ rtis_status rtis_matched_filter(rtis_plan* plan, const int16_t* d_in, float* d_a
 
 /*
  * rtis_beamform_td -- time-domain delay-and-sum with the fused envelope,
- * low-pass and subsampling epilogue, from a matched-filter output.
+ * low-pass and subsampling epilogue, from a matched-filter output (always
+ * complex float, whatever opt.precision).
  *   d_a    device complex float [n_mics][n_samples], 16-byte aligned
  *   d_out  device float [n_dirs][n_out]
  */

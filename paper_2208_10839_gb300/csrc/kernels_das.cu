@@ -133,6 +133,39 @@ __device__ __forceinline__ void td_mic(uint64_t (&acc)[kTdOutPerThread], const u
     }
 }
 
+// The same with BF16 (re, im) pairs staged, 4 bytes per sample: `p` points at
+// the 8-byte aligned pair of samples holding the first tap (or the sample
+// before it when ODD); each sample widens to FP32 exactly (BF16 is the top
+// half of an FP32) before the packed FMAs.
+__device__ __forceinline__ uint64_t widen_bf16x2(uint32_t u) {
+    return pack2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+template <bool ODD>
+__device__ __forceinline__ void td_mic_bf16(uint64_t (&acc)[kTdOutPerThread], const uint2* __restrict__ p,
+                                            uint64_t w0, uint64_t w1, uint64_t w2, uint64_t w3) {
+    constexpr int T = kTdOutPerThread;
+    constexpr int NP = (T + 4) / 2;
+    uint64_t v[2 * NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const uint2 q = p[k];
+        v[2 * k] = widen_bf16x2(q.x);
+        v[2 * k + 1] = widen_bf16x2(q.y);
+    }
+    constexpr int TB = 6;
+#pragma unroll
+    for (int tb = 0; tb < T; tb += TB) {
+#pragma unroll
+        for (int t = tb; t < tb + TB; ++t) fma2(acc[t], w0, v[t + ODD]);
+#pragma unroll
+        for (int t = tb; t < tb + TB; ++t) fma2(acc[t], w1, v[t + 1 + ODD]);
+#pragma unroll
+        for (int t = tb; t < tb + TB; ++t) fma2(acc[t], w2, v[t + 2 + ODD]);
+#pragma unroll
+        for (int t = tb; t < tb + TB; ++t) fma2(acc[t], w3, v[t + 3 + ODD]);
+    }
+}
+
 // Persistent over a flat list of tiles that may span several sensors (each
 // with its own geometry, record length and direction set).  Tile t of sensor
 // s covers 8 directions (direction group t % n_dgroups) x one range tile.
@@ -141,13 +174,14 @@ __device__ __forceinline__ void td_mic(uint64_t (&acc)[kTdOutPerThread], const u
 // issues the TMA refill.  Barrier phases run on across tiles.  Waits are
 // bounded; a timeout sets the status word, stops the CTA's compute, and the
 // CTA drains its copies before exit.
-template <int MS, int NS>
+template <int MS, int NS, bool BF>
 __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
     td_beamform_kernel(const __grid_constant__ TdMaps maps, const __grid_constant__ TdBatch bt) {
     constexpr int NT = 32 * kTdDirsPerCta;
     constexpr int T = kTdOutPerThread;
+    constexpr int ES = BF ? 4 : 8;  // bytes per staged sample
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float2* stage = reinterpret_cast<float2*>(smem_raw);
+    unsigned char* stage = smem_raw;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + static_cast<size_t>(NS) * MS * bt.row_max * 8);
     int* done = reinterpret_cast<int*>(bar + NS);
     int* issued = done + NS;
@@ -177,19 +211,21 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
         const int i0 = (local / S.n_dgroups) * S.bins_per_tile;
         const int half = (S.lpf_len - 1) >> 1;
         const int n_start = S.R * i0 - half;
-        const int x0 = (n_start - S.H) & ~1;  // even: 16-byte aligned TMA x coordinate
+        // TMA x coordinate: x0 * ES a multiple of 16 bytes
+        const int x0 = BF ? ((n_start - S.H) & ~3) : ((n_start - S.H) & ~1);
         const int M = S.M, row = S.row;
         const int nstages = (M + MS - 1) / MS;
-        const uint32_t stage_bytes = static_cast<uint32_t>(MS * S.nbox * kTdBox * 8);
+        const uint32_t stage_bytes = static_cast<uint32_t>(MS * S.nbox * kTdBox * ES);
 
         auto issue = [&](int st) {
             const int b = (g0 + st) % NS;
             issued[b] += 1;
             ptx::mbar_arrive_expect_tx(&bar[b], stage_bytes);
             for (int mi = 0; mi < MS; ++mi) {
-                float2* dst = stage + static_cast<size_t>(b * MS + mi) * row;
+                unsigned char* dst = stage + static_cast<size_t>(b * MS + mi) * row * ES;
                 for (int bx = 0; bx < S.nbox; ++bx)
-                    ptx::tma_load_2d(dst + bx * kTdBox, tmap, x0 + bx * kTdBox, st * MS + mi, &bar[b]);
+                    ptx::tma_load_2d(dst + static_cast<size_t>(bx) * kTdBox * ES, tmap, x0 + bx * kTdBox,
+                                     st * MS + mi, &bar[b]);
             }
         };
 
@@ -234,12 +270,20 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
                     const float f2 = __shfl_sync(0xffffffffu, my_w.z, m);
                     const float f3 = __shfl_sync(0xffffffffu, my_w.w, m);
                     const int s0 = lane_base + J;  // parity is warp-uniform (T even)
-                    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
-                        stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
-                    if (s0 & 1)
-                        td_mic<true>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
-                    else
-                        td_mic<false>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+                    const unsigned char* rowp = stage + (static_cast<size_t>(b * MS + mi) * row + (s0 & ~1)) * ES;
+                    if constexpr (BF) {
+                        const uint2* p = reinterpret_cast<const uint2*>(rowp);
+                        if (s0 & 1)
+                            td_mic_bf16<true>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+                        else
+                            td_mic_bf16<false>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+                    } else {
+                        const ulonglong2* p = reinterpret_cast<const ulonglong2*>(rowp);
+                        if (s0 & 1)
+                            td_mic<true>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+                        else
+                            td_mic<false>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+                    }
                 }
             }
             // release buffer b; the CTA's last warp to get here refills it
@@ -316,13 +360,13 @@ size_t td_smem_bytes(int row_max, int lpf_max) {
 size_t td_smem_bytes(const Plan& p) { return td_smem_bytes(p.td_row, p.lpf_len); }
 
 namespace {
-template <int MS, int NS>
+template <int MS, int NS, bool BF>
 cudaError_t td_launch_t(const TdMaps& maps, const TdBatch& bt, int grid, size_t smem, cudaStream_t st) {
     static_assert(MS * NS == kTdMicsPerStage * kTdStages, "variants share one shared-memory size");
-    cudaError_t e = cudaFuncSetAttribute(td_beamform_kernel<MS, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = cudaFuncSetAttribute(td_beamform_kernel<MS, NS, BF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    td_beamform_kernel<MS, NS><<<grid, 32 * kTdDirsPerCta, smem, st>>>(maps, bt);
+    td_beamform_kernel<MS, NS, BF><<<grid, 32 * kTdDirsPerCta, smem, st>>>(maps, bt);
     return cudaGetLastError();
 }
 }  // namespace
@@ -352,10 +396,18 @@ int td_tiles(const Plan& p) {
 
 cudaError_t launch_td_batch(const TdMaps& maps, const TdBatch& bt, int variant, int grid, cudaStream_t st) {
     const size_t smem = td_smem_bytes(bt.row_max, bt.lpf_max);
+    if (bt.bf16) {
+        switch (variant) {
+            case 0: return td_launch_t<2, 4, true>(maps, bt, grid, smem, st);
+            case 1: return td_launch_t<4, 2, true>(maps, bt, grid, smem, st);
+            case 2: return td_launch_t<1, 8, true>(maps, bt, grid, smem, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (variant) {
-        case 0: return td_launch_t<2, 4>(maps, bt, grid, smem, st);
-        case 1: return td_launch_t<4, 2>(maps, bt, grid, smem, st);
-        case 2: return td_launch_t<1, 8>(maps, bt, grid, smem, st);
+        case 0: return td_launch_t<2, 4, false>(maps, bt, grid, smem, st);
+        case 1: return td_launch_t<4, 2, false>(maps, bt, grid, smem, st);
+        case 2: return td_launch_t<1, 8, false>(maps, bt, grid, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -365,9 +417,10 @@ cudaError_t launch_td_batch(const TdMaps& maps, const TdBatch& bt, int variant, 
 // and keeps the fastest.
 cudaError_t td_autotune(Plan& p, float* d_scratch_out) {
     TdMaps maps;
-    maps.m[0] = p.tmap_a;
+    maps.m[0] = p.a_bf16 ? p.tmap_a16 : p.tmap_a;
     TdBatch bt;
     std::memset(&bt, 0, sizeof(bt));
+    bt.bf16 = p.a_bf16 ? 1 : 0;
     td_fill_sensor(p, d_scratch_out, 0, &bt.s[0]);
     bt.n_sensors = 1;
     bt.total_tiles = td_tiles(p);
@@ -409,11 +462,12 @@ cudaError_t td_autotune(Plan& p, float* d_scratch_out) {
     return e;
 }
 
-cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, float* d_out, cudaStream_t st) {
+cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, bool bf16, float* d_out, cudaStream_t st) {
     TdMaps maps;
     maps.m[0] = tmap;
     TdBatch bt;
     std::memset(&bt, 0, sizeof(bt));
+    bt.bf16 = bf16 ? 1 : 0;
     td_fill_sensor(p, d_out, 0, &bt.s[0]);
     bt.n_sensors = 1;
     bt.total_tiles = td_tiles(p);

@@ -14,6 +14,8 @@
 // autosort FFT (radix 16 passes plus one smaller pass), each thread holding
 // its butterflies in registers between passes; twiddles come from an F-point
 // table computed on the host in FP64.
+#include <cuda_bf16.h>
+
 #include "fft.cuh"
 #include "rtis_internal.h"
 
@@ -58,7 +60,8 @@ __global__ void __launch_bounds__(kMfThreads) mf_inverse_kernel(const float2* __
                                                                 const float2* __restrict__ tw, int F,
                                                                 int k_lo, int Kb, int N,
                                                                 float2* __restrict__ a,
-                                                                float2* __restrict__ A_out) {
+                                                                float2* __restrict__ A_out,
+                                                                uint32_t* __restrict__ a16) {
     extern __shared__ float2 sbuf[];
     constexpr int P = 1 << LOGP;
     const int m = blockIdx.x, q = blockIdx.y;
@@ -88,16 +91,20 @@ __global__ void __launch_bounds__(kMfThreads) mf_inverse_kernel(const float2* __
         }
         sbuf[spad(kp)] = g;
     }
-    if (a == nullptr) return;  // spectrum only (uniform across the block)
+    if (a == nullptr && a16 == nullptr) return;  // spectrum only (uniform across the block)
     __syncthreads();
     fft_smem<LOGP, true, kMfThreads>(sbuf, GlobalTwiddles{tw}, F);
-    float2* arow = a + static_cast<size_t>(m) * N;
     const unsigned fmask = static_cast<unsigned>(F - 1);
     for (int p = threadIdx.x; p < P; p += kMfThreads) {
         const int n = 4 * p + q;
         if (n < N) {
             const unsigned idx = (static_cast<unsigned>(k_lo) * static_cast<unsigned>(n)) & fmask;
-            arow[n] = cmul(sbuf[spad(p)], conjf2(__ldg(tw + idx)));
+            const float2 v = cmul(sbuf[spad(p)], conjf2(__ldg(tw + idx)));
+            if (a) a[static_cast<size_t>(m) * N + n] = v;
+            if (a16) {  // round to nearest even; re in the low half, im in the high half
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+                a16[static_cast<size_t>(m) * N + n] = *reinterpret_cast<const uint32_t*>(&h);
+            }
         }
     }
 }
@@ -118,14 +125,14 @@ cudaError_t mf_forward_t(const Plan& p, const int16_t* d_in, cudaStream_t st) {
 }
 
 template <int LOGP>
-cudaError_t mf_inverse_t(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st) {
+cudaError_t mf_inverse_t(const Plan& p, float2* d_a, float2* d_A, uint32_t* d_a16, cudaStream_t st) {
     const size_t sm = mf_smem<LOGP>();
     cudaError_t e = cudaFuncSetAttribute(mf_inverse_kernel<LOGP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sm));
     if (e != cudaSuccess) return e;
-    const int nq = d_a ? 4 : 1;
+    const int nq = (d_a || d_a16) ? 4 : 1;
     mf_inverse_kernel<LOGP><<<dim3(p.M, nq), kMfThreads, sm, st>>>(p.d_Z, p.d_C, p.d_tw, p.F, p.k_lo, p.Kb,
-                                                                  p.N, d_a, d_A);
+                                                                  p.N, d_a, d_A, d_a16);
     return cudaGetLastError();
 }
 
@@ -146,17 +153,17 @@ cudaError_t launch_mf_forward(const Plan& p, const int16_t* d_in, cudaStream_t s
     }
 }
 
-cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st) {
+cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st, uint32_t* d_a16) {
     switch (p.logP) {
-        case 6: return mf_inverse_t<6>(p, d_a, d_A, st);
-        case 7: return mf_inverse_t<7>(p, d_a, d_A, st);
-        case 8: return mf_inverse_t<8>(p, d_a, d_A, st);
-        case 9: return mf_inverse_t<9>(p, d_a, d_A, st);
-        case 10: return mf_inverse_t<10>(p, d_a, d_A, st);
-        case 11: return mf_inverse_t<11>(p, d_a, d_A, st);
-        case 12: return mf_inverse_t<12>(p, d_a, d_A, st);
-        case 13: return mf_inverse_t<13>(p, d_a, d_A, st);
-        case 14: return mf_inverse_t<14>(p, d_a, d_A, st);
+        case 6: return mf_inverse_t<6>(p, d_a, d_A, d_a16, st);
+        case 7: return mf_inverse_t<7>(p, d_a, d_A, d_a16, st);
+        case 8: return mf_inverse_t<8>(p, d_a, d_A, d_a16, st);
+        case 9: return mf_inverse_t<9>(p, d_a, d_A, d_a16, st);
+        case 10: return mf_inverse_t<10>(p, d_a, d_A, d_a16, st);
+        case 11: return mf_inverse_t<11>(p, d_a, d_A, d_a16, st);
+        case 12: return mf_inverse_t<12>(p, d_a, d_A, d_a16, st);
+        case 13: return mf_inverse_t<13>(p, d_a, d_A, d_a16, st);
+        case 14: return mf_inverse_t<14>(p, d_a, d_A, d_a16, st);
         default: return cudaErrorInvalidValue;
     }
 }

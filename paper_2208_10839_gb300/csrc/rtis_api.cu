@@ -31,7 +31,8 @@ cudaError_t dev_alloc(T** ptr, size_t count, size_t* total) {
 
 void free_plan_buffers(Plan& p) {
     void* bufs[] = {p.d_mic, p.d_dirs, p.d_gain, p.d_delay, p.d_tw, p.d_C, p.d_h,
-                    p.d_shift, p.d_wt, p.d_dphase, p.d_wraw, p.d_wder, p.d_adj, p.d_Z, p.d_a, p.d_A, p.d_status};
+                    p.d_shift, p.d_wt, p.d_dphase, p.d_wraw, p.d_wder, p.d_adj, p.d_Z, p.d_a, p.d_A, p.d_a16,
+                    p.d_status};
     for (void* b : bufs)
         if (b) cudaFree(b);
 }
@@ -80,6 +81,15 @@ bool encode_tmap(CUtensorMap* map, CUtensorMapDataType dtype, uint32_t rank, con
         return false;
     }
     return true;
+}
+
+bool encode_tmap_2d_u32(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                        uint32_t box_rows, std::string* err) {
+    const uint64_t dims[2] = {cols, rows};
+    const uint64_t strides[1] = {cols * 4};
+    const uint32_t box[2] = {box_cols, box_rows};
+    return encode_tmap(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, base, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       err);
 }
 
 bool encode_tmap_2d_u64(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols,
@@ -160,6 +170,10 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: max_delay_s and position_slack_m must be >= 0");
     if (opt.path != RTIS_PATH_TD && opt.path != RTIS_PATH_FD)
         return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: unknown path");
+    if (opt.precision != RTIS_PREC_FP32 && opt.precision != RTIS_PREC_BF16)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: precision must be RTIS_PREC_FP32 or RTIS_PREC_BF16");
+    if (opt.precision == RTIS_PREC_BF16 && opt.path != RTIS_PATH_TD)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: BF16 storage applies to the time-domain path only");
     if (!rtis::all_finite(mic_xyz, 3 * static_cast<size_t>(n_mics)) ||
         !rtis::all_finite(directions, 3 * static_cast<size_t>(n_dirs)) ||
         !rtis::all_finite(chirp, chirp_len) || (opt.lpf_taps && !rtis::all_finite(opt.lpf_taps, lpf_len)))
@@ -196,6 +210,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     p.n_out = n_samples / opt.decim;
     p.fs = fs;
     p.c = opt.c;
+    p.a_bf16 = (opt.precision == RTIS_PREC_BF16);
 
     // largest |delta| the geometry (plus calibration slack) can produce
     double pmax = 0.0, umax = 0.0;
@@ -212,8 +227,9 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     H = (H + 3) & ~3;
     p.H = H;
     p.Jlim = H - 2;
-    // a lane reads pairs from an even index up to lane_base + Jlim + T + 3
-    p.td_nbox = (H + p.Jlim + rtis::kTdWarpSamples + 4 + rtis::kTdBox - 1) / rtis::kTdBox;
+    // a lane reads pairs from an even index up to lane_base + Jlim + T + 3, and the
+    // row starts up to 3 samples before n_start - H (x0 rounded down to 4 for BF16)
+    p.td_nbox = (H + p.Jlim + rtis::kTdWarpSamples + 8 + rtis::kTdBox - 1) / rtis::kTdBox;
     p.td_row = p.td_nbox * rtis::kTdBox;
     p.td_bins_per_tile = (rtis::kTdWarpSamples - lpf_len) / p.R + 1;
     if (rtis::td_smem_bytes(p) > 227 * 1024) {
@@ -288,6 +304,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     RTIS_ALLOC(p.d_A, static_cast<size_t>(n_mics) * p.Kb)
     RTIS_ALLOC(p.d_Z, static_cast<size_t>(n_mics) * 2 * p.P)
     RTIS_ALLOC(p.d_a, static_cast<size_t>(n_mics) * n_samples)
+    if (p.a_bf16) RTIS_ALLOC(p.d_a16, static_cast<size_t>(n_mics) * n_samples)
     RTIS_ALLOC(p.d_status, 1)
 #undef RTIS_ALLOC
     p.bytes = total;
@@ -318,7 +335,9 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     }
     std::string err;
     if (!rtis::encode_tmap_2d_u64(&p.tmap_a, p.d_a, static_cast<uint64_t>(n_samples), static_cast<uint64_t>(n_mics),
-                                  rtis::kTdBox, 1, &err)) {
+                                  rtis::kTdBox, 1, &err) ||
+        (p.a_bf16 && !rtis::encode_tmap_2d_u32(&p.tmap_a16, p.d_a16, static_cast<uint64_t>(n_samples),
+                                               static_cast<uint64_t>(n_mics), rtis::kTdBox, 1, &err))) {
         rtis::free_plan_buffers(p);
         delete plan;
         return fail(RTIS_ERR_CUDA, "rtis_plan_create: " + err);
@@ -329,6 +348,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         // autotune the beamformer on the zeroed workspace with a scratch output
         float* scratch = nullptr;
         e = cudaMemset(p.d_a, 0, static_cast<size_t>(n_mics) * n_samples * sizeof(float2));
+        if (e == cudaSuccess && p.a_bf16) e = cudaMemset(p.d_a16, 0, static_cast<size_t>(n_mics) * n_samples * 4);
         if (e == cudaSuccess) e = cudaMalloc(&scratch, static_cast<size_t>(n_dirs) * p.n_out * sizeof(float));
         if (e == cudaSuccess) e = rtis::td_autotune(p, scratch);
         if (scratch) cudaFree(scratch);
@@ -415,7 +435,7 @@ rtis_status rtis_beamform_td(rtis_plan* plan, const float* d_a, float* d_out, vo
         return fail(RTIS_ERR_CUDA, "rtis_beamform_td: " + err);
     rtis_status s = ensure_table(p, st);
     if (s != RTIS_OK) return s;
-    cudaError_t e = rtis::launch_td_beamform(p, map, d_out, st);
+    cudaError_t e = rtis::launch_td_beamform(p, map, false, d_out, st);  // the caller's complex-float a
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_beamform_td: launch");
 }
 
@@ -432,8 +452,13 @@ rtis_status rtis_process(rtis_plan* plan, const int16_t* d_in, float* d_out, voi
         if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, nullptr, p.d_A, st);
         if (e == cudaSuccess) e = rtis::launch_fd_energyscape(p, p.d_A, d_out, st);
     } else {
-        if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, p.d_a, nullptr, st);
-        if (e == cudaSuccess) e = rtis::launch_td_beamform(p, p.tmap_a, d_out, st);
+        if (p.a_bf16) {
+            if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, nullptr, nullptr, st, p.d_a16);
+            if (e == cudaSuccess) e = rtis::launch_td_beamform(p, p.tmap_a16, true, d_out, st);
+        } else {
+            if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, p.d_a, nullptr, st);
+            if (e == cudaSuccess) e = rtis::launch_td_beamform(p, p.tmap_a, false, d_out, st);
+        }
     }
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_process: launch");
 }

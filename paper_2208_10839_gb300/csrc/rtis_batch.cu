@@ -48,7 +48,9 @@ cudaError_t enqueue(rtis_batch* b, const int16_t* const* d_in, float* const* d_o
     for (size_t i = 0; i < b->plans.size(); ++i) {
         rtis::Plan& p = b->plans[i]->p;
         cudaError_t e = rtis::launch_mf_forward(p, d_in[i], st);
-        if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, p.d_a, nullptr, st);
+        if (e == cudaSuccess)
+            e = p.a_bf16 ? rtis::launch_mf_inverse(p, nullptr, nullptr, st, p.d_a16)
+                         : rtis::launch_mf_inverse(p, p.d_a, nullptr, st);
         if (e != cudaSuccess) return e;
         b->bt.s[i].E = d_out[i];
     }
@@ -112,13 +114,16 @@ rtis_status build_tables(rtis_plan* const* plans, int n, rtis::TdMaps* maps, rti
     for (int i = 0; i < n; ++i) {
         if (!plans[i]) return fail(RTIS_ERR_INVALID_ARG, "batch: NULL plan");
         const rtis::Plan& p = plans[i]->p;
-        maps->m[i] = p.tmap_a;
+        if (p.a_bf16 != plans[0]->p.a_bf16)
+            return fail(RTIS_ERR_INVALID_ARG, "batch: plans must share one storage precision (FP32 or BF16)");
+        maps->m[i] = p.a_bf16 ? p.tmap_a16 : p.tmap_a;
         rtis::td_fill_sensor(p, nullptr, tiles, &bt->s[i]);
         tiles += rtis::td_tiles(p);
         row_max = std::max(row_max, p.td_row);
         lpf_max = std::max(lpf_max, p.lpf_len);
     }
     bt->n_sensors = n;
+    bt->bf16 = plans[0]->p.a_bf16 ? 1 : 0;
     bt->total_tiles = tiles;
     bt->row_max = row_max;
     bt->lpf_max = lpf_max;

@@ -57,10 +57,13 @@ struct Plan {
     float2* d_Z = nullptr;      // [M][2][P] half-size spectra
     float2* d_a = nullptr;      // [M][N] analytic matched-filter output
     float2* d_A = nullptr;      // [M][Kb] in-band matched-filter spectra (frequency-domain path)
+    uint32_t* d_a16 = nullptr;  // [M][N] a as BF16 (re, im) pairs (time-domain path, BF16 storage)
     unsigned* d_status = nullptr;
     size_t bytes = 0;
 
     CUtensorMap tmap_a;         // TMA view of d_a as [M][N] 8-byte elements
+    CUtensorMap tmap_a16;       // TMA view of d_a16 as [M][N] 4-byte elements (BF16 plans)
+    bool a_bf16 = false;        // rtis_process / batches beamform from the BF16 copy of a
     bool table_dirty = true;
 };
 
@@ -93,9 +96,11 @@ rtis_status cuda_fail(cudaError_t e, const char* what);
 // launchers (return cudaGetLastError() of the launch)
 // ----------------------------------------------------------------------------
 cudaError_t launch_mf_forward(const Plan& p, const int16_t* d_in, cudaStream_t st);
-cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st);
+// writes a (complex float) and/or a16 (BF16 pairs) and/or the in-band spectra A
+cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st, uint32_t* d_a16 = nullptr);
 cudaError_t launch_steering_table(Plan& p, cudaStream_t st);
-cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, float* d_out, cudaStream_t st);
+// bf16: tmap views BF16 pairs (4-byte elements) rather than complex floats
+cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, bool bf16, float* d_out, cudaStream_t st);
 size_t td_smem_bytes(const Plan& p);
 size_t td_smem_bytes(int row_max, int lpf_max);
 cudaError_t launch_fd_energyscape(const Plan& p, const float2* d_A, float* d_out, cudaStream_t st);
@@ -115,6 +120,7 @@ struct TdSensor {
 struct TdBatch {
     TdSensor s[kTdMaxSensors];
     int n_sensors, total_tiles, row_max, lpf_max;
+    int bf16;  // the staged rows are BF16 (re, im) pairs, 4 bytes per sample
     unsigned* status;
 };
 struct TdMaps {
@@ -131,6 +137,8 @@ size_t adj_smem_bytes(const Plan& p);
 cudaError_t launch_td_batch(const TdMaps& maps, const TdBatch& bt, int variant, int grid, cudaStream_t st);
 
 bool encode_tmap_2d_u64(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows,
+                        uint32_t box_cols, uint32_t box_rows, std::string* err);
+bool encode_tmap_2d_u32(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows,
                         uint32_t box_cols, uint32_t box_rows, std::string* err);
 // generic tiled tensor map: dims[rank], strides[rank-1] in bytes, box[rank]
 bool encode_tmap(CUtensorMap* map, CUtensorMapDataType dtype, uint32_t rank, const void* base, const uint64_t* dims,

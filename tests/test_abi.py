@@ -74,6 +74,8 @@ def _args():
     (dict(decim=0), 1),
     (dict(band=(80e3, 20e3)), 1),
     (dict(band=(20e3, 150e3)), 4),        # band above fs/4
+    (dict(precision=2), 4),               # FP16 storage is not offered
+    (dict(precision=1, path=1), 4),       # BF16 storage on the frequency-domain path
 ])
 def test_plan_create_rejects(nat, kw, status):
     mic, ch, dirs = _args()
@@ -89,6 +91,10 @@ def test_plan_create_rejects(nat, kw, status):
         o.decim = kw["decim"]
     if "band" in kw:
         o.band_lo_hz, o.band_hi_hz = kw["band"]
+    if "precision" in kw:
+        o.precision = kw["precision"]
+    if "path" in kw:
+        o.path = kw["path"]
     with pytest.raises(nat.RtisError) as ei:
         nat.rtis_plan_create(mic, kw.get("fs", 450e3), ch, dirs, kw.get("n_samples", 4096), o)
     assert ei.value.status == status
