@@ -78,6 +78,43 @@ __host__ __device__ inline FdesSmem fdes_layout(int P, int F, int Kb, int n_out,
     return L;
 }
 
+// Steered spectrum on NBIN slots of one thread: bins kp0 + 256 i, i < NBIN.
+// Per mic the phase is anchored exactly at kp0 (compensated FP32, integer
+// cycles removed) and advanced by exp(2 pi i 256 delta/F) per slot.
+template <int NBIN>
+__device__ __forceinline__ void fdes_gemv_chunk(const FdesArgs& a, const float2* __restrict__ dph,
+                                                const float* gs, const float2* step, float2* B, int kp0) {
+    const int M = a.M, Kb = a.Kb;
+    float2 acc[NBIN];
+#pragma unroll
+    for (int i = 0; i < NBIN; ++i) acc[i] = make_float2(0.f, 0.f);
+    const float k0 = static_cast<float>(a.k_lo + kp0);
+#pragma unroll 2
+    for (int m = 0; m < M; ++m) {
+        float s, c;
+        __sincosf(6.28318530717958647692f * frac_cycles(k0, __ldg(dph + m)), &s, &c);
+        const float g = gs[m];
+        float2 w = make_float2(g * c, g * s);
+        const float2 st = step[m];
+        const float2* Am = a.A + static_cast<size_t>(m) * Kb;
+#pragma unroll
+        for (int i = 0; i < NBIN; ++i) {
+            const int kp = kp0 + i * kFdesThreads;
+            if (kp < Kb) {
+                const float2 v = __ldg(Am + kp);
+                acc[i].x = fmaf(w.x, v.x, fmaf(-w.y, v.y, acc[i].x));
+                acc[i].y = fmaf(w.x, v.y, fmaf(w.y, v.x, acc[i].y));
+            }
+            if (i + 1 < NBIN) w = cmul(w, st);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NBIN; ++i) {
+        const int kp = kp0 + i * kFdesThreads;
+        if (kp < Kb) B[kp] = acc[i];
+    }
+}
+
 // One inverse radix-16 Stockham pass over P points (padded layout fpad),
 // Ns = product of the earlier radices.  The last pass (Ns = P/16) writes
 // env[p] = |b(4p + q)| for p < p_need instead of the complex values.
@@ -169,38 +206,22 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
     const SplitTwiddles tws{twhi, twlo};
 
     // ---- steered spectrum B_d ------------------------------------------------
+    // slots of 256 bins: full chunks of kFdesChunk slots, then the tail in chunks
+    // of 4, 2, 1 so that no thread advances the recurrence past the band
     const float2* dph = a.dphase + static_cast<size_t>(d) * M;
-    for (int c0 = 0; c0 * kFdesThreads < Kb; c0 += kFdesChunk) {
-        const int kp0 = c0 * kFdesThreads + tid;  // bins kp0 + 256 i, i < kFdesChunk
-        float2 acc[kFdesChunk];
-#pragma unroll
-        for (int i = 0; i < kFdesChunk; ++i) acc[i] = make_float2(0.f, 0.f);
-        const float k0 = static_cast<float>(a.k_lo + kp0);
-#pragma unroll 2
-        for (int m = 0; m < M; ++m) {
-            float s, c;
-            __sincosf(6.28318530717958647692f * frac_cycles(k0, __ldg(dph + m)), &s, &c);
-            const float g = gs[m];
-            float2 w = make_float2(g * c, g * s);
-            const float2 st = step[m];
-            const float2* Am = a.A + static_cast<size_t>(m) * Kb;
-#pragma unroll
-            for (int i = 0; i < kFdesChunk; ++i) {
-                const int kp = kp0 + i * kFdesThreads;
-                if (kp < Kb) {
-                    const float2 v = __ldg(Am + kp);
-                    acc[i].x = fmaf(w.x, v.x, fmaf(-w.y, v.y, acc[i].x));
-                    acc[i].y = fmaf(w.x, v.y, fmaf(w.y, v.x, acc[i].y));
-                }
-                w = cmul(w, st);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < kFdesChunk; ++i) {
-            const int kp = kp0 + i * kFdesThreads;
-            if (kp < Kb) B[kp] = acc[i];
-        }
+    const int nslots = (Kb + kFdesThreads - 1) / kFdesThreads;
+    int c0 = 0;
+    for (; c0 + kFdesChunk <= nslots; c0 += kFdesChunk)
+        fdes_gemv_chunk<kFdesChunk>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
+    if ((nslots - c0) & 4) {
+        fdes_gemv_chunk<4>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
+        c0 += 4;
     }
+    if ((nslots - c0) & 2) {
+        fdes_gemv_chunk<2>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
+        c0 += 2;
+    }
+    if ((nslots - c0) & 1) fdes_gemv_chunk<1>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
     __syncthreads();
 
     // ---- four phase IFFTs, each folded into the low-pass outputs ------------
