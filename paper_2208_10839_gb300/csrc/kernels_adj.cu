@@ -30,6 +30,7 @@ namespace {
 
 constexpr uint32_t kAdjPolls = 1u << 22;
 constexpr int kAdjMS = 2, kAdjNS = 4;  // mics per stage, ring depth (the forward's default layout)
+static_assert(kAdjMS == 2, "the pass-B reduction pairs the two mics of a stage");
 
 struct AdjArgs {
     const int* shift;
@@ -202,61 +203,103 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
             }
         }
         const bool pass_b = st >= ngroups;
+        const int grp = st % ngroups;
         if (dir_ok && !__any_sync(0xffffffffu, timed_out)) {
+            if (!pass_b) {
 #pragma unroll 1
-            for (int mi = 0; mi < MS; ++mi) {
-                const int m = (st % ngroups) * MS + mi;
-                if (m >= M) break;
-                const int J = __shfl_sync(0xffffffffu, my_shift, m);
-                const int s0 = lane_base + J;
-                const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
-                    stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
-                const float w0 = __shfl_sync(0xffffffffu, my_w.x, m), w1 = __shfl_sync(0xffffffffu, my_w.y, m);
-                const float w2 = __shfl_sync(0xffffffffu, my_w.z, m), w3 = __shfl_sync(0xffffffffu, my_w.w, m);
-                if (!pass_b) {
+                for (int mi = 0; mi < MS; ++mi) {
+                    const int m = grp * MS + mi;
+                    if (m >= M) break;
+                    const int J = __shfl_sync(0xffffffffu, my_shift, m);
+                    const int s0 = lane_base + J;
+                    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
+                        stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
                     const float g = __shfl_sync(0xffffffffu, my_g, m);
-                    const float f0 = g * w0, f1 = g * w1, f2 = g * w2, f3 = g * w3;
+                    const float f0 = g * __shfl_sync(0xffffffffu, my_w.x, m);
+                    const float f1 = g * __shfl_sync(0xffffffffu, my_w.y, m);
+                    const float f2 = g * __shfl_sync(0xffffffffu, my_w.z, m);
+                    const float f3 = g * __shfl_sync(0xffffffffu, my_w.w, m);
                     if (s0 & 1)
                         adj_fwd_mic<true>(acc, p, pack2a(f0, f0), pack2a(f1, f1), pack2a(f2, f2), pack2a(f3, f3));
                     else
                         adj_fwd_mic<false>(acc, p, pack2a(f0, f0), pack2a(f1, f1), pack2a(f2, f2), pack2a(f3, f3));
-                } else {
-                    const float4 C = (s0 & 1) ? adj_corr_mic<true>(acc, p) : adj_corr_mic<false>(acc, p);
-                    const float d0 = __shfl_sync(0xffffffffu, my_wd.x, m), d1 = __shfl_sync(0xffffffffu, my_wd.y, m);
-                    const float d2 = __shfl_sync(0xffffffffu, my_wd.z, m), d3 = __shfl_sync(0xffffffffu, my_wd.w, m);
-                    float sg = fmaf(w0, C.x, fmaf(w1, C.y, fmaf(w2, C.z, w3 * C.w)));
-                    float sd = fmaf(d0, C.x, fmaf(d1, C.y, fmaf(d2, C.z, d3 * C.w)));
+                }
+            } else {
+                // both mics of the stage, then one joint reduction of their (value, slope) sums
+                float red[MS][2];
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        sg += __shfl_xor_sync(0xffffffffu, sg, o);
-                        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                for (int mi = 0; mi < MS; ++mi) {
+                    red[mi][0] = red[mi][1] = 0.f;
+                    const int m = grp * MS + mi;
+                    if (m < M) {
+                        const int J = __shfl_sync(0xffffffffu, my_shift, m);
+                        const int s0 = lane_base + J;
+                        const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
+                            stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
+                        const float4 C = (s0 & 1) ? adj_corr_mic<true>(acc, p) : adj_corr_mic<false>(acc, p);
+                        const float w0 = __shfl_sync(0xffffffffu, my_w.x, m), w1 = __shfl_sync(0xffffffffu, my_w.y, m);
+                        const float w2 = __shfl_sync(0xffffffffu, my_w.z, m), w3 = __shfl_sync(0xffffffffu, my_w.w, m);
+                        const float d0 = __shfl_sync(0xffffffffu, my_wd.x, m), d1 = __shfl_sync(0xffffffffu, my_wd.y, m);
+                        const float d2 = __shfl_sync(0xffffffffu, my_wd.z, m), d3 = __shfl_sync(0xffffffffu, my_wd.w, m);
+                        red[mi][0] = fmaf(w0, C.x, fmaf(w1, C.y, fmaf(w2, C.z, w3 * C.w)));
+                        red[mi][1] = fmaf(d0, C.x, fmaf(d1, C.y, fmaf(d2, C.z, d3 * C.w)));
                     }
-                    if (lane == m) {
-                        sum_g = sg;
-                        sum_d = sd;
-                    }
+                }
+                // reduce-scatter of the 4 sums over the warp: after the xor-16 and xor-8
+                // exchanges lane bits (4, 3) select (mic, value/slope); then a plain sum
+                const bool b16 = lane & 16, b8 = lane & 8;
+                float k0 = b16 ? red[1][0] : red[0][0], k1 = b16 ? red[1][1] : red[0][1];
+                const float s0 = b16 ? red[0][0] : red[1][0], s1 = b16 ? red[0][1] : red[1][1];
+                k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+                k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+                float k = b8 ? k1 : k0;
+                k += __shfl_xor_sync(0xffffffffu, b8 ? k0 : k1, 8);
+                k += __shfl_xor_sync(0xffffffffu, k, 4);
+                k += __shfl_xor_sync(0xffffffffu, k, 2);
+                k += __shfl_xor_sync(0xffffffffu, k, 1);
+                const int m0 = grp * MS;
+                const int src = (lane == m0 + 1) ? 16 : 0;
+                const float tg = __shfl_sync(0xffffffffu, k, src), td = __shfl_sync(0xffffffffu, k, src + 8);
+                if (lane == m0 || lane == m0 + 1) {
+                    sum_g = tg;
+                    sum_d = td;
                 }
             }
         }
         if (st == ngroups - 1 && dir_ok && !__any_sync(0xffffffffu, timed_out)) {
-            // beams of this tile are complete: turn them into G_b = G_env b / |b| on owned samples
+            // beams of this tile are complete: turn them into G_b = G_env b / |b| on owned
+            // samples.  G_env[n] sums the bins i in [ceil((n - half)/R), floor((n + half)/R)]
+            // (tap j = n - R i + half); both ends advance incrementally with n.
             __syncwarp();
+            const int R = args.R;
+            const int n_first = n_start + lane * T;
+            const int xo = n_first - half + R * reach * 4;  // > 0
+            int i_lo = (xo + R - 1) / R - reach * 4;           // ceil((n - half)/R)
+            int r_lo = (i_lo + reach * 4) * R - xo;            // R i_lo - (n - half), in [0, R)
+            const int yo = n_first + half + R * reach * 4;
+            int i_hi = yo / R - reach * 4;                     // floor((n + half)/R)
+            int r_hi = yo - (i_hi + reach * 4) * R;            // (n + half) - R i_hi, in [0, R)
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                const int n = n_start + lane * T + t;
+                const int n = n_first + t;
                 float ge = 0.f;
                 if (n >= own_lo && n < own_hi && n >= 0 && n < args.N) {
-                    // bins i with |n - R i| <= half, taken from the segment
-                    const int ilo = (n - half + args.R * reach * 4) / args.R - reach * 4;  // floor((n-half)/R)
-                    for (int i = ilo; i <= ilo + 2 * reach; ++i) {
-                        const int j = n - args.R * i + half;
-                        if (j >= 0 && j < args.lpf_len) ge = fmaf(gs[i - iseg0], hs[j], ge);
-                    }
+                    int j = 2 * half - r_lo;  // tap of bin i_lo
+                    for (int i = i_lo; i <= i_hi; ++i, j -= R) ge = fmaf(gs[i - iseg0], hs[j], ge);
                 }
                 const float2 v = unpack2a(acc[t]);
-                const float mag = sqrtf(v.x * v.x + v.y * v.y);
-                const float sc = mag > 0.f ? ge / mag : 0.f;
+                const float m2 = v.x * v.x + v.y * v.y;
+                const float sc = m2 > 0.f ? ge * rsqrtf(m2) : 0.f;
                 acc[t] = pack2a(sc * v.x, sc * v.y);
+                // n -> n + 1
+                if (--r_lo < 0) {
+                    r_lo += R;
+                    ++i_lo;
+                }
+                if (++r_hi == R) {
+                    r_hi = 0;
+                    ++i_hi;
+                }
             }
         }
         // release buffer b; the CTA's last warp to get here refills it
