@@ -54,6 +54,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(values, dev=None):
+    """Element-wise max of per-rank timings (the slowest replica sets the clock).
+    With one process the values come back unchanged; NCCL reduces on the GPU,
+    gloo on the CPU."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    on = dev if (dev is not None and dist.get_backend() == "nccl") else "cpu"
+    tt = torch.tensor([float(v) for v in values], dtype=torch.float64, device=on)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return [float(v) for v in tt.cpu()]
+
+
+def replica_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput of independent replicas: every rank's units over the slowest time."""
+    return world * units_per_rank / seconds
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -210,9 +229,7 @@ def run_fd_gemm(args, rank, world, local):
     ms = [a.elapsed_time(b) for a, b in evs]
     t = sum(ms) / 1e3
     if world > 1:
-        tt = torch.tensor([t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt[0])
+        (t,) = max_over_ranks([t], dev)
     # error against the FP64 oracle on sampled bins (test infrastructure)
     import oracle
     picks = sorted({0, K // 4, K // 2, (3 * K) // 4, K - 1})
@@ -225,7 +242,7 @@ def run_fd_gemm(args, rank, world, local):
     launch_s = statistics.mean(ms) / 1e3
     hbm = peaks.get("hbm_gbs")
     line = {
-        "metric": "frames/s (1200-bin x 2048-dir x 32-mic steering GEMM per frame)", "value": world * args.steps * T / t,
+        "metric": "frames/s (1200-bin x 2048-dir x 32-mic steering GEMM per frame)", "value": replica_rate(args.steps * T, world, t),
         "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.precision, "data": "synthetic",
@@ -293,13 +310,11 @@ def run_ring(args, rank, world, local):
         torch.cuda.synchronize()
         seq.append(e0.elapsed_time(e1))
     if world > 1:
-        tt = torch.tensor([t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt[0])
+        (t,) = max_over_ranks([t], dev)
     n_s = len(sensors)
     line = {
         "metric": "energyscapes/s (ring of 8 sensors, ragged N and D, one batch per step)",
-        "value": world * args.steps * n_s / t, "unit": "energyscapes/s", "n_gpus": world, "steps": args.steps,
+        "value": replica_rate(args.steps * n_s, world, t), "unit": "energyscapes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16 storage, f32 arithmetic",
         "data": "synthetic",
@@ -416,9 +431,7 @@ def run_calibration(args, rank, world, local):
     torch.cuda.synchronize()
     t_e2e = ee0.elapsed_time(ee1) / 1e3
     if world > 1:
-        tt = torch.tensor([t, t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t, t_e2e = float(tt[0]), float(tt[1])
+        t, t_e2e = max_over_ranks([t, t_e2e], dev)
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     peak_tf = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
@@ -428,13 +441,13 @@ def run_calibration(args, rank, world, local):
     line = {
         "metric": "calibration gradients/s (energyscape + L2 loss + adjoint wrt mic xyz, gain, delay; "
                   "32ch x 16384 samples x 2048 dirs)",
-        "value": world * args.steps / t, "unit": "gradients/s", "n_gpus": world, "steps": args.steps,
+        "value": replica_rate(args.steps, world, t), "unit": "gradients/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "calibration: 32 mics perturbed by N(0, 1 mm), gains U(0.8, 1.2), delays "
                                "U(-2, 2) us; 16384 samples, 2048 Fibonacci half-sphere dirs, 10 known reflectors",
                    "l2": "flushed between steps (512 MiB write, then a 256 MiB read so write-backs finish), outside the timed events"},
-        "e2e": {"value": world * n_e2e / t_e2e, "unit": "gradients/s", "h2d_bytes_per_step": int(x.numel() * 2),
+        "e2e": {"value": replica_rate(n_e2e, world, t_e2e), "unit": "gradients/s", "h2d_bytes_per_step": int(x.numel() * 2),
                 "d2h_bytes_per_step": int(4 * (gx.numel() + gg.numel() + gd.numel() + 1))},
         "gpu_launches": 10 * args.steps,
         "kernels_ms": {"forward_and_loss": statistics.mean(fwd_ms), "backward": statistics.mean(bwd_ms),
@@ -587,12 +600,10 @@ def main():
     t_e2e = ee0.elapsed_time(ee1) / 1e3
 
     if world > 1:
-        tt = torch.tensor([t_total, t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total, t_e2e = float(tt[0]), float(tt[1])
+        t_total, t_e2e = max_over_ranks([t_total, t_e2e], dev)
 
-    value = world * args.steps / t_total
-    e2e_value = world * e2e_steps / t_e2e
+    value = replica_rate(args.steps, world, t_total)
+    e2e_value = replica_rate(e2e_steps, world, t_e2e)
     clocks = clk.summary()
 
     # rooflines of the two beamformers, both bound by the FP32 ALU (FMA pipe); the
