@@ -7,7 +7,7 @@
 //   E[d][i] = sum_j h[j] |b_d[R i + j - half]|
 //
 // B_d: thread t owns the bins k' = t + 256 c (coalesced loads of A); per mic
-// and chunk of 8 bins it anchors the steering phase exactly (compensated FP32
+// and chunk of up to 16 bins it anchors the steering phase exactly (compensated FP32
 // product k * delta/F, integer cycles removed) and then advances it with one
 // complex multiply by exp(2 pi i 256 delta/F) per bin.  b_d: with n = 4p + q
 // the band (below F/4) needs four P = F/4 point inverse FFTs of
@@ -29,7 +29,7 @@ namespace {
 using namespace fft;
 
 constexpr int kFdesThreads = 256;
-constexpr int kFdesChunk = 8;  // bins per thread per anchor
+constexpr int kFdesChunk = 16;  // slots of 256 bins per thread per anchor (tail: 8, 4, 2, 1)
 
 struct FdesArgs {
     const float2* A;      // [M][Kb] in-band matched-filter spectra (already / F)
@@ -89,7 +89,7 @@ __device__ __forceinline__ void fdes_gemv_chunk(const FdesArgs& a, const float2*
 #pragma unroll
     for (int i = 0; i < NBIN; ++i) acc[i] = make_float2(0.f, 0.f);
     const float k0 = static_cast<float>(a.k_lo + kp0);
-#pragma unroll 2
+#pragma unroll 4
     for (int m = 0; m < M; ++m) {
         float s, c;
         __sincosf(6.28318530717958647692f * frac_cycles(k0, __ldg(dph + m)), &s, &c);
@@ -207,12 +207,17 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
 
     // ---- steered spectrum B_d ------------------------------------------------
     // slots of 256 bins: full chunks of kFdesChunk slots, then the tail in chunks
-    // of 4, 2, 1 so that no thread advances the recurrence past the band
+    // of 8, 4, 2, 1 so that no thread advances the recurrence past the band
     const float2* dph = a.dphase + static_cast<size_t>(d) * M;
     const int nslots = (Kb + kFdesThreads - 1) / kFdesThreads;
     int c0 = 0;
     for (; c0 + kFdesChunk <= nslots; c0 += kFdesChunk)
         fdes_gemv_chunk<kFdesChunk>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
+    static_assert(kFdesChunk == 16, "the tail below covers remainders up to 15 slots");
+    if ((nslots - c0) & 8) {
+        fdes_gemv_chunk<8>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
+        c0 += 8;
+    }
     if ((nslots - c0) & 4) {
         fdes_gemv_chunk<4>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
         c0 += 4;
