@@ -53,7 +53,7 @@ struct FdArgs {
     const float2* tau;    // [D][M] seconds, hi/lo
     const float2* freq;   // [K] Hz, hi/lo
     const float* gain;    // [M]
-    const float* scale;   // [M] per-channel power-of-two scale s_m
+    const float* scale;   // [M] per-channel max |Re X|, |Im X| as float bits (fd_absmax_kernel)
     unsigned* status;
     int K, M, D, T;
     int n_items;          // direction tiles x bins, item = tile * K + k
@@ -163,7 +163,12 @@ __global__ void __launch_bounds__(kFdThreads, 1)
         if (args.tma_y) ptx::prefetch_tmap(&ymap);
     }
     if (tid < 32) {
-        const float s = tid < M ? args.scale[tid] : 1.f;
+        // s_m = smallest power of two >= max |Re X|, |Im X| of mic m (1 if silent or not finite)
+        float s = 1.f;
+        if (tid < M) {
+            const float amax = __uint_as_float(reinterpret_cast<const unsigned*>(args.scale)[tid]);
+            if (amax > 0.f && isfinite(amax)) s = exp2f(ceilf(log2f(amax)));
+        }
         float mx = tid < M ? s : 0.f;
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         s_scale[tid] = s;
@@ -354,28 +359,37 @@ __global__ void __launch_bounds__(kFdThreads, 1)
     if (warp == 0) ptx::tmem_dealloc(tmem, 2 * NCOL);
 }
 
-// s_m = smallest power of two >= max |Re X|, |Im X| over bins and frames of mic m (1 if silent)
-__global__ void fd_scale_kernel(const float2* __restrict__ X, int K, int M, int T, float* __restrict__ scale) {
-    const int m = blockIdx.x;
-    float mx = 0.f;
-    for (int i = threadIdx.x; i < K * T; i += blockDim.x) {
-        const int k = i / T, t = i - k * T;
-        const float2 x = __ldg(X + (static_cast<size_t>(k) * M + m) * T + t);
-        mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
-    }
-    __shared__ float red[32];
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+// Per-mic max of |Re X|, |Im X| over bins and frames, as float bits (the
+// values are non-negative, so their bit patterns order like the floats):
+// CTAs stride over bins, each thread keeps the maxima of its (mic, frame)
+// slots, then shared and global atomicMax.  bits[] starts at zero.
+__global__ void __launch_bounds__(256) fd_absmax_kernel(const float2* __restrict__ X, int K, int M, int T,
+                                                        unsigned* __restrict__ bits) {
+    __shared__ unsigned smax[kMaxMics];
+    if (threadIdx.x < kMaxMics) smax[threadIdx.x] = 0u;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (threadIdx.x == 0) {
-            float s = 1.0f;
-            if (mx > 0.f && isfinite(mx)) s = exp2f(ceilf(log2f(mx)));
-            scale[m] = s;
+    const int MT = M * T;  // <= 32 x 64 = 8 x 256
+    float mx[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) mx[j] = 0.f;
+    for (int k = blockIdx.x; k < K; k += gridDim.x) {
+        const float2* Xk = X + static_cast<size_t>(k) * MT;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int i = threadIdx.x + 256 * j;
+            if (i < MT) {
+                const float2 x = __ldg(Xk + i);
+                mx[j] = fmaxf(mx[j], fmaxf(fabsf(x.x), fabsf(x.y)));
+            }
         }
     }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int i = threadIdx.x + 256 * j;
+        if (i < MT) atomicMax(&smax[i / T], __float_as_uint(mx[j]));
+    }
+    __syncthreads();
+    if (threadIdx.x < M) atomicMax(&bits[threadIdx.x], smax[threadIdx.x]);
 }
 
 template <int PREC>
@@ -401,8 +415,12 @@ bool fd_gemm_encode_ymap(const FdGemmPlan& g, float2* d_Y, CUtensorMap* map, std
 
 cudaError_t launch_fd_gemm(const FdGemmPlan& g, const float2* d_X, float2* d_Y, const CUtensorMap* ymap,
                            cudaStream_t st) {
-    fd_scale_kernel<<<g.M, 256, 0, st>>>(d_X, g.K, g.M, g.T, g.d_scale);
-    cudaError_t e = cudaGetLastError();
+    // per-channel scales come from the max |X| of this call's input
+    cudaError_t e = cudaMemsetAsync(g.d_scale, 0, static_cast<size_t>(g.M) * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    fd_absmax_kernel<<<std::min(g.K, 4 * std::max(g.n_sm, 1)), 256, 0, st>>>(
+        d_X, g.K, g.M, g.T, reinterpret_cast<unsigned*>(g.d_scale));
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     FdArgs a;
     a.X = d_X;

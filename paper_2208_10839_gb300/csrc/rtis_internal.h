@@ -77,7 +77,7 @@ struct FdGemmPlan {
     float2* d_tau = nullptr;    // [D][M] seconds, (hi, lo)
     float2* d_freq = nullptr;   // [K] Hz, (hi, lo)
     float* d_gain = nullptr;    // [M]
-    float* d_scale = nullptr;   // [M]
+    float* d_scale = nullptr;   // [M] per-channel max |Re X|, |Im X| of the last run (float bits)
     unsigned* d_status = nullptr;
 };
 // ymap: TMA view of Y (fd_gemm_encode_ymap) or nullptr for plain stores
