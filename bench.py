@@ -44,7 +44,11 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each beamformer (ncu capture of this
 # workload, see profiles/); set to None whenever that kernel changes until it is re-captured
 TD_TRAFFIC_BYTES = 5539584
-FD_TRAFFIC_BYTES = 1736704
+FD_TRAFFIC_BYTES = 1774336
+# td_adjoint_kernel on the calibration workload (32 x 16384 x 2048)
+ADJ_TRAFFIC_BYTES = 20086784
+# fd_gemm_kernel<BF16> captured at 400 bins (DRAM read + write), per bin; X and Y both grow with the bins
+FD_GEMM_TRAFFIC_PER_BIN = (13952256 + 358419200) / 400
 
 
 def dist_env():
@@ -251,7 +255,8 @@ def run_fd_gemm(args, rank, world, local):
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "hbm", "kernel": "fd_gemm_kernel", "achieved": bytes_alg / launch_s / 1e9,
                      "peak": hbm, "unit": "GB/s", "frac": (bytes_alg / launch_s / 1e9) / hbm if hbm else None,
-                     "traffic": None, "algorithmic_bytes_per_launch": bytes_alg, "launch_ms": launch_s * 1e3,
+                     "traffic": (FD_GEMM_TRAFFIC_PER_BIN * K) if args.precision == "bf16" else None,
+                     "traffic_note": "BF16 capture at 400 bins scaled by the bin count", "algorithmic_bytes_per_launch": bytes_alg, "launch_ms": launch_s * 1e3,
                      "tensor_flops_per_launch": 8.0 * K * D * M * T * (3 if args.precision == "fp32" else 1)},
         "clocks": clk.summary(),
     }
@@ -449,13 +454,13 @@ def run_calibration(args, rank, world, local):
                    "l2": "flushed between steps (512 MiB write, then a 256 MiB read so write-backs finish), outside the timed events"},
         "e2e": {"value": replica_rate(n_e2e, world, t_e2e), "unit": "gradients/s", "h2d_bytes_per_step": int(x.numel() * 2),
                 "d2h_bytes_per_step": int(4 * (gx.numel() + gg.numel() + gd.numel() + 1))},
-        "gpu_launches": 10 * args.steps,
+        "gpu_launches": 11 * args.steps,
         "kernels_ms": {"forward_and_loss": statistics.mean(fwd_ms), "backward": statistics.mean(bwd_ms),
                        "matched_filter": statistics.mean(mf),
                        "adjoint_and_reduce": statistics.mean(bwd_ms) - statistics.mean(mf)},
         "roofline": {"bound": "alu", "kernel": "td_adjoint_kernel (+ adj_reduce_kernel)",
                      "achieved": flops / adj_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": flops / adj_s / 1e12 / peak_tf, "traffic": None,
+                     "frac": flops / adj_s / 1e12 / peak_tf, "traffic": ADJ_TRAFFIC_BYTES,
                      "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x "
                                    f"{SM_MAX_MHZ_NOMINAL:.0f} MHz",
                      "algorithmic_flops_per_launch": flops, "launch_ms": adj_s * 1e3},

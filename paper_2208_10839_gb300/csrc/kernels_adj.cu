@@ -330,46 +330,59 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
     }
 }
 
-// One CTA per mic: fixed-order sums over range tiles and directions.
-__global__ void adj_reduce_kernel(const float2* __restrict__ part, const float* __restrict__ dirs, int M, int D,
-                                  int n_tiles, double fs, double fs_over_c, float* __restrict__ gxyz,
-                                  float* __restrict__ ggain, float* __restrict__ gdelay) {
-    constexpr int NT = 256;
-    const int m = blockIdx.x;
-    float sd = 0.f, sg = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-    for (int d = threadIdx.x; d < D; d += NT) {
+// Two-stage fixed-order reduction of the per-(tile, direction, mic) partials.
+// Stage 1: CTA (m, blk) sums directions [blk D/NB, (blk + 1) D/NB) over all
+// range tiles into five values: sum dL/d delta, sum dL/d g, sum dL/d delta u.
+constexpr int kAdjRedBlocks = 16, kAdjRedThreads = 256;
+
+__global__ void __launch_bounds__(kAdjRedThreads) adj_reduce1_kernel(const float2* __restrict__ part,
+                                                                     const float* __restrict__ dirs, int M, int D,
+                                                                     int n_tiles, float* __restrict__ red5) {
+    const int m = blockIdx.x, blk = blockIdx.y;
+    const int d_lo = static_cast<int>((static_cast<long long>(blk) * D) / kAdjRedBlocks);
+    const int d_hi = static_cast<int>((static_cast<long long>(blk + 1) * D) / kAdjRedBlocks);
+    float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int d = d_lo + threadIdx.x; d < d_hi; d += kAdjRedThreads) {
         float pd = 0.f, pg = 0.f;
         for (int t = 0; t < n_tiles; ++t) {
-            const float2 v = part[(static_cast<size_t>(t) * D + d) * M + m];
-            pd += v.x;
-            pg += v.y;
+            const float2 x = part[(static_cast<size_t>(t) * D + d) * M + m];
+            pd += x.x;
+            pg += x.y;
         }
-        sd += pd;
-        sg += pg;
-        sx = fmaf(pd, dirs[3 * d], sx);
-        sy = fmaf(pd, dirs[3 * d + 1], sy);
-        sz = fmaf(pd, dirs[3 * d + 2], sz);
+        v[0] += pd;
+        v[1] += pg;
+        v[2] = fmaf(pd, dirs[3 * d], v[2]);
+        v[3] = fmaf(pd, dirs[3 * d + 1], v[3]);
+        v[4] = fmaf(pd, dirs[3 * d + 2], v[4]);
     }
-    __shared__ float red[5][NT];
-    red[0][threadIdx.x] = sd;
-    red[1][threadIdx.x] = sg;
-    red[2][threadIdx.x] = sx;
-    red[3][threadIdx.x] = sy;
-    red[4][threadIdx.x] = sz;
+    __shared__ float red[5][kAdjRedThreads];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) red[k][threadIdx.x] = v[k];
     __syncthreads();
-    for (int w = NT / 2; w > 0; w >>= 1) {
+    for (int w = kAdjRedThreads / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w)
+#pragma unroll
             for (int k = 0; k < 5; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        if (gdelay) gdelay[m] = static_cast<float>(fs * red[0][0]);
-        if (ggain) ggain[m] = red[1][0];
-        if (gxyz) {
-            gxyz[3 * m] = static_cast<float>(-fs_over_c * red[2][0]);
-            gxyz[3 * m + 1] = static_cast<float>(-fs_over_c * red[3][0]);
-            gxyz[3 * m + 2] = static_cast<float>(-fs_over_c * red[4][0]);
-        }
+    if (threadIdx.x < 5) red5[(m * kAdjRedBlocks + blk) * 5 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Stage 2: one thread per mic sums the blocks in order and applies the chain rule.
+__global__ void adj_reduce2_kernel(const float* __restrict__ red5, int M, double fs, double fs_over_c,
+                                   float* __restrict__ gxyz, float* __restrict__ ggain, float* __restrict__ gdelay) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int blk = 0; blk < kAdjRedBlocks; ++blk)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[k] += red5[(m * kAdjRedBlocks + blk) * 5 + k];
+    if (gdelay) gdelay[m] = static_cast<float>(fs * v[0]);
+    if (ggain) ggain[m] = static_cast<float>(v[1]);
+    if (gxyz) {
+        gxyz[3 * m] = static_cast<float>(-fs_over_c * v[2]);
+        gxyz[3 * m + 1] = static_cast<float>(-fs_over_c * v[3]);
+        gxyz[3 * m + 2] = static_cast<float>(-fs_over_c * v[4]);
     }
 }
 
@@ -454,8 +467,11 @@ cudaError_t launch_td_adjoint(const Plan& p, const float* d_grad_out, float* d_g
     td_adjoint_kernel<<<grid, 32 * kTdDirsPerCta, smem, st>>>(p.tmap_a, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    adj_reduce_kernel<<<p.M, 256, 0, st>>>(p.d_adj, p.d_dirs, p.M, p.D, n_tiles, p.fs, p.fs / p.c, d_gxyz, d_ggain,
-                                           d_gdelay);
+    adj_reduce1_kernel<<<dim3(p.M, kAdjRedBlocks), kAdjRedThreads, 0, st>>>(p.d_adj, p.d_dirs, p.M, p.D, n_tiles,
+                                                                         p.d_adj_red);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    adj_reduce2_kernel<<<1, kMaxMics, 0, st>>>(p.d_adj_red, p.M, p.fs, p.fs / p.c, d_gxyz, d_ggain, d_gdelay);
     return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ cudaError_t dev_alloc(T** ptr, size_t count, size_t* total) {
 
 void free_plan_buffers(Plan& p) {
     void* bufs[] = {p.d_mic, p.d_dirs, p.d_gain, p.d_delay, p.d_tw, p.d_C, p.d_h,
-                    p.d_shift, p.d_wt, p.d_dphase, p.d_wraw, p.d_wder, p.d_adj, p.d_Z, p.d_a, p.d_A, p.d_a16,
+                    p.d_shift, p.d_wt, p.d_dphase, p.d_wraw, p.d_wder, p.d_adj, p.d_adj_red, p.d_Z, p.d_a, p.d_A, p.d_a16,
                     p.d_status};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -301,6 +301,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     // adjoint partials [range tiles][D][M]; also the loss's per-block partials (<= 1024 floats)
     RTIS_ALLOC(p.d_adj, std::max<size_t>(512, static_cast<size_t>((p.n_out + p.td_bins_per_tile - 1) /
                                                                    p.td_bins_per_tile) * n_dirs * n_mics))
+    RTIS_ALLOC(p.d_adj_red, static_cast<size_t>(n_mics) * 16 * 5)
     RTIS_ALLOC(p.d_A, static_cast<size_t>(n_mics) * p.Kb)
     RTIS_ALLOC(p.d_Z, static_cast<size_t>(n_mics) * 2 * p.P)
     RTIS_ALLOC(p.d_a, static_cast<size_t>(n_mics) * n_samples)

@@ -53,6 +53,7 @@ struct Plan {
     float4* d_wraw = nullptr;   // [D][M] Catmull-Rom weights without the gain (adjoint)
     float4* d_wder = nullptr;   // [D][M] their slopes d/dmu (adjoint)
     float2* d_adj = nullptr;    // [range tiles][D][M] adjoint partials (d/d delta, d/d gain)
+    float* d_adj_red = nullptr; // [M][16][5] first-stage sums of the adjoint reduction
     // device workspaces (owned)
     float2* d_Z = nullptr;      // [M][2][P] half-size spectra
     float2* d_a = nullptr;      // [M][N] analytic matched-filter output
