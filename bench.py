@@ -578,31 +578,70 @@ def main():
     assert bits == 0, f"device status {bits:#x}"
 
     # end to end through the public calls: pinned host input -> device -> both
-    # energyscapes -> pinned host
+    # energyscapes -> pinned host, every step.  Copies run on their own streams
+    # (input, and one per energyscape) and two buffer sets alternate, so the
+    # copies of one measurement overlap the beamforming of the next; events
+    # order each buffer's reuse.
+    # both on pool streams: work on the legacy default stream would serialise with the copies
+    hs = torch.cuda.Stream(device=dev)   # input copies
+    cs = torch.cuda.Stream(device=dev)   # output copies (one stream per energyscape)
+    cs2 = torch.cuda.Stream(device=dev)
+    ks = torch.cuda.Stream(device=dev)
+    ksh = ks.cuda_stream
     xh = torch.from_numpy(cfg["x"]).pin_memory()
-    Eh_td = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32).pin_memory()
-    Eh_fd = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32).pin_memory()
-    xd = torch.empty_like(x)
+    Eh_td = [torch.empty((N_DIRS, plan.n_out), dtype=torch.float32).pin_memory() for _ in range(2)]
+    Eh_fd = [torch.empty((N_DIRS, plan.n_out), dtype=torch.float32).pin_memory() for _ in range(2)]
+    xd = [torch.empty_like(x) for _ in range(2)]
+    Ed_td = [E_td, torch.empty_like(E_td)]
+    Ed_fd = [E_fd, torch.empty_like(E_fd)]
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    ev_out2 = [torch.cuda.Event() for _ in range(2)]
+    ks.wait_stream(stream)
+    for e in ev_done + ev_out + ev_out2:
+        e.record(ks)
 
-    def e2e_step():
-        xd.copy_(xh, non_blocking=True)
-        nat.rtis_matched_filter(h, xd, a, A, sh)
-        nat.rtis_beamform_td(h, a, E_td, sh)
-        nat.rtis_beamform_fd(h, A, E_fd, sh)
-        Eh_td.copy_(E_td, non_blocking=True)
-        Eh_fd.copy_(E_fd, non_blocking=True)
+    def e2e_step(i):
+        b = i & 1
+        hs.wait_event(ev_done[b])  # the beamforming that last read xd[b] has finished
+        with torch.cuda.stream(hs):
+            xd[b].copy_(xh, non_blocking=True)
+        ev_in[b].record(hs)
+        ks.wait_event(ev_in[b])
+        ks.wait_event(ev_out[b])  # the copies that last read Ed_*[b] have finished
+        ks.wait_event(ev_out2[b])
+        nat.rtis_matched_filter(h, xd[b], a, A, ksh)
+        nat.rtis_beamform_td(h, a, Ed_td[b], ksh)
+        nat.rtis_beamform_fd(h, A, Ed_fd[b], ksh)
+        ev_done[b].record(ks)
+        cs.wait_event(ev_done[b])
+        cs2.wait_event(ev_done[b])
+        with torch.cuda.stream(cs):
+            Eh_td[b].copy_(Ed_td[b], non_blocking=True)
+        with torch.cuda.stream(cs2):
+            Eh_fd[b].copy_(Ed_fd[b], non_blocking=True)
+        ev_out[b].record(cs)
+        ev_out2[b].record(cs2)
 
-    for _ in range(3):
-        e2e_step()
+    for i in range(4):
+        e2e_step(i)
     torch.cuda.synchronize()
     ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_steps = max(args.steps // 2, 3)
-    ee0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    ee1.record(stream)
+    ee0.record(ks)
+    for c in (hs, cs, cs2):
+        c.wait_event(ee0)
+    for i in range(e2e_steps):
+        e2e_step(i)
+    for e in ev_out + ev_out2:
+        ks.wait_event(e)
+    ee1.record(ks)
     torch.cuda.synchronize()
     t_e2e = ee0.elapsed_time(ee1) / 1e3
+    # every step beamforms the same measurement, so each host copy must equal the device result
+    ref_td, ref_fd = Ed_td[0].cpu(), Ed_fd[0].cpu()
+    assert all(torch.equal(hb, ref_td) for hb in Eh_td) and all(torch.equal(hb, ref_fd) for hb in Eh_fd)
 
     if world > 1:
         t_total, t_e2e = max_over_ranks([t_total, t_e2e], dev)
@@ -651,7 +690,8 @@ def main():
                    "parallelism": f"{world} independent replica(s), one measurement per rank per step"},
         "e2e": {"value": e2e_value, "unit": "energyscapes/s", "h2d_bytes_per_step": int(x.numel() * 2),
                 "d2h_bytes_per_step": int(E_td.numel() * 4 + E_fd.numel() * 4),
-                "calls": "rtis_matched_filter, rtis_beamform_td, rtis_beamform_fd"},
+                "calls": "rtis_matched_filter, rtis_beamform_td, rtis_beamform_fd",
+                "pipelining": "H2D and D2H on their own streams, two buffer sets; copies overlap the next step"},
         "gpu_launches": 4 * args.steps,
         "kernels_ms": {"matched_filter": statistics.mean(mf_ms), "td_beamform": statistics.mean(td_ms),
                        "fd_energyscape": statistics.mean(fd_ms)},
