@@ -65,6 +65,21 @@ typedef enum rtis_status {
 /* Device status-word bits reported by rtis_plan_sync(). */
 #define RTIS_DEV_DELAY_RANGE 0x1u   /* |floor(delta)| beyond the plan's staged halo */
 #define RTIS_DEV_TIMEOUT     0x2u   /* a bounded mbarrier wait ran out */
+#define RTIS_DEV_NONFINITE   0x4u   /* an energyscape value came out NaN or infinite */
+
+/*
+ * Host-side fault injection (testing the error paths; nothing faults the GPU).
+ * The environment variable RTIS_FAULT, read at each call, selects:
+ *   "alloc"   -- rtis_plan_create, rtis_batch_create and rtis_fd_gemm_create
+ *                fail with RTIS_ERR_OOM before allocating anything;
+ *   "launch"  -- the entry points that launch kernels fail with RTIS_ERR_CUDA
+ *                before launching anything;
+ *   "stall"   -- the time-domain beamformer withholds the first TMA copy of
+ *                each CTA and waits for it with a short bound (thousands of
+ *                polls): every CTA gives up, sets RTIS_DEV_TIMEOUT, lets its
+ *                other copies land and returns; the next sync reports
+ *                RTIS_ERR_TIMEOUT and the context stays usable.
+ */
 
 enum { RTIS_PATH_TD = 0, RTIS_PATH_FD = 1 };
 enum { RTIS_PREC_FP32 = 0, RTIS_PREC_BF16 = 1, RTIS_PREC_FP16 = 2 };

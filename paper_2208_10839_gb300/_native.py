@@ -25,6 +25,7 @@ RTIS_ERR_NONFINITE = 6
 RTIS_ERR_DEVICE = 7
 RTIS_DEV_DELAY_RANGE = 0x1
 RTIS_DEV_TIMEOUT = 0x2
+RTIS_DEV_NONFINITE = 0x4
 RTIS_PATH_TD, RTIS_PATH_FD = 0, 1
 RTIS_PREC_FP32, RTIS_PREC_BF16, RTIS_PREC_FP16 = 0, 1, 2
 
@@ -289,9 +290,9 @@ def rtis_loss_l2(plan, d_E, d_E_ref, d_grad_out, d_loss, stream=None):
 def rtis_plan_sync(plan) -> int:
     bits = C.c_uint(0)
     st = lib().rtis_plan_sync(plan, C.byref(bits))
-    if st not in (RTIS_OK, RTIS_ERR_DEVICE, RTIS_ERR_TIMEOUT):
+    if st not in (RTIS_OK, RTIS_ERR_DEVICE, RTIS_ERR_TIMEOUT, RTIS_ERR_NONFINITE):
         check(st, "rtis_plan_sync")
-    return bits.value
+    return bits.value  # device status bits (RTIS_DEV_*); 0 when all went well
 
 
 def rtis_status_string(status: int) -> str:

@@ -34,7 +34,8 @@
 namespace rtis {
 namespace {
 
-constexpr uint32_t kWaitPolls = 1u << 22;  // bounded mbarrier wait (~ seconds)
+constexpr uint32_t kWaitPolls = 1u << 22;   // bounded mbarrier wait (~ seconds)
+constexpr uint32_t kStallPolls = 1u << 12;  // the injected-stall test's short bound
 
 __global__ void steering_table_kernel(const float* __restrict__ mic, const float* __restrict__ dirs,
                                       const float* __restrict__ gain, const float* __restrict__ delay_s,
@@ -200,6 +201,8 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
 
     int g0 = 0;  // stages consumed by this CTA before the current tile
     bool timed_out = false;
+    const uint32_t polls = bt.stall ? kStallPolls : kWaitPolls;
+    bool first_tile = true;
     for (int tile = blockIdx.x; tile < bt.total_tiles; tile += gridDim.x) {
         int si = 0;
         while (si + 1 < bt.n_sensors && tile >= bt.s[si + 1].tile_base) ++si;
@@ -232,8 +235,10 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
         __syncthreads();  // the previous tile's epilogue is done with the stage buffers and taps
         if (threadIdx.x == 0) {
             ptx::prefetch_tmap(tmap);
-            for (int st = 0; st < NS && st < nstages; ++st) issue(st);
+            for (int st = 0; st < NS && st < nstages; ++st)
+                if (!(bt.stall && first_tile && st == 0)) issue(st);  // injected stall: withhold one copy
         }
+        first_tile = false;
         for (int j = threadIdx.x; j < S.lpf_len; j += NT) hs[j] = S.h[j];
 
         // lane m of each warp holds the steering entry of mic m for this warp's direction
@@ -254,12 +259,13 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
             const int b = (g0 + st) % NS;
             if (!timed_out) {
                 const uint32_t par = static_cast<uint32_t>(((g0 + st) / NS) & 1);
-                if (!ptx::mbar_wait_bounded(&bar[b], par, kWaitPolls)) {
+                if (!ptx::mbar_wait_bounded(&bar[b], par, polls)) {
                     timed_out = true;
                     atomicOr(bt.status, RTIS_DEV_TIMEOUT);
                 }
             }
-            if (dir_ok && !__any_sync(0xffffffffu, timed_out)) {
+            const bool warp_timed_out = __any_sync(0xffffffffu, timed_out);
+            if (dir_ok && !warp_timed_out) {
 #pragma unroll 1
                 for (int mi = 0; mi < MS; ++mi) {
                     const int m = st * MS + mi;
@@ -294,7 +300,7 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
                 if (prev == kTdDirsPerCta - 1) {
                     done[b] = 0;
                     __threadfence_block();
-                    if (st + NS < nstages) {
+                    if (st + NS < nstages && !warp_timed_out) {  // no refills once a wait has given up
                         ptx::fence_proxy_async();
                         issue(st + NS);
                     }
@@ -322,6 +328,7 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
                 const float* e = env + S.R * il;
                 float acc_e = 0.f;
                 for (int j = 0; j < S.lpf_len; ++j) acc_e = fmaf(hs[j], e[j], acc_e);
+                if (!isfinite(acc_e)) atomicOr(bt.status, RTIS_DEV_NONFINITE);
                 Erow[i] = acc_e;
             }
         }
@@ -332,7 +339,7 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
         if (threadIdx.x == 0) {
             for (int b = 0; b < NS; ++b)
                 if (issued[b] > 0)
-                    ptx::mbar_wait_bounded(&bar[b], static_cast<uint32_t>((issued[b] - 1) & 1), kWaitPolls);
+                    ptx::mbar_wait_bounded(&bar[b], static_cast<uint32_t>((issued[b] - 1) & 1), polls);
         }
         __syncthreads();
     }
@@ -468,6 +475,7 @@ cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, bool bf16
     TdBatch bt;
     std::memset(&bt, 0, sizeof(bt));
     bt.bf16 = bf16 ? 1 : 0;
+    bt.stall = (fault_mode() == kFaultStall) ? 1 : 0;
     td_fill_sensor(p, d_out, 0, &bt.s[0]);
     bt.n_sensors = 1;
     bt.total_tiles = td_tiles(p);

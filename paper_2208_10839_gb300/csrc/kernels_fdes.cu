@@ -38,6 +38,7 @@ struct FdesArgs {
     const float2* tw;     // [F]
     const float* h;       // [lpf_len]
     float* E;             // [D][n_out]
+    unsigned* status;
     int M, D, N, F, k_lo, Kb, R, lpf_len, n_out;
 };
 
@@ -269,7 +270,11 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
         __syncthreads();
     }
     float* Erow = a.E + static_cast<size_t>(d) * a.n_out;
-    for (int i = tid; i < a.n_out; i += kFdesThreads) Erow[i] = Eacc[i];
+    for (int i = tid; i < a.n_out; i += kFdesThreads) {
+        const float e = Eacc[i];
+        if (!isfinite(e)) atomicOr(a.status, RTIS_DEV_NONFINITE);
+        Erow[i] = e;
+    }
 }
 
 template <int LOGP>
@@ -294,6 +299,7 @@ cudaError_t fdes_launch_t(const Plan& p, const float2* d_A, float* d_out, cudaSt
     a.R = p.R;
     a.lpf_len = p.lpf_len;
     a.n_out = p.n_out;
+    a.status = p.d_status;
     fd_energyscape_kernel<LOGP><<<p.D, kFdesThreads, sm, st>>>(a);
     return cudaGetLastError();
 }

@@ -70,6 +70,7 @@ extern "C" rtis_status rtis_matched_filter_noalloc(const int16_t* d_in, int n_mi
                                                    const float* d_chirp, int chirp_len, double fs,
                                                    double band_lo_hz, double band_hi_hz, float* d_a,
                                                    float* d_A, void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_matched_filter_noalloc: injected launch failure");
     using namespace rtis;
     if (!d_in || !d_chirp) return fail(RTIS_ERR_INVALID_ARG, "rtis_matched_filter_noalloc: NULL input");
     if (!d_a && !d_A) return fail(RTIS_ERR_INVALID_ARG, "rtis_matched_filter_noalloc: no output requested");

@@ -3,6 +3,7 @@
 // launch sequence of each entry point.  No C++ exception leaves this file.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -41,6 +42,15 @@ bool aligned(const void* ptr, size_t a) { return (reinterpret_cast<uintptr_t>(pt
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fault_mode() {
+    const char* f = std::getenv("RTIS_FAULT");
+    if (!f || !*f) return kFaultNone;
+    if (!std::strcmp(f, "alloc")) return kFaultAlloc;
+    if (!std::strcmp(f, "launch")) return kFaultLaunch;
+    if (!std::strcmp(f, "stall")) return kFaultStall;
+    return kFaultNone;
+}
 
 rtis_status fail(rtis_status s, const std::string& msg) {
     set_error(msg);
@@ -190,6 +200,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: band must lie below fs/4");
     if (n_samples / opt.decim < 1) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: decim larger than N");
 
+    if (rtis::fault_mode() == rtis::kFaultAlloc) return fail(RTIS_ERR_OOM, "rtis_plan_create: injected allocation failure");
     rtis_plan* plan = new (std::nothrow) rtis_plan();
     if (!plan) return fail(RTIS_ERR_OOM, "rtis_plan_create: host allocation failed");
     Plan& p = plan->p;
@@ -411,6 +422,7 @@ static rtis_status ensure_table(Plan& p, cudaStream_t st) {
 }
 
 rtis_status rtis_matched_filter(rtis_plan* plan, const int16_t* d_in, float* d_a, float* d_A, void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_matched_filter: injected launch failure");
     if (!plan || !d_in) return fail(RTIS_ERR_INVALID_ARG, "rtis_matched_filter: NULL plan or input");
     if (!rtis::aligned(d_in, 8)) return fail(RTIS_ERR_INVALID_ARG, "rtis_matched_filter: d_in must be 8-byte aligned");
     if ((d_a && !rtis::aligned(d_a, 8)) || (d_A && !rtis::aligned(d_A, 8)))
@@ -425,6 +437,7 @@ rtis_status rtis_matched_filter(rtis_plan* plan, const int16_t* d_in, float* d_a
 }
 
 rtis_status rtis_beamform_td(rtis_plan* plan, const float* d_a, float* d_out, void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_beamform_td: injected launch failure");
     if (!plan || !d_a || !d_out) return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_td: NULL argument");
     if (!rtis::aligned(d_a, 16)) return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_td: d_a must be 16-byte aligned");
     if (!rtis::aligned(d_out, 4)) return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_td: d_out must be 4-byte aligned");
@@ -441,6 +454,7 @@ rtis_status rtis_beamform_td(rtis_plan* plan, const float* d_a, float* d_out, vo
 }
 
 rtis_status rtis_process(rtis_plan* plan, const int16_t* d_in, float* d_out, void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_process: injected launch failure");
     if (!plan || !d_in || !d_out) return fail(RTIS_ERR_INVALID_ARG, "rtis_process: NULL argument");
     if (!rtis::aligned(d_in, 8)) return fail(RTIS_ERR_INVALID_ARG, "rtis_process: d_in must be 8-byte aligned");
     if (!rtis::aligned(d_out, 4)) return fail(RTIS_ERR_INVALID_ARG, "rtis_process: d_out must be 4-byte aligned");
@@ -465,6 +479,7 @@ rtis_status rtis_process(rtis_plan* plan, const int16_t* d_in, float* d_out, voi
 }
 
 rtis_status rtis_beamform_fd(rtis_plan* plan, const float* d_A, float* d_out, void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_beamform_fd: injected launch failure");
     if (!plan || !d_A || !d_out) return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_fd: NULL argument");
     if (!rtis::aligned(d_A, 8) || !rtis::aligned(d_out, 4))
         return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_fd: d_A must be 8-byte aligned");
@@ -479,6 +494,7 @@ rtis_status rtis_beamform_fd(rtis_plan* plan, const float* d_A, float* d_out, vo
 }
 
 rtis_status rtis_steering_table(rtis_plan* plan, int32_t* d_shift, float* d_weight, void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_steering_table: injected launch failure");
     if (!plan || !d_shift || !d_weight) return fail(RTIS_ERR_INVALID_ARG, "rtis_steering_table: NULL argument");
     if (!rtis::aligned(d_weight, 16) || !rtis::aligned(d_shift, 4))
         return fail(RTIS_ERR_INVALID_ARG, "rtis_steering_table: d_weight must be 16-byte aligned");
@@ -495,6 +511,7 @@ rtis_status rtis_steering_table(rtis_plan* plan, int32_t* d_shift, float* d_weig
 rtis_status rtis_fd_gemm_create(rtis_fd_gemm** out, const float* mic_xyz, int n_mics, const float* directions,
                                 int n_dirs, const double* freqs_hz, int n_bins, int n_frames, double c,
                                 const float* gain, const float* delay_s, int precision) {
+    if (rtis::fault_mode() == rtis::kFaultAlloc) return rtis::fail(RTIS_ERR_OOM, "rtis_fd_gemm_create: injected allocation failure");
     if (!out) return fail(RTIS_ERR_INVALID_ARG, "rtis_fd_gemm_create: out is NULL");
     *out = nullptr;
     if (!mic_xyz || !directions || !freqs_hz)
@@ -567,6 +584,7 @@ rtis_status rtis_fd_gemm_create(rtis_fd_gemm** out, const float* mic_xyz, int n_
 }
 
 rtis_status rtis_fd_gemm_run(rtis_fd_gemm* plan, const float* d_X, float* d_Y, void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_fd_gemm_run: injected launch failure");
     if (!plan || !d_X || !d_Y) return fail(RTIS_ERR_INVALID_ARG, "rtis_fd_gemm_run: NULL argument");
     if (!rtis::aligned(d_X, 8) || !rtis::aligned(d_Y, 16))
         return fail(RTIS_ERR_INVALID_ARG, "rtis_fd_gemm_run: d_X must be 8-byte and d_Y 16-byte aligned");
@@ -596,6 +614,7 @@ void rtis_fd_gemm_destroy(rtis_fd_gemm* plan) {
 
 rtis_status rtis_set_calibration(rtis_plan* plan, const float* d_mic_xyz, const float* d_gain, const float* d_delay_s,
                                  void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_set_calibration: injected launch failure");
     if (!plan) return fail(RTIS_ERR_INVALID_ARG, "rtis_set_calibration: NULL plan");
     Plan& p = plan->p;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -611,6 +630,7 @@ rtis_status rtis_set_calibration(rtis_plan* plan, const float* d_mic_xyz, const 
 
 rtis_status rtis_backward(rtis_plan* plan, const int16_t* d_in, const float* d_grad_out, float* d_grad_xyz,
                           float* d_grad_gain, float* d_grad_delay, void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_backward: injected launch failure");
     if (!plan || !d_in || !d_grad_out) return fail(RTIS_ERR_INVALID_ARG, "rtis_backward: NULL argument");
     if (!d_grad_xyz && !d_grad_gain && !d_grad_delay)
         return fail(RTIS_ERR_INVALID_ARG, "rtis_backward: no gradient requested");
@@ -635,6 +655,7 @@ rtis_status rtis_backward(rtis_plan* plan, const int16_t* d_in, const float* d_g
 
 rtis_status rtis_loss_l2(rtis_plan* plan, const float* d_E, const float* d_E_ref, float* d_grad_out, float* d_loss,
                          void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_loss_l2: injected launch failure");
     if (!plan || !d_E || !d_E_ref || !d_loss) return fail(RTIS_ERR_INVALID_ARG, "rtis_loss_l2: NULL argument");
     cudaError_t e = rtis::launch_l2_loss(plan->p, d_E, d_E_ref, d_grad_out, d_loss, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_loss_l2: launch");
@@ -653,6 +674,8 @@ rtis_status rtis_plan_sync(rtis_plan* plan, unsigned* bits_out) {
     if (bits & RTIS_DEV_TIMEOUT) return fail(RTIS_ERR_TIMEOUT, "rtis_plan_sync: a bounded device wait ran out");
     if (bits & RTIS_DEV_DELAY_RANGE)
         return fail(RTIS_ERR_DEVICE, "rtis_plan_sync: a steering delay exceeded the staged halo");
+    if (bits & RTIS_DEV_NONFINITE)
+        return fail(RTIS_ERR_NONFINITE, "rtis_plan_sync: an energyscape value was NaN or infinite");
     return RTIS_OK;
 }
 

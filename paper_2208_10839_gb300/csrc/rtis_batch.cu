@@ -124,6 +124,7 @@ rtis_status build_tables(rtis_plan* const* plans, int n, rtis::TdMaps* maps, rti
     }
     bt->n_sensors = n;
     bt->bf16 = plans[0]->p.a_bf16 ? 1 : 0;
+    bt->stall = 0;  // set per run (fault injection)
     bt->total_tiles = tiles;
     bt->row_max = row_max;
     bt->lpf_max = lpf_max;
@@ -143,6 +144,7 @@ void drop_graph(rtis_batch* b) {
 extern "C" {
 
 rtis_status rtis_batch_create(rtis_batch** out, rtis_plan* const* plans, int n) {
+    if (rtis::fault_mode() == rtis::kFaultAlloc) return rtis::fail(RTIS_ERR_OOM, "rtis_batch_create: injected allocation failure");
     if (!out) return fail(RTIS_ERR_INVALID_ARG, "rtis_batch_create: out is NULL");
     *out = nullptr;
     rtis_batch* b = new (std::nothrow) rtis_batch();
@@ -184,6 +186,7 @@ void rtis_batch_destroy(rtis_batch* b) {
 }
 
 rtis_status rtis_batch_run(rtis_batch* b, const int16_t* const* d_in, float* const* d_out, void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_batch_run: injected launch failure");
     if (!b) return fail(RTIS_ERR_INVALID_ARG, "rtis_batch_run: NULL batch");
     rtis_status s = validate_io(b, d_in, d_out, "rtis_batch_run");
     if (s != RTIS_OK) return s;
@@ -254,6 +257,7 @@ rtis_status rtis_batch_sync(rtis_batch* b, unsigned* bits_out) {
 
 rtis_status rtis_process_batch(rtis_plan* const* plans, int n, const int16_t* const* d_in, float* const* d_out,
                                void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_process_batch: injected launch failure");
     // allocation-free: a stack-built tile table, plain launches on the caller's stream
     rtis_batch b;
     rtis_status s = build_tables(plans, n, &b.maps, &b.bt);

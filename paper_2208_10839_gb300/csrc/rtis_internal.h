@@ -90,6 +90,9 @@ bool fd_gemm_encode_ymap(const FdGemmPlan& g, float2* d_Y, CUtensorMap* map, std
 // error reporting (thread-local last message)
 // ----------------------------------------------------------------------------
 void set_error(const std::string& msg);
+// host fault injection (RTIS_FAULT): 0 none, 1 alloc, 2 launch, 3 stall
+enum { kFaultNone = 0, kFaultAlloc = 1, kFaultLaunch = 2, kFaultStall = 3 };
+int fault_mode();
 rtis_status fail(rtis_status s, const std::string& msg);
 rtis_status cuda_fail(cudaError_t e, const char* what);
 
@@ -122,6 +125,7 @@ struct TdBatch {
     TdSensor s[kTdMaxSensors];
     int n_sensors, total_tiles, row_max, lpf_max;
     int bf16;  // the staged rows are BF16 (re, im) pairs, 4 bytes per sample
+    int stall;  // fault injection: withhold each CTA's first copy and wait for it briefly
     unsigned* status;
 };
 struct TdMaps {

@@ -110,3 +110,19 @@ def test_null_arguments(nat):
     assert lib.rtis_plan_sync(None, None) == nat.RTIS_ERR_INVALID_ARG
     lib.rtis_plan_destroy(None)
     assert nat.rtis_status_string(0) == "ok"
+
+
+def test_injected_allocation_and_launch_failures(nat, monkeypatch):
+    """RTIS_FAULT forces the host error paths without touching the GPU."""
+    mic, ch, dirs = _args()
+    monkeypatch.setenv("RTIS_FAULT", "alloc")
+    with pytest.raises(nat.RtisError) as ei:
+        nat.rtis_plan_create(mic, 450e3, ch, dirs, 4096, nat.default_options())
+    assert ei.value.status == nat.RTIS_ERR_OOM and "injected" in nat.last_error()
+    monkeypatch.setenv("RTIS_FAULT", "launch")
+    lib = nat.lib()
+    assert lib.rtis_process(None, None, None, None) == nat.RTIS_ERR_CUDA
+    assert "injected" in nat.last_error()
+    assert lib.rtis_backward(None, None, None, None, None, None, None) == nat.RTIS_ERR_CUDA
+    monkeypatch.setenv("RTIS_FAULT", "")
+    assert lib.rtis_process(None, None, None, None) == nat.RTIS_ERR_INVALID_ARG
