@@ -98,6 +98,8 @@ typedef struct rtis_options {
                                     stay FP32).  The FD path takes FP32 only. */
     double max_delay_s;          /* bound on |Delta_m| set by calibration (default 10e-6) */
     double position_slack_m;     /* bound on calibrated mic displacement (default 0.01) */
+    int max_batch;               /* most measurements one rtis_process_many call takes through
+                                    the batched FD GEMM (0: none, <= 64); sizes its buffers */
 } rtis_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -152,6 +154,24 @@ rtis_status rtis_plan_get_info(const rtis_plan* plan, rtis_plan_info* info);
  *   d_out  device float [n_dirs][n_out]
  */
 rtis_status rtis_process(rtis_plan* plan, const int16_t* d_in, float* d_out, void* stream);
+
+/*
+ * rtis_process_many -- the whole chain for n measurements of the plan's
+ * geometry, d_in [n][n_mics][n_samples], one matched filter per measurement
+ * feeding either or both delay-and-sum forms:
+ *   d_out_td  [n][n_dirs][n_out]: time-domain energyscapes (or NULL);
+ *   d_out_fd  [n][n_dirs][n_out]: frequency-domain energyscapes (or NULL;
+ *             needs n <= opt.max_batch and F <= 32768).
+ * The frequency-domain delay-and-sum of all n runs as ONE batched complex
+ * GEMM on the tensor cores (the phase-ramp form of Fig. 3 / Sec. 4.1 with the
+ * measurements as frames: Y[d][k][t] = sum_m g_m e^{+2 pi i k delta_dm/F} A_m^t[k],
+ * FP32 operands as three BF16 products), followed by the per-direction phase
+ * IFFTs, envelope, low-pass and subsampling of each measurement.  Results
+ * match rtis_process to the FP32 energyscape tolerance.
+ *   d_in   device int16, 8-byte aligned
+ */
+rtis_status rtis_process_many(rtis_plan* plan, const int16_t* d_in, int n, float* d_out_td, float* d_out_fd,
+                              void* stream);
 
 /*
  * rtis_matched_filter -- the matched-filter stage alone (Sec. 4.1/4.3).

@@ -42,6 +42,7 @@ class rtis_options(C.Structure):
         ("precision", C.c_int),
         ("max_delay_s", C.c_double),
         ("position_slack_m", C.c_double),
+        ("max_batch", C.c_int),
     ]
 
 
@@ -74,6 +75,7 @@ _PROTOS = {
     "rtis_plan_destroy": (None, [_VP]),
     "rtis_plan_get_info": (C.c_int, [_VP, C.POINTER(rtis_plan_info)]),
     "rtis_process": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "rtis_process_many": (C.c_int, [_VP, _VP, C.c_int, _VP, _VP, _VP]),
     "rtis_matched_filter": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "rtis_beamform_td": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_beamform_fd": (C.c_int, [_VP, _VP, _VP, _VP]),
@@ -179,6 +181,11 @@ def rtis_plan_get_info(plan) -> rtis_plan_info:
 
 def rtis_process(plan, d_in, d_out, stream=None):
     check(lib().rtis_process(plan, ptr(d_in), ptr(d_out), stream_handle(stream)), "rtis_process")
+
+
+def rtis_process_many(plan, d_in, n, d_out_td=None, d_out_fd=None, stream=None):
+    check(lib().rtis_process_many(plan, ptr(d_in), int(n), ptr(d_out_td), ptr(d_out_fd), stream_handle(stream)),
+          "rtis_process_many")
 
 
 def rtis_matched_filter(plan, d_in, d_a, d_A=None, stream=None):

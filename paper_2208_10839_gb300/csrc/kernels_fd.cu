@@ -59,6 +59,7 @@ struct FdArgs {
     int n_items;          // direction tiles x bins, item = tile * K + k
     int bulk_x;           // X rows of one bin fetched by one bulk copy (M*T*8 % 16 == 0)
     int tma_y;            // Y written by TMA tensor stores (T even)
+    int y_dkt;            // Y laid out [D][K][T] instead of [K][D][T]
 };
 
 __device__ __forceinline__ uint32_t kmajor_off(int r, int kc) {
@@ -317,13 +318,17 @@ __global__ void __launch_bounds__(kFdThreads, 1)
                     ptx::fence_proxy_async();
                     __syncwarp();
                     if (lane == 0) {
-                        ptx::tma_store_3d(&ymap, stg, 32 * h, ptile * kFdDirTile + 32 * q, pk);
+                        if (args.y_dkt)
+                            ptx::tma_store_3d(&ymap, stg, 32 * h, pk, ptile * kFdDirTile + 32 * q);
+                        else
+                            ptx::tma_store_3d(&ymap, stg, 32 * h, ptile * kFdDirTile + 32 * q, pk);
                         ptx::bulk_commit();
                     }
                 } else {
                     const int d = ptile * kFdDirTile + row;
                     if (d < D) {
-                        float2* dst = args.Y + (static_cast<size_t>(pk) * D + d) * T;
+                        float2* dst = args.Y + (args.y_dkt ? (static_cast<size_t>(d) * K + pk)
+                                                           : (static_cast<size_t>(pk) * D + d)) * T;
 #pragma unroll
                         for (int c = 0; c < 16; ++c) {
                             const int t = 16 * h + c;
@@ -405,6 +410,14 @@ cudaError_t fd_launch_t(const CUtensorMap& ymap, const FdArgs& a, int grid, cuda
 }  // namespace
 
 bool fd_gemm_encode_ymap(const FdGemmPlan& g, float2* d_Y, CUtensorMap* map, std::string* err) {
+    if (g.y_dkt) {
+        // Y as float32 [D][K][2T]; box = 32 floats (128 B) x 1 bin x 32 directions, 128B swizzle
+        uint64_t dims[3] = {static_cast<uint64_t>(2 * g.T), static_cast<uint64_t>(g.K), static_cast<uint64_t>(g.D)};
+        uint64_t strides[2] = {static_cast<uint64_t>(g.T) * 8, static_cast<uint64_t>(g.K) * g.T * 8};
+        uint32_t box[3] = {32, 1, 32};
+        return encode_tmap(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, d_Y, dims, strides, box,
+                           CU_TENSOR_MAP_SWIZZLE_128B, err);
+    }
     // Y as float32 [K][D][2T]; box = 32 floats (128 B) x 32 directions x 1 bin, 128B swizzle
     uint64_t dims[3] = {static_cast<uint64_t>(2 * g.T), static_cast<uint64_t>(g.D), static_cast<uint64_t>(g.K)};
     uint64_t strides[2] = {static_cast<uint64_t>(g.T) * 8, static_cast<uint64_t>(g.D) * g.T * 8};
@@ -438,6 +451,7 @@ cudaError_t launch_fd_gemm(const FdGemmPlan& g, const float2* d_X, float2* d_Y, 
     a.n_items = n_tiles * g.K;
     a.bulk_x = ((static_cast<size_t>(g.M) * g.T * 8) % 16 == 0 && reinterpret_cast<uintptr_t>(d_X) % 16 == 0) ? 1 : 0;
     a.tma_y = ymap != nullptr ? 1 : 0;
+    a.y_dkt = g.y_dkt;
     CUtensorMap dummy;
     std::memset(&dummy, 0, sizeof(dummy));
     const CUtensorMap& ym = ymap ? *ymap : dummy;

@@ -37,7 +37,9 @@ struct FdesArgs {
     const float* gain;    // [M]
     const float2* tw;     // [F]
     const float* h;       // [lpf_len]
-    float* E;             // [D][n_out]
+    float* E;             // [D][n_out], or [T][D][n_out] from Y
+    const float2* Y;      // [D][Kb][T] steered spectra (from-Y variant)
+    int T;
     unsigned* status;
     int M, D, N, F, k_lo, Kb, R, lpf_len, n_out;
 };
@@ -175,7 +177,10 @@ __device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const Split
     __syncthreads();
 }
 
-template <int LOGP>
+// FROM_Y: the steered spectra come from the batched GEMM (Y[d][k'][t]); CTA b
+// handles direction b / T of measurement b % T (neighbouring measurements share
+// Y's sectors and run side by side).  Otherwise the CTA steers direction b itself.
+template <int LOGP, bool FROM_Y>
 __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const FdesArgs a) {
     constexpr int P = 1 << LOGP;
     extern __shared__ __align__(16) unsigned char sm[];
@@ -189,7 +194,8 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
     float* hs = reinterpret_cast<float*>(sm + L.hs);
     float* gs = reinterpret_cast<float*>(sm + L.gs);
 
-    const int d = blockIdx.x;
+    const int d = FROM_Y ? static_cast<int>(blockIdx.x) / a.T : static_cast<int>(blockIdx.x);
+    const int t_meas = FROM_Y ? static_cast<int>(blockIdx.x) - d * a.T : 0;
     const int tid = threadIdx.x;
     const int M = a.M, Kb = a.Kb;
     for (int j = tid; j < 256; j += kFdesThreads) twlo[j] = __ldg(a.tw + j);
@@ -206,29 +212,35 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
     __syncthreads();
     const SplitTwiddles tws{twhi, twlo};
 
-    // ---- steered spectrum B_d ------------------------------------------------
-    // slots of 256 bins: full chunks of kFdesChunk slots, then the tail in chunks
-    // of 8, 4, 2, 1 so that no thread advances the recurrence past the band
-    const float2* dph = a.dphase + static_cast<size_t>(d) * M;
-    const int nslots = (Kb + kFdesThreads - 1) / kFdesThreads;
-    int c0 = 0;
-    for (; c0 + kFdesChunk <= nslots; c0 += kFdesChunk)
-        fdes_gemv_chunk<kFdesChunk>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
-    static_assert(kFdesChunk == 16, "the tail below covers remainders up to 15 slots");
-    if ((nslots - c0) & 8) {
-        fdes_gemv_chunk<8>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
-        c0 += 8;
+    if constexpr (FROM_Y) {
+        for (int kp = tid; kp < Kb; kp += kFdesThreads)
+            B[kp] = __ldg(a.Y + (static_cast<size_t>(d) * Kb + kp) * a.T + t_meas);
+        __syncthreads();
+    } else {
+        // ---- steered spectrum B_d ------------------------------------------------
+        // slots of 256 bins: full chunks of kFdesChunk slots, then the tail in chunks
+        // of 8, 4, 2, 1 so that no thread advances the recurrence past the band
+        const float2* dph = a.dphase + static_cast<size_t>(d) * M;
+        const int nslots = (Kb + kFdesThreads - 1) / kFdesThreads;
+        int c0 = 0;
+        for (; c0 + kFdesChunk <= nslots; c0 += kFdesChunk)
+            fdes_gemv_chunk<kFdesChunk>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
+        static_assert(kFdesChunk == 16, "the tail below covers remainders up to 15 slots");
+        if ((nslots - c0) & 8) {
+            fdes_gemv_chunk<8>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
+            c0 += 8;
+        }
+        if ((nslots - c0) & 4) {
+            fdes_gemv_chunk<4>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
+            c0 += 4;
+        }
+        if ((nslots - c0) & 2) {
+            fdes_gemv_chunk<2>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
+            c0 += 2;
+        }
+        if ((nslots - c0) & 1) fdes_gemv_chunk<1>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
+        __syncthreads();
     }
-    if ((nslots - c0) & 4) {
-        fdes_gemv_chunk<4>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
-        c0 += 4;
-    }
-    if ((nslots - c0) & 2) {
-        fdes_gemv_chunk<2>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
-        c0 += 2;
-    }
-    if ((nslots - c0) & 1) fdes_gemv_chunk<1>(a, dph, gs, step, B, c0 * kFdesThreads + tid);
-    __syncthreads();
 
     // ---- four phase IFFTs, each folded into the low-pass outputs ------------
     constexpr int R0 = P / kFdesThreads;  // first-pass radix, 1 .. 32
@@ -269,7 +281,7 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
         }
         __syncthreads();
     }
-    float* Erow = a.E + static_cast<size_t>(d) * a.n_out;
+    float* Erow = a.E + (static_cast<size_t>(t_meas) * a.D + d) * a.n_out;
     for (int i = tid; i < a.n_out; i += kFdesThreads) {
         const float e = Eacc[i];
         if (!isfinite(e)) atomicOr(a.status, RTIS_DEV_NONFINITE);
@@ -277,11 +289,11 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
     }
 }
 
-template <int LOGP>
-cudaError_t fdes_launch_t(const Plan& p, const float2* d_A, float* d_out, cudaStream_t st) {
+template <int LOGP, bool FROM_Y>
+cudaError_t fdes_launch_t(const Plan& p, const float2* d_A, const float2* d_Y, int T, float* d_out, cudaStream_t st) {
     const size_t sm = static_cast<size_t>(fdes_layout(1 << LOGP, p.F, p.Kb, p.n_out, p.lpf_len, p.M).bytes);
-    cudaError_t e = cudaFuncSetAttribute(fd_energyscape_kernel<LOGP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(sm));
+    cudaError_t e = cudaFuncSetAttribute(fd_energyscape_kernel<LOGP, FROM_Y>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
     if (e != cudaSuccess) return e;
     FdesArgs a;
     a.A = d_A;
@@ -290,6 +302,8 @@ cudaError_t fdes_launch_t(const Plan& p, const float2* d_A, float* d_out, cudaSt
     a.tw = p.d_tw;
     a.h = p.d_h;
     a.E = d_out;
+    a.Y = d_Y;
+    a.T = T;
     a.M = p.M;
     a.D = p.D;
     a.N = p.N;
@@ -300,8 +314,21 @@ cudaError_t fdes_launch_t(const Plan& p, const float2* d_A, float* d_out, cudaSt
     a.lpf_len = p.lpf_len;
     a.n_out = p.n_out;
     a.status = p.d_status;
-    fd_energyscape_kernel<LOGP><<<p.D, kFdesThreads, sm, st>>>(a);
+    fd_energyscape_kernel<LOGP, FROM_Y><<<p.D * (FROM_Y ? T : 1), kFdesThreads, sm, st>>>(a);
     return cudaGetLastError();
+}
+
+template <bool FROM_Y>
+cudaError_t fdes_dispatch(const Plan& p, const float2* d_A, const float2* d_Y, int T, float* d_out, cudaStream_t st) {
+    switch (p.logP) {
+        case 8: return fdes_launch_t<8, FROM_Y>(p, d_A, d_Y, T, d_out, st);
+        case 9: return fdes_launch_t<9, FROM_Y>(p, d_A, d_Y, T, d_out, st);
+        case 10: return fdes_launch_t<10, FROM_Y>(p, d_A, d_Y, T, d_out, st);
+        case 11: return fdes_launch_t<11, FROM_Y>(p, d_A, d_Y, T, d_out, st);
+        case 12: return fdes_launch_t<12, FROM_Y>(p, d_A, d_Y, T, d_out, st);
+        case 13: return fdes_launch_t<13, FROM_Y>(p, d_A, d_Y, T, d_out, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -312,15 +339,11 @@ size_t fdes_smem_bytes(const Plan& p) {
 }
 
 cudaError_t launch_fd_energyscape(const Plan& p, const float2* d_A, float* d_out, cudaStream_t st) {
-    switch (p.logP) {
-        case 8: return fdes_launch_t<8>(p, d_A, d_out, st);
-        case 9: return fdes_launch_t<9>(p, d_A, d_out, st);
-        case 10: return fdes_launch_t<10>(p, d_A, d_out, st);
-        case 11: return fdes_launch_t<11>(p, d_A, d_out, st);
-        case 12: return fdes_launch_t<12>(p, d_A, d_out, st);
-        case 13: return fdes_launch_t<13>(p, d_A, d_out, st);
-        default: return cudaErrorInvalidValue;
-    }
+    return fdes_dispatch<false>(p, d_A, nullptr, 1, d_out, st);
+}
+
+cudaError_t launch_fd_energyscape_from_y(const Plan& p, const float2* d_Y, int T, float* d_out, cudaStream_t st) {
+    return fdes_dispatch<true>(p, nullptr, d_Y, T, d_out, st);
 }
 
 }  // namespace rtis

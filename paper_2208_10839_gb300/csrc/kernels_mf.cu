@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kMfThreads) mf_inverse_kernel(const float2* __
                                                                 int k_lo, int Kb, int N,
                                                                 float2* __restrict__ a,
                                                                 float2* __restrict__ A_out,
-                                                                uint32_t* __restrict__ a16) {
+                                                                uint32_t* __restrict__ a16, int a_ms, int a_ks) {
     extern __shared__ float2 sbuf[];
     constexpr int P = 1 << LOGP;
     const int m = blockIdx.x, q = blockIdx.y;
@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(kMfThreads) mf_inverse_kernel(const float2* __
             X.x += t1.x + t2.x + t3.x;
             X.y += t1.y + t2.y + t3.y;
             const float2 Av = cmul(X, __ldg(C + kp));
-            if (A_out != nullptr && q == 0) A_out[static_cast<size_t>(m) * Kb + kp] = Av;
+            if (A_out != nullptr && q == 0)
+                A_out[static_cast<size_t>(m) * a_ms + static_cast<size_t>(kp) * a_ks] = Av;
             g = (q == 0) ? Av : cmul(Av, conjf2(__ldg(tw + ((kp * q) & (F - 1)))));
         }
         sbuf[spad(kp)] = g;
@@ -125,14 +126,15 @@ cudaError_t mf_forward_t(const Plan& p, const int16_t* d_in, cudaStream_t st) {
 }
 
 template <int LOGP>
-cudaError_t mf_inverse_t(const Plan& p, float2* d_a, float2* d_A, uint32_t* d_a16, cudaStream_t st) {
+cudaError_t mf_inverse_t(const Plan& p, float2* d_a, float2* d_A, uint32_t* d_a16, int a_ms, int a_ks,
+                         cudaStream_t st) {
     const size_t sm = mf_smem<LOGP>();
     cudaError_t e = cudaFuncSetAttribute(mf_inverse_kernel<LOGP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sm));
     if (e != cudaSuccess) return e;
     const int nq = (d_a || d_a16) ? 4 : 1;
     mf_inverse_kernel<LOGP><<<dim3(p.M, nq), kMfThreads, sm, st>>>(p.d_Z, p.d_C, p.d_tw, p.F, p.k_lo, p.Kb,
-                                                                  p.N, d_a, d_A, d_a16);
+                                                                  p.N, d_a, d_A, d_a16, a_ms, a_ks);
     return cudaGetLastError();
 }
 
@@ -153,17 +155,19 @@ cudaError_t launch_mf_forward(const Plan& p, const int16_t* d_in, cudaStream_t s
     }
 }
 
-cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st, uint32_t* d_a16) {
+cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st, uint32_t* d_a16, int a_ms,
+                              int a_ks) {
+    if (a_ms < 0) a_ms = p.Kb;
     switch (p.logP) {
-        case 6: return mf_inverse_t<6>(p, d_a, d_A, d_a16, st);
-        case 7: return mf_inverse_t<7>(p, d_a, d_A, d_a16, st);
-        case 8: return mf_inverse_t<8>(p, d_a, d_A, d_a16, st);
-        case 9: return mf_inverse_t<9>(p, d_a, d_A, d_a16, st);
-        case 10: return mf_inverse_t<10>(p, d_a, d_A, d_a16, st);
-        case 11: return mf_inverse_t<11>(p, d_a, d_A, d_a16, st);
-        case 12: return mf_inverse_t<12>(p, d_a, d_A, d_a16, st);
-        case 13: return mf_inverse_t<13>(p, d_a, d_A, d_a16, st);
-        case 14: return mf_inverse_t<14>(p, d_a, d_A, d_a16, st);
+        case 6: return mf_inverse_t<6>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
+        case 7: return mf_inverse_t<7>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
+        case 8: return mf_inverse_t<8>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
+        case 9: return mf_inverse_t<9>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
+        case 10: return mf_inverse_t<10>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
+        case 11: return mf_inverse_t<11>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
+        case 12: return mf_inverse_t<12>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
+        case 13: return mf_inverse_t<13>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
+        case 14: return mf_inverse_t<14>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
         default: return cudaErrorInvalidValue;
     }
 }

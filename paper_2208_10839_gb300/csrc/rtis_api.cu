@@ -33,7 +33,7 @@ cudaError_t dev_alloc(T** ptr, size_t count, size_t* total) {
 void free_plan_buffers(Plan& p) {
     void* bufs[] = {p.d_mic, p.d_dirs, p.d_gain, p.d_delay, p.d_tw, p.d_C, p.d_h,
                     p.d_shift, p.d_wt, p.d_dphase, p.d_wraw, p.d_wder, p.d_adj, p.d_adj_red, p.d_Z, p.d_a, p.d_A, p.d_a16,
-                    p.d_status};
+                    p.d_X, p.d_Y, p.d_kbin, p.d_xmax, p.d_status};
     for (void* b : bufs)
         if (b) cudaFree(b);
 }
@@ -182,6 +182,8 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: unknown path");
     if (opt.precision != RTIS_PREC_FP32 && opt.precision != RTIS_PREC_BF16)
         return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: precision must be RTIS_PREC_FP32 or RTIS_PREC_BF16");
+    if (opt.max_batch < 0 || opt.max_batch > rtis::kFdMaxFrames)
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: max_batch must be in [0, 64]");
     if (opt.precision == RTIS_PREC_BF16 && opt.path != RTIS_PATH_TD)
         return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: BF16 storage applies to the time-domain path only");
     if (!rtis::all_finite(mic_xyz, 3 * static_cast<size_t>(n_mics)) ||
@@ -222,6 +224,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     p.fs = fs;
     p.c = opt.c;
     p.a_bf16 = (opt.precision == RTIS_PREC_BF16);
+    p.max_batch = opt.max_batch;
 
     // largest |delta| the geometry (plus calibration slack) can produce
     double pmax = 0.0, umax = 0.0;
@@ -313,6 +316,12 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     RTIS_ALLOC(p.d_adj, std::max<size_t>(512, static_cast<size_t>((p.n_out + p.td_bins_per_tile - 1) /
                                                                    p.td_bins_per_tile) * n_dirs * n_mics))
     RTIS_ALLOC(p.d_adj_red, static_cast<size_t>(n_mics) * 16 * 5)
+    if (p.max_batch > 0) {
+        RTIS_ALLOC(p.d_X, static_cast<size_t>(p.Kb) * n_mics * p.max_batch)
+        RTIS_ALLOC(p.d_Y, static_cast<size_t>(p.Kb) * n_dirs * p.max_batch)
+        RTIS_ALLOC(p.d_kbin, static_cast<size_t>(p.Kb))
+        RTIS_ALLOC(p.d_xmax, static_cast<size_t>(n_mics))
+    }
     RTIS_ALLOC(p.d_A, static_cast<size_t>(n_mics) * p.Kb)
     RTIS_ALLOC(p.d_Z, static_cast<size_t>(n_mics) * 2 * p.P)
     RTIS_ALLOC(p.d_a, static_cast<size_t>(n_mics) * n_samples)
@@ -333,6 +342,9 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     RTIS_UP(p.d_dirs, directions, 3 * static_cast<size_t>(n_dirs) * sizeof(float))
     RTIS_UP(p.d_gain, ones.data(), n_mics * sizeof(float))
     RTIS_UP(p.d_delay, zeros.data(), n_mics * sizeof(float))
+    std::vector<float2> kbin(p.max_batch > 0 ? p.Kb : 0);
+    for (int kp = 0; kp < static_cast<int>(kbin.size()); ++kp) kbin[kp] = make_float2(static_cast<float>(k_lo + kp), 0.f);
+    if (p.max_batch > 0) RTIS_UP(p.d_kbin, kbin.data(), kbin.size() * sizeof(float2))
     RTIS_UP(p.d_tw, tw.data(), F * sizeof(float2))
     RTIS_UP(p.d_C, C.data(), p.Kb * sizeof(float2))
     RTIS_UP(p.d_h, h.data(), lpf_len * sizeof(float))
@@ -476,6 +488,65 @@ rtis_status rtis_process(rtis_plan* plan, const int16_t* d_in, float* d_out, voi
         }
     }
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_process: launch");
+}
+
+rtis_status rtis_process_many(rtis_plan* plan, const int16_t* d_in, int n, float* d_out_td, float* d_out_fd,
+                              void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_process_many: injected launch failure");
+    if (!plan || !d_in || (!d_out_td && !d_out_fd)) return fail(RTIS_ERR_INVALID_ARG, "rtis_process_many: NULL argument");
+    if (n < 1) return fail(RTIS_ERR_INVALID_ARG, "rtis_process_many: n must be >= 1");
+    if (!rtis::aligned(d_in, 8) || (d_out_td && !rtis::aligned(d_out_td, 4)) || (d_out_fd && !rtis::aligned(d_out_fd, 4)))
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_process_many: d_in must be 8-byte and the outputs 4-byte aligned");
+    Plan& p = plan->p;
+    if (d_out_fd && n > p.max_batch)
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_process_many: n exceeds the plan's max_batch (rtis_options)");
+    if (d_out_fd && rtis::fdes_smem_bytes(p) > 227 * 1024)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_process_many: the frequency-domain path needs F <= 32768");
+    const size_t in_stride = static_cast<size_t>(p.M) * p.N, out_stride = static_cast<size_t>(p.D) * p.n_out;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rtis_status s = ensure_table(p, st);
+    if (s != RTIS_OK) return s;
+    cudaError_t e = cudaSuccess;
+    // per measurement: matched filter -> analytic signal (time domain) and/or the
+    // in-band spectra as frame t of X [Kb][M][n]; the time-domain energyscape
+    for (int t = 0; t < n && e == cudaSuccess; ++t) {
+        e = rtis::launch_mf_forward(p, d_in + t * in_stride, st);
+        float2* a32 = (d_out_td && !p.a_bf16) ? p.d_a : nullptr;
+        uint32_t* a16 = (d_out_td && p.a_bf16) ? p.d_a16 : nullptr;
+        float2* Xt = d_out_fd ? p.d_X + t : nullptr;
+        if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, a32, Xt, st, a16, n, p.M * n);
+        if (e == cudaSuccess && d_out_td)
+            e = rtis::launch_td_beamform(p, p.a_bf16 ? p.tmap_a16 : p.tmap_a, p.a_bf16, d_out_td + t * out_stride, st);
+    }
+    if (e == cudaSuccess && d_out_fd) {
+        // the steering GEMM: "frequency" k' + k_lo (exact) times "delay" delta/F (the
+        // steering table's phase slope), so the phases equal the per-direction path's
+        rtis::FdGemmPlan g;
+        g.M = p.M;
+        g.D = p.D;
+        g.K = p.Kb;
+        g.T = n;
+        g.precision = RTIS_PREC_FP32;
+        g.y_dkt = 1;  // per direction, the bins of all measurements together
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&g.n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) g.n_sm = 1;
+        g.d_tau = p.d_dphase;
+        g.d_freq = p.d_kbin;
+        g.d_gain = p.d_gain;
+        g.d_scale = p.d_xmax;
+        g.d_status = p.d_status;
+        CUtensorMap ymap;
+        const CUtensorMap* ym = nullptr;
+        if (n % 2 == 0 && n >= 16) {
+            std::string err;
+            if (!rtis::fd_gemm_encode_ymap(g, p.d_Y, &ymap, &err)) return fail(RTIS_ERR_CUDA, "rtis_process_many: " + err);
+            ym = &ymap;
+        }
+        e = rtis::launch_fd_gemm(g, p.d_X, p.d_Y, ym, st);
+        if (e == cudaSuccess) e = rtis::launch_fd_energyscape_from_y(p, p.d_Y, n, d_out_fd, st);
+    }
+    return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_process_many: launch");
 }
 
 rtis_status rtis_beamform_fd(rtis_plan* plan, const float* d_A, float* d_out, void* stream) {

@@ -59,6 +59,13 @@ struct Plan {
     float2* d_a = nullptr;      // [M][N] analytic matched-filter output
     float2* d_A = nullptr;      // [M][Kb] in-band matched-filter spectra (frequency-domain path)
     uint32_t* d_a16 = nullptr;  // [M][N] a as BF16 (re, im) pairs (time-domain path, BF16 storage)
+    // batched frequency-domain path (rtis_process_many): spectra of up to max_batch
+    // measurements as GEMM frames, the steered spectra, and the GEMM's bin "frequencies" k
+    int max_batch = 0;
+    float2* d_X = nullptr;      // [Kb][M][T] in-band spectra, frame t = measurement t
+    float2* d_Y = nullptr;      // [D][Kb][T] steered spectra
+    float2* d_kbin = nullptr;   // [Kb] (k_lo + k', 0): phase k delta/F uses d_dphase as "tau"
+    float* d_xmax = nullptr;    // [M] per-channel max |X| bits for the GEMM scales
     unsigned* d_status = nullptr;
     size_t bytes = 0;
 
@@ -74,6 +81,7 @@ struct Plan {
 constexpr int kFdMaxFrames = 64;
 struct FdGemmPlan {
     int M = 0, D = 0, K = 0, T = 0, precision = 0;
+    int y_dkt = 0;              // output layout: 0 = [K][D][T] (public ABI), 1 = [D][K][T]
     int n_sm = 0;               // persistent grid size
     float2* d_tau = nullptr;    // [D][M] seconds, (hi, lo)
     float2* d_freq = nullptr;   // [K] Hz, (hi, lo)
@@ -100,14 +108,18 @@ rtis_status cuda_fail(cudaError_t e, const char* what);
 // launchers (return cudaGetLastError() of the launch)
 // ----------------------------------------------------------------------------
 cudaError_t launch_mf_forward(const Plan& p, const int16_t* d_in, cudaStream_t st);
-// writes a (complex float) and/or a16 (BF16 pairs) and/or the in-band spectra A
-cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st, uint32_t* d_a16 = nullptr);
+// writes a (complex float) and/or a16 (BF16 pairs) and/or the in-band spectra A,
+// A_m[k'] at d_A[m a_ms + k' a_ks] (default a_ms = Kb, a_ks = 1)
+cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st, uint32_t* d_a16 = nullptr,
+                              int a_ms = -1, int a_ks = 1);
 cudaError_t launch_steering_table(Plan& p, cudaStream_t st);
 // bf16: tmap views BF16 pairs (4-byte elements) rather than complex floats
 cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, bool bf16, float* d_out, cudaStream_t st);
 size_t td_smem_bytes(const Plan& p);
 size_t td_smem_bytes(int row_max, int lpf_max);
 cudaError_t launch_fd_energyscape(const Plan& p, const float2* d_A, float* d_out, cudaStream_t st);
+// energyscapes of T measurements from their steered spectra Y [D][Kb][T]; out [T][D][n_out]
+cudaError_t launch_fd_energyscape_from_y(const Plan& p, const float2* d_Y, int T, float* d_out, cudaStream_t st);
 size_t fdes_smem_bytes(const Plan& p);
 
 // persistent multi-sensor time-domain beamformer

@@ -18,7 +18,8 @@ class Plan:
     """
 
     def __init__(self, mic_xyz, fs, chirp, directions, n_samples, *, c=343.0, decim=10, lpf_taps=None,
-                 band=(20e3, 80e3), path="td", precision="fp32", max_delay_s=10e-6, position_slack_m=0.01):
+                 band=(20e3, 80e3), path="td", precision="fp32", max_delay_s=10e-6, position_slack_m=0.01,
+                 max_batch=0):
         import torch  # device memory and streams only
         self._torch = torch
         o = nat.default_options()
@@ -34,7 +35,9 @@ class Plan:
         o.precision = _PRECS[precision]
         o.max_delay_s = float(max_delay_s)
         o.position_slack_m = float(position_slack_m)
+        o.max_batch = int(max_batch)
         self.handle = nat.rtis_plan_create(mic_xyz, fs, chirp, directions, n_samples, o)
+        self.info_path = path
         self.info = nat.rtis_plan_get_info(self.handle)
         self.M, self.N, self.D = self.info.n_mics, self.info.n_samples, self.info.n_dirs
         self.n_out = self.info.n_out
@@ -68,6 +71,26 @@ class Plan:
             out = self._torch.empty((self.D, self.n_out), dtype=self._torch.float32, device=x.device)
         nat.rtis_process(self.handle, x, out, stream)
         return out
+
+    def process_many(self, x, paths=None, out_td=None, out_fd=None, stream=None):
+        """int16 [n][M][N] device tensor -> energyscapes float32 [n][D][n_out].
+
+        paths: None (the plan's own path, one tensor back) or a tuple of "td"/"fd"
+        (a tuple of tensors back, one matched filter per measurement feeding both).
+        The frequency-domain form runs the n measurements through one batched GEMM
+        (n <= max_batch)."""
+        t = self._torch
+        n = int(x.shape[0])
+        want = (self.info_path,) if paths is None else tuple(paths)
+        shape = (n, self.D, self.n_out)
+        if "td" in want and out_td is None:
+            out_td = t.empty(shape, dtype=t.float32, device=x.device)
+        if "fd" in want and out_fd is None:
+            out_fd = t.empty(shape, dtype=t.float32, device=x.device)
+        nat.rtis_process_many(self.handle, x.contiguous(), n, out_td if "td" in want else None,
+                              out_fd if "fd" in want else None, stream)
+        res = tuple(out_td if w == "td" else out_fd for w in want)
+        return res[0] if paths is None else res
 
     def matched_filter(self, x, want_a=True, want_spectrum=False, stream=None):
         t = self._torch
