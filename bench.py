@@ -484,6 +484,185 @@ def run_calibration(args, rank, world, local):
     plan.close()
 
 
+def run_hemisphere_batched(args, rank, world, local):
+    """B measurements per step through rtis_process_many: per measurement the matched
+    filter and the time-domain energyscape, and for the whole batch the frequency-domain
+    energyscapes via one tcgen05 GEMM with the measurements as frames."""
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2208_10839_gb300 import Plan, _native as nat
+    from paper_2208_10839_gb300 import build as _b
+    _b.build()
+    dev = torch.device("cuda", local)
+    B = args.batch
+    cfgs = [synth.hemisphere(seed_scene=1 + 1000 * rank + i) for i in range(B)]
+    cfg = cfgs[0]
+    plan = Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"], max_batch=B)
+    h = plan.handle
+    xs_host = np.stack([c["x"] for c in cfgs])
+    x = torch.from_numpy(xs_host).to(dev)
+    shape = (B, N_DIRS, plan.n_out)
+    E_td = torch.empty(shape, dtype=torch.float32, device=dev)
+    E_fd = torch.empty(shape, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    def step():
+        nat.rtis_process_many(h, x, B, E_td, E_fd, sh)
+
+    for _ in range(args.warmup):
+        flush(1.0)
+        step()
+    torch.cuda.synchronize()
+    assert plan.sync() == 0
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush(float(k))
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_total = sum(step_ms) / 1e3
+    assert plan.sync() == 0
+
+    # breakdown, same calls split by path, and the beamformer kernels alone (per launch)
+    nb = max(3, min(args.steps, 10))
+    brk = {"td_path": [], "fd_path": [], "matched_filter": [], "td_beamform": []}
+    a = torch.empty((N_MICS, N_SAMPLES), dtype=torch.complex64, device=dev)
+    for k in range(nb):
+        flush(float(k))
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        e[0].record(stream)
+        nat.rtis_process_many(h, x, B, E_td, None, sh)
+        e[1].record(stream)
+        nat.rtis_process_many(h, x, B, None, E_fd, sh)
+        e[2].record(stream)
+        nat.rtis_matched_filter(h, x[k % B], a, None, sh)
+        e[3].record(stream)
+        nat.rtis_beamform_td(h, a, E_td[k % B], sh)
+        e[4].record(stream)
+        torch.cuda.synchronize()
+        for name, i in (("td_path", 0), ("fd_path", 1), ("matched_filter", 2), ("td_beamform", 3)):
+            brk[name].append(e[i].elapsed_time(e[i + 1]))
+    bk = {k: statistics.median(v) for k, v in brk.items()}
+    mf_ms = bk["matched_filter"]
+    td_ms = bk["td_beamform"]
+    fd_ms_per = bk["fd_path"] / B - mf_ms  # GEMM + per-direction IFFTs per measurement
+    assert plan.sync() == 0
+
+    # end to end: pinned host batch in, both energyscape batches out, every step;
+    # copies on their own streams, two buffer sets, overlapping the next batch
+    hs, cs, cs2, ks = (torch.cuda.Stream(device=dev) for _ in range(4))
+    ksh = ks.cuda_stream
+    xh = torch.from_numpy(xs_host).pin_memory()
+    Eh_td = [torch.empty(shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    Eh_fd = [torch.empty(shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    xd = [x, torch.empty_like(x)]
+    Ed_td = [E_td, torch.empty_like(E_td)]
+    Ed_fd = [E_fd, torch.empty_like(E_fd)]
+    ev_in, ev_done, ev_out, ev_out2 = ([torch.cuda.Event() for _ in range(2)] for _ in range(4))
+    ks.wait_stream(stream)
+    for e_ in ev_done + ev_out + ev_out2:
+        e_.record(ks)
+
+    def e2e_step(i):
+        b = i & 1
+        hs.wait_event(ev_done[b])
+        with torch.cuda.stream(hs):
+            xd[b].copy_(xh, non_blocking=True)
+        ev_in[b].record(hs)
+        ks.wait_event(ev_in[b])
+        ks.wait_event(ev_out[b])
+        ks.wait_event(ev_out2[b])
+        nat.rtis_process_many(h, xd[b], B, Ed_td[b], Ed_fd[b], ksh)
+        ev_done[b].record(ks)
+        cs.wait_event(ev_done[b])
+        cs2.wait_event(ev_done[b])
+        with torch.cuda.stream(cs):
+            Eh_td[b].copy_(Ed_td[b], non_blocking=True)
+        with torch.cuda.stream(cs2):
+            Eh_fd[b].copy_(Ed_fd[b], non_blocking=True)
+        ev_out[b].record(cs)
+        ev_out2[b].record(cs2)
+
+    for i in range(2):
+        e2e_step(i)
+    torch.cuda.synchronize()
+    e2e_steps = max(args.steps // 2, 3)
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ee0.record(ks)
+    for c in (hs, cs, cs2):
+        c.wait_event(ee0)
+    for i in range(e2e_steps):
+        e2e_step(i)
+    for e_ in ev_out + ev_out2:
+        ks.wait_event(e_)
+    ee1.record(ks)
+    torch.cuda.synchronize()
+    t_e2e = ee0.elapsed_time(ee1) / 1e3
+    assert torch.equal(Eh_td[0], Eh_td[1]) and torch.equal(Eh_fd[0], Eh_fd[1])
+    assert plan.sync() == 0
+
+    if world > 1:
+        t_total, t_e2e = max_over_ranks([t_total, t_e2e], dev)
+    value = replica_rate(args.steps * B, world, t_total)
+    e2e_value = replica_rate(e2e_steps * B, world, t_e2e)
+    clocks = clk.summary()
+
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    peak_tf = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    basis = f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {SM_MAX_MHZ_NOMINAL:.0f} MHz"
+    td_flops = float(N_DIRS) * N_SAMPLES * N_MICS * 4 * 2 * 2
+    ach = td_flops / (td_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "td_beamform_kernel", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": ach / peak_tf, "traffic": TD_TRAFFIC_BYTES, "peak_basis": basis,
+                "algorithmic_flops_per_launch": td_flops, "launch_ms": td_ms,
+                "timing": "CUDA events around rtis_beamform_td calls in a breakdown loop of this run"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "energyscapes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_mics": N_MICS, "n_samples": N_SAMPLES, "n_dirs": N_DIRS,
+                   "n_out": plan.n_out, "decim": 10, "batch_per_step": B,
+                   "paths_per_step": "time-domain (Catmull-Rom) and frequency-domain (phase ramp, batched "
+                                     "tcgen05 GEMM over the step's measurements) energyscapes of every "
+                                     "measurement; value counts measurements",
+                   "l2": "flushed between steps (512 MiB write, then a 256 MiB read so write-backs finish), "
+                         "outside the timed events; the step's GEMM output (4.6 GB) exceeds L2 anyway",
+                   "parallelism": f"{world} independent replica(s), {B} measurements per rank per step"},
+        "e2e": {"value": e2e_value, "unit": "energyscapes/s", "h2d_bytes_per_step": int(x.numel() * 2),
+                "d2h_bytes_per_step": int(E_td.numel() * 4 + E_fd.numel() * 4), "calls": "rtis_process_many",
+                "pipelining": "H2D and D2H on their own streams, two buffer sets; copies overlap the next step"},
+        "gpu_launches": args.steps * (3 * B + 3),
+        "kernels_ms": {"matched_filter_per_measurement": mf_ms, "td_beamform_per_launch": td_ms,
+                       "fd_batched_per_measurement": fd_ms_per, "td_path_per_step": bk["td_path"],
+                       "fd_path_per_step": bk["fd_path"]},
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_es, t_mf, t_das = oracle_sample_time(cfg, args.cpu_dirs)
+        line["cpu_baseline"] = {"value": 1.0 / t_es, "unit": "energyscapes/s", "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 oracle, one process: matched filter on all 32 channels "
+                                          f"({t_mf:.2f} s) + time- and frequency-domain DAS/envelope on "
+                                          f"{args.cpu_dirs} of {N_DIRS} directions ({t_das:.2f} s), scaled to "
+                                          f"{N_DIRS} directions"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -499,6 +678,9 @@ def main():
                          "energyscape + L2 loss + adjoint of a perturbed 32-mic array")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--bins", type=int, default=1200, help="fd_gemm: frequency bins (1200 = the full workload)")
+    ap.add_argument("--batch", type=int, default=64,
+                    help="hemisphere: measurements per step (1: per-measurement calls; >1: rtis_process_many, "
+                         "the frequency-domain form as one batched tensor-core GEMM)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -518,6 +700,8 @@ def main():
         return run_ring(args, rank, world, local)
     if args.workload == "calibration":
         return run_calibration(args, rank, world, local)
+    if args.batch > 1:
+        return run_hemisphere_batched(args, rank, world, local)
 
     import synth
     from paper_2208_10839_gb300 import Plan, _native as nat
