@@ -129,12 +129,20 @@ __device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const Split
     static_assert(!LAST || NS == NB, "the last pass has Ns = P/16");
     const int tw_scale = F / (NS * 16);
     float2 v[BPT][16];
+    // with NB a multiple of 32, fpad(j + r NB) = fpad(j) + r (NB + NB/32) for j < NB
+    constexpr int NBP = NB + NB / 32;
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
         const int j = threadIdx.x + b * kFdesThreads;
         if (NB % kFdesThreads == 0 || j < NB) {
+            if constexpr (NB % 32 == 0) {
+                const float2* src = buf + fpad(j);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) v[b][r] = buf[fpad(j + r * NB)];
+                for (int r = 0; r < 16; ++r) v[b][r] = src[r * NBP];
+            } else {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) v[b][r] = buf[fpad(j + r * NB)];
+            }
         }
     }
     __syncthreads();
@@ -156,15 +164,32 @@ __device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const Split
         if (NB % kFdesThreads == 0 || j < NB) {
             const int k = j & (NS - 1);
             if (NS > 1) {
-                if (!SHARED_K) twiddles(k);
+                if (!SHARED_K) {
+                    // P = 8192, last pass: k = t + 256 b, so w_k^r = w_t^r e^{+2 pi i 256 b r / P}
+                    // = w_t^r rot32(r b): the second butterfly's twiddles are exact rotations
+                    if (b == 0 || !(BPT == 2 && P == 8192))
+                        twiddles(k);
+                }
 #pragma unroll
-                for (int r = 1; r < 16; ++r) v[b][r] = cmul(v[b][r], w[r]);
+                for (int r = 1; r < 16; ++r) {
+                    float2 wr = w[r];
+                    if constexpr (!SHARED_K && BPT == 2 && P == 8192) {
+                        if (b == 1) wr = rot32<true>(wr, r);
+                    }
+                    v[b][r] = cmul(v[b][r], wr);
+                }
             }
             dft_reg<16, true>(v[b]);
             if constexpr (!LAST) {
                 const int base = (j - k) * 16 + k;
+                if constexpr (NS % 32 == 0) {  // fpad(base + r NS) = fpad(base) + r (NS + NS/32)
+                    float2* dst = buf + fpad(base);
 #pragma unroll
-                for (int r = 0; r < 16; ++r) buf[fpad(base + r * NS)] = v[b][r];
+                    for (int r = 0; r < 16; ++r) dst[r * (NS + NS / 32)] = v[b][r];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) buf[fpad(base + r * NS)] = v[b][r];
+                }
             } else {
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
@@ -263,8 +288,10 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
                 v[r] = g;
             }
             dft_reg<R0, true>(v);
+            // R0 divides 32, so t R0 + r stays in one 32-point block: fpad is linear in r
+            float2* dst = fbuf + fpad(tid * R0);
 #pragma unroll
-            for (int r = 0; r < R0; ++r) fbuf[fpad(tid * R0 + r)] = v[r];
+            for (int r = 0; r < R0; ++r) dst[r] = v[r];
         }
         __syncthreads();
         fdes_pass16<LOGP, R0, false>(fbuf, env, tws, a.F, p_need);
