@@ -53,7 +53,7 @@ __device__ __forceinline__ float frac_cycles(float k, float2 ph) {
 }
 
 struct FdesSmem {
-    int fbuf, B, twhi, twlo, Eacc, hs, step, gs, bytes;
+    int fbuf, B, twhi, twlo, Eacc, hs, step, gs, ct, bytes;
 };
 
 __host__ __device__ constexpr int fpad(int i) { return i + (i >> 5); }  // 1-in-32 bank skew
@@ -77,6 +77,9 @@ __host__ __device__ inline FdesSmem fdes_layout(int P, int F, int Kb, int n_out,
     o += lpf_len * 4;
     L.gs = o;
     o += M * 4;
+    o = (o + 7) & ~7;
+    L.ct = o;  // last-pass twiddles: 32 x e^{+2 pi i l/P}, then 16 x e^{+2 pi i 32 h/P}
+    o += 48 * 8;
     L.bytes = o;
     return L;
 }
@@ -122,7 +125,8 @@ __device__ __forceinline__ void fdes_gemv_chunk(const FdesArgs& a, const float2*
 // Ns = product of the earlier radices.  The last pass (Ns = P/16) writes
 // env[p] = |b(4p + q)| for p < p_need instead of the complex values.
 template <int LOGP, int NS, bool LAST>
-__device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const SplitTwiddles& tws, int F, int p_need) {
+__device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const SplitTwiddles& tws, const float2* ct, int F,
+                                            int p_need) {
     constexpr int P = 1 << LOGP;
     constexpr int NB = P / 16;
     constexpr int BPT = (NB + kFdesThreads - 1) / kFdesThreads;
@@ -167,8 +171,22 @@ __device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const Split
                 if (!SHARED_K) {
                     // P = 8192, last pass: k = t + 256 b, so w_k^r = w_t^r e^{+2 pi i 256 b r / P}
                     // = w_t^r rot32(r b): the second butterfly's twiddles are exact rotations
-                    if (b == 0 || !(BPT == 2 && P == 8192))
-                        twiddles(k);
+                    if (b == 0 || !(BPT == 2 && P == 8192)) {
+                        if constexpr (LAST) {
+                            // w = e^{+2 pi i k/P} from two small tables read without bank
+                            // conflicts (k = 32 h + l), then w^2, w^4, w^8 by squaring
+                            const float2 w1 = cmul(ct[32 + (k >> 5)], ct[k & 31]);
+                            w[1] = w1;
+                            w[2] = cmul(w1, w1);
+                            w[4] = cmul(w[2], w[2]);
+                            w[8] = cmul(w[4], w[4]);
+#pragma unroll
+                            for (int r = 3; r < 16; ++r)
+                                if (r & (r - 1)) w[r] = cmul(w[r & (r - 1)], w[r & -r]);
+                        } else {
+                            twiddles(k);
+                        }
+                    }
                 }
 #pragma unroll
                 for (int r = 1; r < 16; ++r) {
@@ -226,6 +244,11 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
     for (int j = tid; j < 256; j += kFdesThreads) twlo[j] = __ldg(a.tw + j);
     for (int j = tid; j < a.F / 256; j += kFdesThreads) twhi[j] = __ldg(a.tw + j * 256);
     for (int j = tid; j < a.lpf_len; j += kFdesThreads) hs[j] = a.h[j];
+    float2* ct = reinterpret_cast<float2*>(sm + L.ct);
+    if (tid < 48) {  // e^{+2 pi i l/P} = conj(tw[4 l]), e^{+2 pi i 32 h/P} = conj(tw[128 h]) (F = 4P)
+        const int idx = tid < 32 ? 4 * tid : 128 * (tid - 32);
+        ct[tid] = conjf2(__ldg(a.tw + (idx & (a.F - 1))));
+    }
     for (int i = tid; i < a.n_out; i += kFdesThreads) Eacc[i] = 0.f;
     if (tid < M) {
         const float2 ph = __ldg(a.dphase + static_cast<size_t>(d) * M + tid);
@@ -294,8 +317,8 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
             for (int r = 0; r < R0; ++r) dst[r] = v[r];
         }
         __syncthreads();
-        fdes_pass16<LOGP, R0, false>(fbuf, env, tws, a.F, p_need);
-        fdes_pass16<LOGP, 16 * R0, true>(fbuf, env, tws, a.F, p_need);
+        fdes_pass16<LOGP, R0, false>(fbuf, env, tws, ct, a.F, p_need);
+        fdes_pass16<LOGP, 16 * R0, true>(fbuf, env, tws, ct, a.F, p_need);
         for (int i = tid; i < a.n_out; i += kFdesThreads) {
             const int n0 = a.R * i - half;          // n = n0 + j
             const int j0 = ((q - n0) % 4 + 4) & 3;  // first tap with n = q (mod 4)
