@@ -18,8 +18,10 @@
 // pre-twiddle in registers (skipping the zero bins above the band), the last
 // writes |b| as floats, only for the samples n < N.  After each phase the
 // low-pass taps that fall on n = q (mod 4) are added to the outputs each
-// thread owns.  Twiddles come from two small shared tables
-// (w^j = hi[j >> 8] lo[j & 255]) instead of the F-point table.
+// thread owns.  The pre-twiddles come from two small shared tables
+// (w^j = hi[j >> 8] lo[j & 255]) instead of the F-point table; the radix-16
+// passes take w = e^{2 pi i x/P} from two more (32 + 16 entries, read without
+// bank conflicts) and its powers by squaring and products.
 #include "fft.cuh"
 #include "rtis_internal.h"
 
@@ -125,13 +127,11 @@ __device__ __forceinline__ void fdes_gemv_chunk(const FdesArgs& a, const float2*
 // Ns = product of the earlier radices.  The last pass (Ns = P/16) writes
 // env[p] = |b(4p + q)| for p < p_need instead of the complex values.
 template <int LOGP, int NS, bool LAST>
-__device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const SplitTwiddles& tws, const float2* ct, int F,
-                                            int p_need) {
+__device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const float2* ct, int p_need) {
     constexpr int P = 1 << LOGP;
     constexpr int NB = P / 16;
     constexpr int BPT = (NB + kFdesThreads - 1) / kFdesThreads;
     static_assert(!LAST || NS == NB, "the last pass has Ns = P/16");
-    const int tw_scale = F / (NS * 16);
     float2 v[BPT][16];
     // with NB a multiple of 32, fpad(j + r NB) = fpad(j) + r (NB + NB/32) for j < NB
     constexpr int NBP = NB + NB / 32;
@@ -154,9 +154,15 @@ __device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const Split
     // when Ns divides the thread count every butterfly of a thread has the same k
     constexpr bool SHARED_K = (NS <= kFdesThreads);
     float2 w[16];
+    // w = e^{+2 pi i k/(16 Ns)} = e^{+2 pi i x/P} with x = k P/(16 Ns) < P/16, from two
+    // small tables read without bank conflicts (x = 32 h + l); w^2, w^4, w^8 by squaring
     auto twiddles = [&](int k) {
-#pragma unroll
-        for (int r = 1; r < 16; r <<= 1) w[r] = conjf2(tws(r * k * tw_scale));
+        const int x = k * (P / (16 * NS));
+        const float2 w1 = cmul(ct[32 + (x >> 5)], ct[x & 31]);
+        w[1] = w1;
+        w[2] = cmul(w1, w1);
+        w[4] = cmul(w[2], w[2]);
+        w[8] = cmul(w[4], w[4]);
 #pragma unroll
         for (int r = 3; r < 16; ++r)
             if (r & (r - 1)) w[r] = cmul(w[r & (r - 1)], w[r & -r]);
@@ -171,22 +177,7 @@ __device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const Split
                 if (!SHARED_K) {
                     // P = 8192, last pass: k = t + 256 b, so w_k^r = w_t^r e^{+2 pi i 256 b r / P}
                     // = w_t^r rot32(r b): the second butterfly's twiddles are exact rotations
-                    if (b == 0 || !(BPT == 2 && P == 8192)) {
-                        if constexpr (LAST) {
-                            // w = e^{+2 pi i k/P} from two small tables read without bank
-                            // conflicts (k = 32 h + l), then w^2, w^4, w^8 by squaring
-                            const float2 w1 = cmul(ct[32 + (k >> 5)], ct[k & 31]);
-                            w[1] = w1;
-                            w[2] = cmul(w1, w1);
-                            w[4] = cmul(w[2], w[2]);
-                            w[8] = cmul(w[4], w[4]);
-#pragma unroll
-                            for (int r = 3; r < 16; ++r)
-                                if (r & (r - 1)) w[r] = cmul(w[r & (r - 1)], w[r & -r]);
-                        } else {
-                            twiddles(k);
-                        }
-                    }
+                    if (b == 0 || !(BPT == 2 && P == 8192)) twiddles(k);
                 }
 #pragma unroll
                 for (int r = 1; r < 16; ++r) {
@@ -317,8 +308,8 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
             for (int r = 0; r < R0; ++r) dst[r] = v[r];
         }
         __syncthreads();
-        fdes_pass16<LOGP, R0, false>(fbuf, env, tws, ct, a.F, p_need);
-        fdes_pass16<LOGP, 16 * R0, true>(fbuf, env, tws, ct, a.F, p_need);
+        fdes_pass16<LOGP, R0, false>(fbuf, env, ct, p_need);
+        fdes_pass16<LOGP, 16 * R0, true>(fbuf, env, ct, p_need);
         for (int i = tid; i < a.n_out; i += kFdesThreads) {
             const int n0 = a.R * i - half;          // n = n0 + j
             const int j0 = ((q - n0) % 4 + 4) & 3;  // first tap with n = q (mod 4)
