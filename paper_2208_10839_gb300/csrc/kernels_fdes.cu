@@ -310,15 +310,18 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
         __syncthreads();
         fdes_pass16<LOGP, R0, false>(fbuf, env, ct, p_need);
         fdes_pass16<LOGP, 16 * R0, true>(fbuf, env, ct, p_need);
+        const int e_end = (a.N - q + 3) >> 2;  // env entries of this phase with n = 4p + q < N
         for (int i = tid; i < a.n_out; i += kFdesThreads) {
             const int n0 = a.R * i - half;          // n = n0 + j
             const int j0 = ((q - n0) % 4 + 4) & 3;  // first tap with n = q (mod 4)
-            float s = 0.f;
-            for (int j = j0; j < a.lpf_len; j += 4) {
-                const int n = n0 + j;
-                if (n >= 0 && n < a.N) s = fmaf(hs[j], env[(n - q) >> 2], s);
-            }
-            Eacc[i] += s;
+            // taps j = j0 + 4 s read env[e0 + s] (n0 + j0 - q is a multiple of 4); only
+            // 0 <= n < N count, i.e. 0 <= e0 + s < e_end
+            const int e0 = (n0 + j0 - q) >> 2;
+            const int s_lo = max(0, -e0);
+            const int s_hi = min((a.lpf_len - j0 + 3) >> 2, e_end - e0);
+            float acc = 0.f;
+            for (int sk = s_lo; sk < s_hi; ++sk) acc = fmaf(hs[j0 + 4 * sk], env[e0 + sk], acc);
+            Eacc[i] += acc;
         }
         __syncthreads();
     }
