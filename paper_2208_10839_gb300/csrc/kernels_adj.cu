@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
         const int grp = st % ngroups;
         if (dir_ok && !__any_sync(0xffffffffu, timed_out)) {
             if (!pass_b) {
-#pragma unroll 1
+#pragma unroll
                 for (int mi = 0; mi < MS; ++mi) {
                     const int m = grp * MS + mi;
                     if (m >= M) break;

@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
             }
             const bool warp_timed_out = __any_sync(0xffffffffu, timed_out);
             if (dir_ok && !warp_timed_out) {
-#pragma unroll 1
+#pragma unroll
                 for (int mi = 0; mi < MS; ++mi) {
                     const int m = st * MS + mi;
                     if (m >= M) break;
