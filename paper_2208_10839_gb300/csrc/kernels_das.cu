@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
         for (int t = 0; t < T; ++t) {
             const int n = n_start + lane * T + t;
             const float2 v = unpack2(acc[t]);
-            env[lane * T + t] = (n >= 0 && n < S.N) ? sqrtf(v.x * v.x + v.y * v.y) : 0.f;
+            env[lane * T + t] = (n >= 0 && n < S.N) ? magnitude_from_norm(v.x * v.x + v.y * v.y) : 0.f;
         }
         __syncwarp();
         if (dir_ok) {

@@ -203,7 +203,7 @@ __device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const float
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     const int p = k + r * NS;
-                    if (p < p_need) env[p] = sqrtf(v[b][r].x * v[b][r].x + v[b][r].y * v[b][r].y);
+                    if (p < p_need) env[p] = magnitude_from_norm(v[b][r].x * v[b][r].x + v[b][r].y * v[b][r].y);
                 }
             }
         }

@@ -23,6 +23,9 @@ constexpr int kTdStages = 4;                          // smem ring depth
 constexpr int kTdBox = 256;                           // TMA box width (8-byte elements)
 constexpr int kMaxMics = 32;                          // lanes hold per-mic steering
 
+// |z| from |z|^2 = x^2 + y^2 as x^2 rsqrt(x^2) (a few ulp, no slow path; 0 for 0)
+__device__ __forceinline__ float magnitude_from_norm(float n2) { return n2 > 0.f ? n2 * rsqrtf(n2) : 0.f; }
+
 // ----------------------------------------------------------------------------
 // plan
 // ----------------------------------------------------------------------------
