@@ -26,14 +26,18 @@ using namespace fft;
 
 constexpr int kMfThreads = 512;
 
-// grid (M, 2): channel m, polyphase pair h (h = 0: x[4p], x[4p+1]; h = 1: x[4p+2], x[4p+3])
+// grid (M, 2, n): channel m, polyphase pair h (h = 0: x[4p], x[4p+1]; h = 1:
+// x[4p+2], x[4p+3]), measurement blockIdx.z (input and spectra advance by their strides)
 template <int LOGP>
 __global__ void __launch_bounds__(kMfThreads) mf_forward_kernel(const int16_t* __restrict__ x, int N,
                                                                 float2* __restrict__ Z,
-                                                                const float2* __restrict__ tw, int F) {
+                                                                const float2* __restrict__ tw, int F,
+                                                                size_t x_stride, size_t z_stride) {
     extern __shared__ float2 sbuf[];
     constexpr int P = 1 << LOGP;
     const int m = blockIdx.x, h = blockIdx.y;
+    x += blockIdx.z * x_stride;
+    Z += blockIdx.z * z_stride;
     const short4* xr = reinterpret_cast<const short4*>(x + static_cast<size_t>(m) * N);
     const int nq = N >> 2;
     const float sc = 1.0f / 32768.0f;
@@ -61,10 +65,15 @@ __global__ void __launch_bounds__(kMfThreads) mf_inverse_kernel(const float2* __
                                                                 int k_lo, int Kb, int N,
                                                                 float2* __restrict__ a,
                                                                 float2* __restrict__ A_out,
-                                                                uint32_t* __restrict__ a16, int a_ms, int a_ks) {
+                                                                uint32_t* __restrict__ a16, int a_ms, int a_ks,
+                                                                size_t z_stride, size_t a_stride, size_t A_tstride) {
     extern __shared__ float2 sbuf[];
     constexpr int P = 1 << LOGP;
     const int m = blockIdx.x, q = blockIdx.y;
+    Z += blockIdx.z * z_stride;  // measurement blockIdx.z
+    if (a) a += blockIdx.z * a_stride;
+    if (a16) a16 += blockIdx.z * a_stride;
+    if (A_out) A_out += blockIdx.z * A_tstride;
     const float2* Za = Z + static_cast<size_t>(m) * 2 * P;
     const float2* Zb = Za + P;
     for (int kp = threadIdx.x; kp < P; kp += kMfThreads) {
@@ -116,58 +125,60 @@ size_t mf_smem() {
 }
 
 template <int LOGP>
-cudaError_t mf_forward_t(const Plan& p, const int16_t* d_in, cudaStream_t st) {
+cudaError_t mf_forward_t(const Plan& p, const int16_t* d_in, cudaStream_t st, const MfBatch& mb) {
     const size_t sm = mf_smem<LOGP>();
     cudaError_t e = cudaFuncSetAttribute(mf_forward_kernel<LOGP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sm));
     if (e != cudaSuccess) return e;
-    mf_forward_kernel<LOGP><<<dim3(p.M, 2), kMfThreads, sm, st>>>(d_in, p.N, p.d_Z, p.d_tw, p.F);
+    mf_forward_kernel<LOGP><<<dim3(p.M, 2, mb.n), kMfThreads, sm, st>>>(d_in, p.N, mb.Z ? mb.Z : p.d_Z, p.d_tw,
+                                                                         p.F, mb.x_stride, mb.z_stride);
     return cudaGetLastError();
 }
 
 template <int LOGP>
 cudaError_t mf_inverse_t(const Plan& p, float2* d_a, float2* d_A, uint32_t* d_a16, int a_ms, int a_ks,
-                         cudaStream_t st) {
+                         cudaStream_t st, const MfBatch& mb) {
     const size_t sm = mf_smem<LOGP>();
     cudaError_t e = cudaFuncSetAttribute(mf_inverse_kernel<LOGP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sm));
     if (e != cudaSuccess) return e;
     const int nq = (d_a || d_a16) ? 4 : 1;
-    mf_inverse_kernel<LOGP><<<dim3(p.M, nq), kMfThreads, sm, st>>>(p.d_Z, p.d_C, p.d_tw, p.F, p.k_lo, p.Kb,
-                                                                  p.N, d_a, d_A, d_a16, a_ms, a_ks);
+    mf_inverse_kernel<LOGP><<<dim3(p.M, nq, mb.n), kMfThreads, sm, st>>>(
+        mb.Z ? mb.Z : p.d_Z, p.d_C, p.d_tw, p.F, p.k_lo, p.Kb, p.N, d_a, d_A, d_a16, a_ms, a_ks, mb.z_stride,
+        mb.a_stride, mb.A_tstride);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_mf_forward(const Plan& p, const int16_t* d_in, cudaStream_t st) {
+cudaError_t launch_mf_forward(const Plan& p, const int16_t* d_in, cudaStream_t st, const MfBatch& mb) {
     switch (p.logP) {
-        case 6: return mf_forward_t<6>(p, d_in, st);
-        case 7: return mf_forward_t<7>(p, d_in, st);
-        case 8: return mf_forward_t<8>(p, d_in, st);
-        case 9: return mf_forward_t<9>(p, d_in, st);
-        case 10: return mf_forward_t<10>(p, d_in, st);
-        case 11: return mf_forward_t<11>(p, d_in, st);
-        case 12: return mf_forward_t<12>(p, d_in, st);
-        case 13: return mf_forward_t<13>(p, d_in, st);
-        case 14: return mf_forward_t<14>(p, d_in, st);
+        case 6: return mf_forward_t<6>(p, d_in, st, mb);
+        case 7: return mf_forward_t<7>(p, d_in, st, mb);
+        case 8: return mf_forward_t<8>(p, d_in, st, mb);
+        case 9: return mf_forward_t<9>(p, d_in, st, mb);
+        case 10: return mf_forward_t<10>(p, d_in, st, mb);
+        case 11: return mf_forward_t<11>(p, d_in, st, mb);
+        case 12: return mf_forward_t<12>(p, d_in, st, mb);
+        case 13: return mf_forward_t<13>(p, d_in, st, mb);
+        case 14: return mf_forward_t<14>(p, d_in, st, mb);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st, uint32_t* d_a16, int a_ms,
-                              int a_ks) {
+                              int a_ks, const MfBatch& mb) {
     if (a_ms < 0) a_ms = p.Kb;
     switch (p.logP) {
-        case 6: return mf_inverse_t<6>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
-        case 7: return mf_inverse_t<7>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
-        case 8: return mf_inverse_t<8>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
-        case 9: return mf_inverse_t<9>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
-        case 10: return mf_inverse_t<10>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
-        case 11: return mf_inverse_t<11>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
-        case 12: return mf_inverse_t<12>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
-        case 13: return mf_inverse_t<13>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
-        case 14: return mf_inverse_t<14>(p, d_a, d_A, d_a16, a_ms, a_ks, st);
+        case 6: return mf_inverse_t<6>(p, d_a, d_A, d_a16, a_ms, a_ks, st, mb);
+        case 7: return mf_inverse_t<7>(p, d_a, d_A, d_a16, a_ms, a_ks, st, mb);
+        case 8: return mf_inverse_t<8>(p, d_a, d_A, d_a16, a_ms, a_ks, st, mb);
+        case 9: return mf_inverse_t<9>(p, d_a, d_A, d_a16, a_ms, a_ks, st, mb);
+        case 10: return mf_inverse_t<10>(p, d_a, d_A, d_a16, a_ms, a_ks, st, mb);
+        case 11: return mf_inverse_t<11>(p, d_a, d_A, d_a16, a_ms, a_ks, st, mb);
+        case 12: return mf_inverse_t<12>(p, d_a, d_A, d_a16, a_ms, a_ks, st, mb);
+        case 13: return mf_inverse_t<13>(p, d_a, d_A, d_a16, a_ms, a_ks, st, mb);
+        case 14: return mf_inverse_t<14>(p, d_a, d_A, d_a16, a_ms, a_ks, st, mb);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -33,7 +33,7 @@ cudaError_t dev_alloc(T** ptr, size_t count, size_t* total) {
 void free_plan_buffers(Plan& p) {
     void* bufs[] = {p.d_mic, p.d_dirs, p.d_gain, p.d_delay, p.d_tw, p.d_C, p.d_h,
                     p.d_shift, p.d_wt, p.d_dphase, p.d_wraw, p.d_wder, p.d_adj, p.d_adj_red, p.d_Z, p.d_a, p.d_A, p.d_a16,
-                    p.d_X, p.d_Y, p.d_kbin, p.d_xmax, p.d_status};
+                    p.d_X, p.d_Y, p.d_kbin, p.d_xmax, p.d_Zb, p.d_ab, p.d_status};
     for (void* b : bufs)
         if (b) cudaFree(b);
 }
@@ -149,6 +149,16 @@ const char* rtis_status_string(rtis_status s) {
 }
 
 const char* rtis_last_error(void) { return rtis::g_last_error.c_str(); }
+
+// TMA views of the per-measurement analytic signals of rtis_process_many
+static bool encode_batch_maps(Plan& p, std::string* err) {
+    p.tmap_ab.resize(p.max_batch);
+    for (int t = 0; t < p.max_batch; ++t)
+        if (!rtis::encode_tmap_2d_u64(&p.tmap_ab[t], p.d_ab + static_cast<size_t>(t) * p.M * p.N,
+                                      static_cast<uint64_t>(p.N), static_cast<uint64_t>(p.M), rtis::kTdBox, 1, err))
+            return false;
+    return true;
+}
 
 rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, double fs, const float* chirp,
                              int chirp_len, const float* directions, int n_dirs, int n_samples,
@@ -321,6 +331,8 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         RTIS_ALLOC(p.d_Y, static_cast<size_t>(p.Kb) * n_dirs * p.max_batch)
         RTIS_ALLOC(p.d_kbin, static_cast<size_t>(p.Kb))
         RTIS_ALLOC(p.d_xmax, static_cast<size_t>(n_mics))
+        RTIS_ALLOC(p.d_Zb, static_cast<size_t>(p.max_batch) * n_mics * 2 * p.P)
+        RTIS_ALLOC(p.d_ab, static_cast<size_t>(p.max_batch) * n_mics * n_samples)
     }
     RTIS_ALLOC(p.d_A, static_cast<size_t>(n_mics) * p.Kb)
     RTIS_ALLOC(p.d_Z, static_cast<size_t>(n_mics) * 2 * p.P)
@@ -361,7 +373,8 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     if (!rtis::encode_tmap_2d_u64(&p.tmap_a, p.d_a, static_cast<uint64_t>(n_samples), static_cast<uint64_t>(n_mics),
                                   rtis::kTdBox, 1, &err) ||
         (p.a_bf16 && !rtis::encode_tmap_2d_u32(&p.tmap_a16, p.d_a16, static_cast<uint64_t>(n_samples),
-                                               static_cast<uint64_t>(n_mics), rtis::kTdBox, 1, &err))) {
+                                               static_cast<uint64_t>(n_mics), rtis::kTdBox, 1, &err)) ||
+        !encode_batch_maps(p, &err)) {
         rtis::free_plan_buffers(p);
         delete plan;
         return fail(RTIS_ERR_CUDA, "rtis_plan_create: " + err);
@@ -507,9 +520,45 @@ rtis_status rtis_process_many(rtis_plan* plan, const int16_t* d_in, int n, float
     rtis_status s = ensure_table(p, st);
     if (s != RTIS_OK) return s;
     cudaError_t e = cudaSuccess;
+    if (n <= p.max_batch && !(d_out_td && p.a_bf16)) {
+        // all n matched filters in two launches (grid z = measurement): analytic
+        // signals into d_ab[t], spectra into frame t of X; then the time-domain
+        // beamformer over up to 16 measurements per persistent launch
+        rtis::MfBatch mb;
+        mb.n = n;
+        mb.x_stride = in_stride;
+        mb.Z = p.d_Zb;
+        mb.z_stride = static_cast<size_t>(p.M) * 2 * p.P;
+        mb.a_stride = in_stride;
+        mb.A_tstride = 1;
+        e = rtis::launch_mf_forward(p, d_in, st, mb);
+        if (e == cudaSuccess)
+            e = rtis::launch_mf_inverse(p, d_out_td ? p.d_ab : nullptr, d_out_fd ? p.d_X : nullptr, st, nullptr, n,
+                                        p.M * n, mb);
+        const int per_sensor = rtis::td_tiles(p);
+        for (int t0 = 0; d_out_td && t0 < n && e == cudaSuccess; t0 += rtis::kTdMaxSensors) {
+            const int cnt = std::min(rtis::kTdMaxSensors, n - t0);
+            rtis::TdMaps maps;
+            rtis::TdBatch bt;
+            std::memset(&bt, 0, sizeof(bt));
+            for (int i = 0; i < cnt; ++i) {
+                maps.m[i] = p.tmap_ab[t0 + i];
+                rtis::td_fill_sensor(p, d_out_td + (t0 + i) * out_stride, i * per_sensor, &bt.s[i]);
+            }
+            bt.n_sensors = cnt;
+            bt.total_tiles = cnt * per_sensor;
+            bt.row_max = p.td_row;
+            bt.lpf_max = p.lpf_len;
+            bt.status = p.d_status;
+            bt.stall = (rtis::fault_mode() == rtis::kFaultStall) ? 1 : 0;
+            // the plan's tuned grid: one CTA per tile, or its persistent CTA count
+            const int grid = (p.td_grid <= 0 || p.td_grid >= per_sensor) ? bt.total_tiles : p.td_grid;
+            e = rtis::launch_td_batch(maps, bt, p.td_variant, grid, st);
+        }
+    }
     // per measurement: matched filter -> analytic signal (time domain) and/or the
     // in-band spectra as frame t of X [Kb][M][n]; the time-domain energyscape
-    for (int t = 0; t < n && e == cudaSuccess; ++t) {
+    for (int t = 0; (n > p.max_batch || (d_out_td && p.a_bf16)) && t < n && e == cudaSuccess; ++t) {
         e = rtis::launch_mf_forward(p, d_in + t * in_stride, st);
         float2* a32 = (d_out_td && !p.a_bf16) ? p.d_a : nullptr;
         uint32_t* a16 = (d_out_td && p.a_bf16) ? p.d_a16 : nullptr;

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/rtis.h"
 
@@ -23,8 +24,9 @@ constexpr int kTdStages = 4;                          // smem ring depth
 constexpr int kTdBox = 256;                           // TMA box width (8-byte elements)
 constexpr int kMaxMics = 32;                          // lanes hold per-mic steering
 
-// |z| from |z|^2 = x^2 + y^2 as x^2 rsqrt(x^2) (a few ulp, no slow path; 0 for 0)
-__device__ __forceinline__ float magnitude_from_norm(float n2) { return n2 > 0.f ? n2 * rsqrtf(n2) : 0.f; }
+// |z| from |z|^2 = x^2 + y^2 as n2 rsqrt(n2) (a few ulp, no slow path); 0 for 0, and a
+// NaN stays NaN (n2 * 0) so non-finite inputs still show in the output
+__device__ __forceinline__ float magnitude_from_norm(float n2) { return n2 > 0.f ? n2 * rsqrtf(n2) : n2 * 0.f; }
 
 // ----------------------------------------------------------------------------
 // plan
@@ -69,6 +71,9 @@ struct Plan {
     float2* d_Y = nullptr;      // [D][Kb][T] steered spectra
     float2* d_kbin = nullptr;   // [Kb] (k_lo + k', 0): phase k delta/F uses d_dphase as "tau"
     float* d_xmax = nullptr;    // [M] per-channel max |X| bits for the GEMM scales
+    float2* d_Zb = nullptr;     // [max_batch][M][2][P] half spectra, one set per measurement
+    float2* d_ab = nullptr;     // [max_batch][M][N] analytic signals, one per measurement
+    std::vector<CUtensorMap> tmap_ab;  // TMA views of the d_ab rows (time-domain beamformer)
     unsigned* d_status = nullptr;
     size_t bytes = 0;
 
@@ -110,11 +115,20 @@ rtis_status cuda_fail(cudaError_t e, const char* what);
 // ----------------------------------------------------------------------------
 // launchers (return cudaGetLastError() of the launch)
 // ----------------------------------------------------------------------------
-cudaError_t launch_mf_forward(const Plan& p, const int16_t* d_in, cudaStream_t st);
+// several measurements per matched-filter launch (grid z): measurement t reads
+// d_in + t x_stride and uses the half spectra Z + t z_stride (Z = nullptr: the
+// plan's single buffer), and writes a + t a_stride, A + t A_tstride
+struct MfBatch {
+    int n = 1;
+    size_t x_stride = 0;
+    float2* Z = nullptr;
+    size_t z_stride = 0, a_stride = 0, A_tstride = 0;
+};
+cudaError_t launch_mf_forward(const Plan& p, const int16_t* d_in, cudaStream_t st, const MfBatch& mb = MfBatch());
 // writes a (complex float) and/or a16 (BF16 pairs) and/or the in-band spectra A,
 // A_m[k'] at d_A[m a_ms + k' a_ks] (default a_ms = Kb, a_ks = 1)
 cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st, uint32_t* d_a16 = nullptr,
-                              int a_ms = -1, int a_ks = 1);
+                              int a_ms = -1, int a_ks = 1, const MfBatch& mb = MfBatch());
 cudaError_t launch_steering_table(Plan& p, cudaStream_t st);
 // bf16: tmap views BF16 pairs (4-byte elements) rather than complex floats
 cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, bool bf16, float* d_out, cudaStream_t st);
