@@ -484,6 +484,78 @@ def run_calibration(args, rank, world, local):
     plan.close()
 
 
+def run_paper_design(args, rank, world, local):
+    """The time-domain chain built the paper's way (cuFFT matched filter, one thread per
+    (direction, sample) delay-and-sum, envelope in device memory, separate low-pass kernel)
+    against the fused kernels, one measurement per step each."""
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2208_10839_gb300 import Plan, _native as nat
+    from paper_2208_10839_gb300 import build as _b
+    _b.build()
+    dev = torch.device("cuda", local)
+    cfg = synth.hemisphere(seed_scene=1 + 1000 * rank)
+    plan = Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"])
+    x = torch.from_numpy(cfg["x"]).to(dev)
+    E = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32, device=dev)
+    Eb = torch.empty_like(E)
+    plan.process(x, E)  # builds the steering table the baseline reads
+    b = nat.rtis_baseline_create(plan.handle)
+    flush = L2Flush(dev)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            flush(1.0)
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(args.steps):
+            flush(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            ms.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(c) for a, c in ms]
+
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        base_ms = timed(lambda: nat.rtis_baseline_process(b, x, Eb, sh))
+        fused_ms = timed(lambda: nat.rtis_process(plan.handle, x, E, sh))
+    torch.cuda.synchronize()
+    assert plan.sync() == 0
+    err = float((Eb - E).abs().max() / E.abs().max())
+    t_base, t_fused = sum(base_ms) / 1e3, sum(fused_ms) / 1e3
+    if world > 1:
+        t_base, t_fused = max_over_ranks([t_base, t_fused], dev)
+    nat.rtis_baseline_destroy(b)
+    line = {
+        "metric": "energyscapes/s, time-domain path, paper-style GPU design (cuFFT + per-sample DAS)",
+        "value": replica_rate(args.steps, world, t_base), "unit": "energyscapes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_base / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("matched filter + time-domain and frequency-domain DAS",
+                                                "time-domain path only"),
+                   "l2": "flushed between steps (512 MiB write, then a 256 MiB read so write-backs finish), "
+                         "outside the timed events"},
+        "fused_rtis_process": {"value": replica_rate(args.steps, world, t_fused), "unit": "energyscapes/s",
+                               "ms_per_step": 1e3 * t_fused / args.steps},
+        "speedup_fused_over_paper_design": t_base / t_fused,
+        "max_abs_diff_over_max": err,
+        "gpu_launches": 6 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def run_hemisphere_batched(args, rank, world, local):
     """B measurements per step through rtis_process_many: per measurement the matched
     filter and the time-domain energyscape, and for the whole batch the frequency-domain
@@ -674,11 +746,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-dirs", type=int, default=128, help="directions in the oracle's timed sample")
-    ap.add_argument("--workload", default="hemisphere", choices=["hemisphere", "fd_gemm", "ring", "calibration"],
+    ap.add_argument("--workload", default="hemisphere", choices=["hemisphere", "fd_gemm", "ring", "calibration", "paper_design"],
                     help="hemisphere: the energyscape chain (default); fd_gemm: the 1200-bin frequency-domain "
                          "beamforming GEMM (32 mics x 64 frames -> 2048 directions); ring: 8 sensors with "
                          "uneven lengths and direction sets in one autotuned, graph-replayed batch; calibration: "
-                         "energyscape + L2 loss + adjoint of a perturbed 32-mic array")
+                         "energyscape + L2 loss + adjoint of a perturbed 32-mic array; paper_design: the "
+                         "time-domain chain built the paper's way (cuFFT + per-sample DAS) vs the fused kernels")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--bins", type=int, default=1200, help="fd_gemm: frequency bins (1200 = the full workload)")
     ap.add_argument("--batch", type=int, default=64,
@@ -703,6 +776,8 @@ def main():
         return run_ring(args, rank, world, local)
     if args.workload == "calibration":
         return run_calibration(args, rank, world, local)
+    if args.workload == "paper_design":
+        return run_paper_design(args, rank, world, local)
     if args.batch > 1:
         return run_hemisphere_batched(args, rank, world, local)
 

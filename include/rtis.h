@@ -326,6 +326,23 @@ rtis_status rtis_fd_gemm_run(rtis_fd_gemm* g, const float* d_X, float* d_Y, void
 void rtis_fd_gemm_destroy(rtis_fd_gemm* g);
 
 /*
+ * Comparison baseline (not the product path): the time-domain chain built the
+ * way the paper's GPU implementation is described (Sec. 4.3) -- cuFFT
+ * convolutions for the matched filter, one thread per (direction, sample) for
+ * the delay-and-sum with the beam's envelope in device memory, then a separate
+ * low-pass/subsample kernel.  Same definitions and plan tables as
+ * rtis_process on the time-domain path; results agree to FP32 rounding.
+ *   rtis_baseline_create   -- cuFFT plans and work buffers for `plan`
+ *                             (M F floats, M (F/2+1) + M F complex, D N floats)
+ *   rtis_baseline_process  -- d_in int16 [M][N] -> d_out float [D][n_out]; the
+ *                             plan must have run once (its steering table)
+ */
+typedef struct rtis_baseline rtis_baseline;
+rtis_status rtis_baseline_create(rtis_baseline** out, const rtis_plan* plan);
+rtis_status rtis_baseline_process(rtis_baseline* b, const int16_t* d_in, float* d_out, void* stream);
+void rtis_baseline_destroy(rtis_baseline* b);
+
+/*
  * rtis_matched_filter_noalloc -- the matched filter of rtis_matched_filter
  * for callers that may not allocate device memory: code that runs where
  * cudaMalloc is not allowed or not wanted (a real-time loop that must never

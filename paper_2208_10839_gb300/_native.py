@@ -84,6 +84,9 @@ _PROTOS = {
     "rtis_set_calibration": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "rtis_backward": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "rtis_loss_l2": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "rtis_baseline_create": (C.c_int, [C.POINTER(_VP), _VP]),
+    "rtis_baseline_process": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "rtis_baseline_destroy": (None, [_VP]),
     "rtis_matched_filter_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, C.c_double, C.c_double,
                                               C.c_double, _VP, _VP, _VP]),
     "rtis_fd_gemm_create": (C.c_int, [C.POINTER(_VP), C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_float), C.c_int,
@@ -292,6 +295,20 @@ def rtis_backward(plan, d_in, d_grad_out, d_grad_xyz=None, d_grad_gain=None, d_g
 def rtis_loss_l2(plan, d_E, d_E_ref, d_grad_out, d_loss, stream=None):
     check(lib().rtis_loss_l2(plan, ptr(d_E), ptr(d_E_ref), ptr(d_grad_out), ptr(d_loss), stream_handle(stream)),
           "rtis_loss_l2")
+
+
+def rtis_baseline_create(plan):
+    out = _VP()
+    check(lib().rtis_baseline_create(C.byref(out), plan), "rtis_baseline_create")
+    return out.value
+
+
+def rtis_baseline_process(b, d_in, d_out, stream=None):
+    check(lib().rtis_baseline_process(b, ptr(d_in), ptr(d_out), stream_handle(stream)), "rtis_baseline_process")
+
+
+def rtis_baseline_destroy(b):
+    lib().rtis_baseline_destroy(b)
 
 
 def rtis_plan_sync(plan) -> int:
