@@ -59,7 +59,8 @@ typedef enum rtis_status {
     RTIS_ERR_UNSUPPORTED = 4,   /* valid request outside what this build implements */
     RTIS_ERR_TIMEOUT = 5,       /* a bounded device wait ran out (status word) */
     RTIS_ERR_NONFINITE = 6,     /* non-finite geometry, chirp or taps */
-    RTIS_ERR_DEVICE = 7         /* a device-side range check failed (status word) */
+    RTIS_ERR_DEVICE = 7,        /* a device-side range check failed (status word) */
+    RTIS_ERR_BUSY = 8           /* no free slot (rtis_stream_submit) */
 } rtis_status;
 
 /* Device status-word bits reported by rtis_plan_sync(). */
@@ -324,6 +325,36 @@ rtis_status rtis_fd_gemm_create(rtis_fd_gemm** out, const float* mic_xyz, int n_
                                 const float* gain, const float* delay_s, int precision);
 rtis_status rtis_fd_gemm_run(rtis_fd_gemm* g, const float* d_X, float* d_Y, void* stream);
 void rtis_fd_gemm_destroy(rtis_fd_gemm* g);
+
+/*
+ * Streaming service: the paper's sensor-to-processor queue (Sec. 3:
+ * measurements arrive at a fixed rate and are turned into images as they come)
+ * as a ring of `depth` pinned host slots around one plan.
+ *   rtis_stream_submit -- copies host_in (int16 [M][N], host memory, free again on
+ *                         return) into the next slot and queues its input copy,
+ *                         rtis_process and the copy of the energyscape (float
+ *                         [D][n_out]) into host_out; returns the ticket.  host_out
+ *                         must stay valid until the ticket is collected; page-locked
+ *                         memory keeps its copy asynchronous.  RTIS_ERR_BUSY when
+ *                         that slot's previous ticket has not been collected
+ *                         (collect tickets in submission order).
+ *   rtis_stream_wait   -- waits at most timeout_ms until `ticket`'s energyscape is
+ *                         in its host_out, then frees the slot; RTIS_ERR_TIMEOUT if
+ *                         not ready (the ticket stays valid).
+ * Input and result copies run on per-slot streams, the chain on one compute
+ * stream, so copies overlap other measurements' processing.  rtis_stream_create
+ * captures each slot's chain (the plan's path) into a CUDA graph that submit
+ * replays; the graphs read the plan's steering tables in place, so
+ * rtis_set_calibration between measurements takes effect.  While tickets are
+ * outstanding the plan's workspaces belong to the service: do not run the plan
+ * on another stream then.  Calls on one stream object are serialised
+ * internally.
+ */
+typedef struct rtis_stream rtis_stream;
+rtis_status rtis_stream_create(rtis_stream** out, rtis_plan* plan, int depth);
+rtis_status rtis_stream_submit(rtis_stream* s, const int16_t* host_in, float* host_out, int64_t* ticket);
+rtis_status rtis_stream_wait(rtis_stream* s, int64_t ticket, int timeout_ms);
+void rtis_stream_destroy(rtis_stream* s);
 
 /*
  * Comparison baseline (not the product path): the time-domain chain built the

@@ -23,6 +23,7 @@ RTIS_ERR_UNSUPPORTED = 4
 RTIS_ERR_TIMEOUT = 5
 RTIS_ERR_NONFINITE = 6
 RTIS_ERR_DEVICE = 7
+RTIS_ERR_BUSY = 8
 RTIS_DEV_DELAY_RANGE = 0x1
 RTIS_DEV_TIMEOUT = 0x2
 RTIS_DEV_NONFINITE = 0x4
@@ -87,6 +88,10 @@ _PROTOS = {
     "rtis_baseline_create": (C.c_int, [C.POINTER(_VP), _VP]),
     "rtis_baseline_process": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_baseline_destroy": (None, [_VP]),
+    "rtis_stream_create": (C.c_int, [C.POINTER(_VP), _VP, C.c_int]),
+    "rtis_stream_submit": (C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_int64)]),
+    "rtis_stream_wait": (C.c_int, [_VP, C.c_int64, C.c_int]),
+    "rtis_stream_destroy": (None, [_VP]),
     "rtis_matched_filter_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_int, C.c_double, C.c_double,
                                               C.c_double, _VP, _VP, _VP]),
     "rtis_fd_gemm_create": (C.c_int, [C.POINTER(_VP), C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_float), C.c_int,
@@ -309,6 +314,33 @@ def rtis_baseline_process(b, d_in, d_out, stream=None):
 
 def rtis_baseline_destroy(b):
     lib().rtis_baseline_destroy(b)
+
+
+def rtis_stream_create(plan, depth):
+    out = _VP()
+    check(lib().rtis_stream_create(C.byref(out), plan, int(depth)), "rtis_stream_create")
+    return out.value
+
+
+def _host_ptr(a) -> int:
+    """Address of a host array: a NumPy array or a (pinned) CPU torch tensor."""
+    return a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()
+
+
+def rtis_stream_submit(s, host_in, host_out) -> int:
+    """host_in: C-contiguous int16 [M][N]; host_out: C-contiguous float32 [D][n_out]
+    (pinned memory keeps the result copy asynchronous).  Returns the ticket."""
+    t = C.c_int64(-1)
+    check(lib().rtis_stream_submit(s, _host_ptr(host_in), _host_ptr(host_out), C.byref(t)), "rtis_stream_submit")
+    return t.value
+
+
+def rtis_stream_wait(s, ticket, timeout_ms=1000):
+    check(lib().rtis_stream_wait(s, int(ticket), int(timeout_ms)), "rtis_stream_wait")
+
+
+def rtis_stream_destroy(s):
+    lib().rtis_stream_destroy(s)
 
 
 def rtis_plan_sync(plan) -> int:

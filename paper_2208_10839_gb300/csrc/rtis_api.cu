@@ -144,6 +144,7 @@ const char* rtis_status_string(rtis_status s) {
         case RTIS_ERR_TIMEOUT: return "device wait timed out";
         case RTIS_ERR_NONFINITE: return "non-finite input";
         case RTIS_ERR_DEVICE: return "device-side check failed";
+        case RTIS_ERR_BUSY: return "no free slot";
     }
     return "unknown status";
 }

@@ -158,10 +158,12 @@ def render_echoes(mic_xyz, scene: Scene, n_samples: int, fs: float = FS, c: floa
 
 
 def quantise(clean, seed: int, snr_db: float = 20.0, full_scale: float = 30000.0):
-    """Add white Gaussian noise at snr_db (vs mean clean power) and round to int16."""
+    """Add white Gaussian noise at snr_db (vs mean clean power) and round to int16.
+    A recording with no echo in its window is noise alone (unit variance before
+    the full-scale normalisation), as a real sensor's would be."""
     clean = np.asarray(clean, dtype=np.float64)
     p_sig = float(np.mean(clean * clean))
-    sigma = math.sqrt(p_sig / 10.0 ** (snr_db / 10.0)) if p_sig > 0 else 0.0
+    sigma = math.sqrt(p_sig / 10.0 ** (snr_db / 10.0)) if p_sig > 0 else 1.0
     noisy = clean + sigma * _noise_rng(seed).normal(size=clean.shape)
     peak = float(np.max(np.abs(noisy)))
     scale = full_scale / peak if peak > 0 else 1.0

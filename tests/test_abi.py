@@ -126,3 +126,17 @@ def test_injected_allocation_and_launch_failures(nat, monkeypatch):
     assert lib.rtis_backward(None, None, None, None, None, None, None) == nat.RTIS_ERR_CUDA
     monkeypatch.setenv("RTIS_FAULT", "")
     assert lib.rtis_process(None, None, None, None) == nat.RTIS_ERR_INVALID_ARG
+
+
+def test_stream_and_baseline_argument_checks(nat):
+    lib = nat.lib()
+    import ctypes as C
+    out = C.c_void_p()
+    assert lib.rtis_stream_create(C.byref(out), None, 4) == nat.RTIS_ERR_INVALID_ARG
+    assert lib.rtis_stream_create(None, None, 4) == nat.RTIS_ERR_INVALID_ARG
+    t = C.c_int64(0)
+    assert lib.rtis_stream_submit(None, None, None, C.byref(t)) == nat.RTIS_ERR_INVALID_ARG
+    assert lib.rtis_stream_wait(None, 0, 10) == nat.RTIS_ERR_INVALID_ARG
+    assert lib.rtis_baseline_create(C.byref(out), None) == nat.RTIS_ERR_INVALID_ARG
+    assert lib.rtis_baseline_process(None, None, None, None) == nat.RTIS_ERR_INVALID_ARG
+    assert nat.rtis_status_string(nat.RTIS_ERR_BUSY) == "no free slot"

@@ -1,0 +1,81 @@
+"""Streaming service: measurements submitted from host memory come back, in
+submission order, bit-identical to rtis_process on the same plan; the ring
+refuses a submit when the slot's previous ticket is uncollected."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_10839_gb300 import build
+    build.build()
+    return torch
+
+
+def test_stream_results_match_process(torch_cuda):
+    torch = torch_cuda
+    from paper_2208_10839_gb300 import Plan, RtisError, _native as nat
+    cfgs = [synth.single_sensor(seed_scene=20 + i, n_samples=8192, n_dirs=48) for i in range(7)]
+    cfg = cfgs[0]
+    assert all(np.count_nonzero(c["x"]) > 0 for c in cfgs)
+    with Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], 8192) as p:
+        refs = [p.process(torch.from_numpy(c["x"]).cuda()).cpu().numpy() for c in cfgs]
+        s = nat.rtis_stream_create(p.handle, 3)
+        try:
+            # results go straight into the caller's buffers: pageable NumPy arrays for
+            # some, pinned torch tensors for others
+            outs = [np.full((p.D, p.n_out), np.nan, dtype=np.float32) if i % 2 else
+                    torch.full((p.D, p.n_out), float("nan")).pin_memory() for i in range(7)]
+            tickets = [nat.rtis_stream_submit(s, np.ascontiguousarray(c["x"]), outs[i]) for i, c in enumerate(cfgs[:3])]
+            with pytest.raises(RtisError) as ei:  # all three slots hold uncollected results
+                nat.rtis_stream_submit(s, np.ascontiguousarray(cfgs[3]["x"]), outs[3])
+            assert ei.value.status == nat.RTIS_ERR_BUSY
+            for i in range(7):  # collect the oldest, submit the next
+                nat.rtis_stream_wait(s, tickets[i], 5000)
+                if i + 3 < 7:
+                    tickets.append(nat.rtis_stream_submit(s, np.ascontiguousarray(cfgs[i + 3]["x"]), outs[i + 3]))
+            assert tickets == list(range(7))
+            with pytest.raises(RtisError):  # already collected
+                nat.rtis_stream_wait(s, tickets[0], 10)
+        finally:
+            nat.rtis_stream_destroy(s)
+        assert p.sync() == 0
+    for g, r in zip(outs, refs):
+        assert np.array_equal(np.asarray(g), r)
+
+
+def test_stream_sees_calibration_and_fd_path(torch_cuda):
+    """The captured graphs read the steering tables in place: a calibration set
+    after the stream was created changes the next result exactly as it changes
+    rtis_process.  The frequency-domain path streams the same way."""
+    torch = torch_cuda
+    from paper_2208_10839_gb300 import Plan, _native as nat
+    cfg = synth.single_sensor(seed_scene=31, n_samples=8192, n_dirs=40)
+    x = np.ascontiguousarray(cfg["x"])
+    assert np.count_nonzero(x) > 0
+    for path in ("td", "fd"):
+        with Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], 8192, path=path) as p:
+            s = nat.rtis_stream_create(p.handle, 2)
+            try:
+                out0 = np.empty((p.D, p.n_out), dtype=np.float32)
+                nat.rtis_stream_wait(s, nat.rtis_stream_submit(s, x, out0), 5000)
+                ref0 = p.process(torch.from_numpy(x).cuda()).cpu().numpy()
+                gain = torch.linspace(0.7, 1.3, p.M, device="cuda")
+                p.set_calibration(gain=gain)
+                torch.cuda.synchronize()
+                out1 = np.empty_like(out0)
+                nat.rtis_stream_wait(s, nat.rtis_stream_submit(s, x, out1), 5000)
+                ref1 = p.process(torch.from_numpy(x).cuda()).cpu().numpy()
+            finally:
+                nat.rtis_stream_destroy(s)
+            assert p.sync() == 0
+        assert np.array_equal(out0, ref0), path
+        assert np.array_equal(out1, ref1), path
+        assert not np.array_equal(out0, out1), path
