@@ -29,6 +29,17 @@ readings of the unstated details given in its docstring:
    b_d = IFFT_F(B_d)[0:N]
 5. envelope |b|, zero-phase low-pass FIR h (4R+1 taps) and subsampling by R
    (Sec. 4.3): E[d][i] = sum_j h[j] |b_d|[R i + j - 2R], i < floor(N/R)
+
+Complex-baseband variant (the paper subsamples the signal before the matched
+filter, Sec. 4.3; here the subsampling moves behind it, onto the demodulated
+analytic signal, where the 60 kHz band allows it):
+
+6. z_m[j] = a_m[Q j] exp(-j 2 pi k_c Q j / F), j < ceil(N/Q), with k_c the
+   mid-band bin (the analytic signal shifted to 0 Hz and kept every Q-th sample)
+7. b_d[j] = sum_m g_m exp(+j 2 pi k_c delta_dm / F) I(z_m, j + delta_dm / Q)
+   (the envelope delayed on the coarse grid, the carrier's phase exactly)
+8. E[d][i] = sum_j h_Ri(Q j - R i) |b_d[j]|: the same windowed-sinc low-pass
+   sampled at the coarse grid's offsets from R i, renormalised to unit DC gain
 """
 from __future__ import annotations
 
@@ -41,10 +52,13 @@ __all__ = [
     "lpf_adjoint", "energyscape_vjp",
     "steering_delays", "das_td", "das_td_bruteforce", "das_fd", "lpf_taps", "envelope_decimate",
     "energyscape", "steering_matrix", "fd_gemm", "DEFAULT_BAND", "DEFAULT_DECIM",
+    "DEFAULT_BB_DECIM", "baseband_centre_bin", "baseband_signal", "das_bb", "das_bb_bruteforce", "lpf_window",
+    "envelope_decimate_bb",
 ]
 
 DEFAULT_BAND = (20e3, 80e3)   # chirp band: the 80 -> 20 kHz sweep
 DEFAULT_DECIM = 10            # R: 8192 samples -> 8192/10 range bins
+DEFAULT_BB_DECIM = 4          # Q: baseband samples per full-rate sample (112.5 kHz complex rate)
 
 
 # --------------------------------------------------------------------------
@@ -245,15 +259,21 @@ def das_fd(A_band, k_lo: int, F: int, n_samples: int, delta, gain=None):
 # --------------------------------------------------------------------------
 # envelope, low-pass and subsampling (Fig. 3, Sec. 4.1, Sec. 4.3)
 # --------------------------------------------------------------------------
+def lpf_window(t, R: int = DEFAULT_DECIM):
+    """The envelope low-pass before normalisation, at full-rate offset t:
+    sinc(t/R) * (1 + cos(pi t/(2R+1)))/2 for |t| <= 2R, 0 beyond (a Hann
+    window whose zeros fall one sample beyond the ends)."""
+    t = np.asarray(t, dtype=np.float64)
+    return np.where(np.abs(t) <= 2 * R, np.sinc(t / R) * 0.5 * (1.0 + np.cos(np.pi * t / (2 * R + 1))), 0.0)
+
+
 def lpf_taps(R: int = DEFAULT_DECIM):
     """Zero-phase low-pass FIR for the envelope: 4R+1 taps, cutoff fs/(2R).
 
-    h[j] ~ sinc(t/R) * (1 + cos(pi t/(2R+1)))/2 with t = j - 2R (a Hann
-    window whose zeros fall one sample beyond the ends), scaled to unit DC
-    gain (sum h = 1).
+    h[j] = lpf_window(j - 2R), scaled to unit DC gain (sum h = 1).
     """
     t = np.arange(-2 * R, 2 * R + 1, dtype=np.float64)
-    h = np.sinc(t / R) * 0.5 * (1.0 + np.cos(np.pi * t / (2 * R + 1)))
+    h = lpf_window(t, R)
     return h / np.sum(h)
 
 
@@ -343,8 +363,9 @@ def energyscape_vjp(x_int16, chirp, mic_xyz, dirs, fs: float, c: float, G, gain=
 
 def energyscape(x_int16, chirp, mic_xyz, dirs, fs: float, c: float, path: str = "td",
                 R: int = DEFAULT_DECIM, gain=None, delay_s=None, band=DEFAULT_BAND, h=None,
-                return_stages: bool = False):
-    """Whole chain: int16 [M][N] -> energyscape E [D][floor(N/R)]."""
+                return_stages: bool = False, Q: int = DEFAULT_BB_DECIM):
+    """Whole chain: int16 [M][N] -> energyscape E [D][floor(N/R)].
+    path: "td" (steps 1-5 with das_td), "fd" (das_fd), "bb" (steps 6-8; Q, no h)."""
     N = np.asarray(x_int16).shape[1]
     delta = steering_delays(mic_xyz, dirs, fs, c, delay_s)
     h = lpf_taps(R) if h is None else np.asarray(h, dtype=np.float64)
@@ -355,11 +376,118 @@ def energyscape(x_int16, chirp, mic_xyz, dirs, fs: float, c: float, path: str = 
         A, k_lo, F = mf_spectrum(x_int16, chirp, fs, band)
         a = None
         b = das_fd(A, k_lo, F, N, delta, gain)
+    elif path == "bb":
+        a = matched_filter(x_int16, chirp, fs, band)
+        F = fft_length(N, np.asarray(chirp).shape[0])
+        k_c = baseband_centre_bin(*band_bins(F, fs, band))
+        z = baseband_signal(a, k_c, F, Q)
+        b = das_bb(z, delta, k_c, F, Q, gain)
+        E = envelope_decimate_bb(b, N, R, Q)
+        return (E, dict(a=a, z=z, b=b, delta=delta, k_c=k_c)) if return_stages else E
     else:
         raise ValueError(path)
     E = envelope_decimate(b, h, R)
     if return_stages:
         return E, dict(a=a, b=b, delta=delta, h=h)
+    return E
+
+
+# --------------------------------------------------------------------------
+# complex-baseband delay-and-sum (subsampling moved behind the matched filter)
+# --------------------------------------------------------------------------
+def baseband_centre_bin(k_lo: int, k_hi: int) -> int:
+    """k_c: the mid-band bin, floor((k_lo + k_hi) / 2); the band k_lo..k_hi maps to
+    about +-30 kHz around 0 after demodulation by k_c."""
+    return (int(k_lo) + int(k_hi)) // 2
+
+
+def baseband_signal(a, k_c: int, F: int, Q: int = DEFAULT_BB_DECIM):
+    """z_m[j] = a_m[Q j] exp(-j 2 pi k_c Q j / F) for j < ceil(N/Q).
+
+    a is the full-rate analytic matched-filter output (complex [M][N]); the
+    band-limited analytic signal demodulated to 0 Hz and kept every Q-th
+    sample.  Nothing is filtered: a's spectrum is already confined to the band.
+    """
+    a = np.asarray(a, dtype=np.complex128)
+    N = a.shape[1]
+    j = np.arange((N + Q - 1) // Q, dtype=np.float64)
+    return a[:, ::Q] * np.exp(-2j * np.pi * k_c * Q * j / F)[None, :]
+
+
+def das_bb(z, delta, k_c: int, F: int, Q: int = DEFAULT_BB_DECIM, gain=None):
+    """Baseband delay-and-sum on the coarse grid.
+
+    b_d[j] = sum_m g_m exp(+j 2 pi k_c delta_dm / F) sum_{q=-1..2} w_q(mu) z_m[J+q]
+    with u = j + delta_dm / Q, J = floor(u), mu = u - J (Catmull-Rom, as in
+    das_td), z_m = 0 outside [0, Nb).  Since a_m(t) = z_m(t/Q) exp(+j 2 pi k_c t/F),
+    |b_d[j]| approximates the full-rate |b_d[Q j]|: the envelope moves by the
+    interpolated delay, the carrier by its exact phase.
+    """
+    z = np.asarray(z, dtype=np.complex128)
+    delta = np.asarray(delta, dtype=np.float64)
+    M, Nb = z.shape
+    D = delta.shape[0]
+    g = np.ones(M) if gain is None else np.asarray(gain, dtype=np.float64)
+    dq = delta / Q
+    rot = g[None, :] * np.exp(2j * np.pi * k_c * delta / F)            # [D][M]
+    pad = int(math.ceil(np.max(np.abs(dq)))) + 4 if delta.size else 4
+    zp = _zero_padded(z, pad)
+    j = np.arange(Nb, dtype=np.float64)
+    b = np.zeros((D, Nb), dtype=np.complex128)
+    for m in range(M):
+        u = j[None, :] + dq[:, m:m + 1]
+        J = np.floor(u)
+        w = catmull_rom(u - J)
+        idx = J.astype(np.int64) + pad
+        s = w[0] * zp[m][idx - 1] + w[1] * zp[m][idx] + w[2] * zp[m][idx + 1] + w[3] * zp[m][idx + 2]
+        b += rot[:, m:m + 1] * s
+    return b
+
+
+def das_bb_bruteforce(z, delta, k_c: int, F: int, Q: int = DEFAULT_BB_DECIM, gain=None):
+    """Triple loop over (d, j, m) of the das_bb definition (tiny inputs only)."""
+    z = np.asarray(z, dtype=np.complex128)
+    M, Nb = z.shape
+    D = delta.shape[0]
+    g = np.ones(M) if gain is None else gain
+    b = np.zeros((D, Nb), dtype=np.complex128)
+    for d in range(D):
+        for j in range(Nb):
+            acc = 0j
+            for m in range(M):
+                dl = float(delta[d][m])
+                u = j + dl / Q
+                J = math.floor(u)
+                ws = catmull_rom(u - J)
+                s = 0j
+                for q, wq in zip((-1, 0, 1, 2), ws):
+                    if 0 <= J + q < Nb:
+                        s += float(wq) * z[m][J + q]
+                acc += g[m] * complex(math.cos(2 * math.pi * k_c * dl / F), math.sin(2 * math.pi * k_c * dl / F)) * s
+            b[d][j] = acc
+    return b
+
+
+def envelope_decimate_bb(b, n_samples: int, R: int = DEFAULT_DECIM, Q: int = DEFAULT_BB_DECIM):
+    """E[d][i] = sum_j h_i(Q j - R i) |b_d[j]| for i < floor(N/R).
+
+    b sits on the coarse grid (full-rate times Q j).  Output bin i keeps the
+    full-rate position R i; its taps are lpf_window at the offsets Q j - R i
+    that fall in [-2R, 2R], renormalised to sum 1 (unit DC gain, as lpf_taps).
+    |b| = 0 outside [0, Nb).  With Q = 1 this is envelope_decimate with lpf_taps(R).
+    """
+    env = np.abs(np.asarray(b))
+    D, Nb = env.shape
+    n_out = n_samples // R
+    E = np.zeros((D, n_out))
+    for i in range(n_out):
+        jlo = -((2 * R - R * i) // Q)          # ceil((R i - 2R) / Q)
+        jhi = (R * i + 2 * R) // Q
+        jj = np.arange(jlo, jhi + 1)
+        w = lpf_window(Q * jj - R * i, R)
+        w = w / np.sum(w)
+        ok = (jj >= 0) & (jj < Nb)
+        E[:, i] = env[:, jj[ok]] @ w[ok]
     return E
 
 

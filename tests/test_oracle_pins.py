@@ -358,3 +358,113 @@ def test_adjoint_gain_gradient_is_exact_for_linear_scaling():
     x, s, mic, dirs, gain, delay, G = _tiny_calibration_case()
     E, gx, gg, gd = orc.energyscape_vjp(x, s, mic, dirs, synth.FS, synth.C_SOUND, G, gain, delay)
     np.testing.assert_allclose(np.sum(gain * gg), np.sum(G * E), rtol=1e-10)
+
+
+# -------------------------------------------------------------- complex baseband
+def _tiny_mf_case(seed=21, M=2, N=103, L=40):
+    rng = np.random.default_rng(seed)
+    x = rng.integers(-20000, 20000, size=(M, N)).astype(np.int16)
+    return x, _short_chirp(L), 450e3
+
+
+def test_baseband_signal_is_the_shifted_band_sum():
+    # z_m[j] written as the inverse DFT of the in-band spectrum moved down by k_c and
+    # read at the coarse times Q j: an explicit double loop, no FFT and no matched_filter
+    x, s, fs = _tiny_mf_case()
+    A, k_lo, F = orc.mf_spectrum(x, s, fs)
+    k_hi = k_lo + A.shape[1] - 1
+    k_c = orc.baseband_centre_bin(k_lo, k_hi)
+    assert k_c == (k_lo + k_hi) // 2
+    for Q in (1, 2, 4):
+        z = orc.baseband_signal(orc.matched_filter(x, s, fs), k_c, F, Q)
+        Nb = (x.shape[1] + Q - 1) // Q
+        assert z.shape == (2, Nb)
+        ref = np.zeros_like(z)
+        for m in range(2):
+            for j in range(Nb):
+                acc = 0j
+                for kk in range(A.shape[1]):
+                    kap = k_lo + kk - k_c
+                    acc += A[m, kk] * complex(math.cos(2 * math.pi * kap * Q * j / F),
+                                              math.sin(2 * math.pi * kap * Q * j / F))
+                ref[m, j] = acc / F
+        np.testing.assert_allclose(z, ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+
+
+def test_das_bb_vectorised_equals_bruteforce():
+    rng = np.random.default_rng(22)
+    M, Nb, D, Q, F, k_c = 3, 40, 4, 4, 1024, 113
+    z = rng.normal(size=(M, Nb)) + 1j * rng.normal(size=(M, Nb))
+    delta = rng.uniform(-30, 30, size=(D, M))
+    delta[0, 0] = -0.5           # reads before sample 0
+    delta[1, 2] = 8.0            # a whole number of coarse samples
+    delta[2, 1] = 3.0            # whole on the fine grid only
+    g = rng.uniform(0.5, 1.5, size=M)
+    np.testing.assert_allclose(orc.das_bb(z, delta, k_c, F, Q, g), orc.das_bb_bruteforce(z, delta, k_c, F, Q, g),
+                               rtol=0, atol=1e-13)
+
+
+def test_das_bb_on_whole_coarse_delays_is_the_full_rate_beam():
+    # delta = Q J exactly: interpolation is the identity and the carrier phase
+    # exp(+j 2 pi k_c Q J / F) puts back what demodulation took out, so
+    # b_bb[j] exp(+j 2 pi k_c Q j / F) equals the full-rate beam at n = Q j
+    x, s, fs = _tiny_mf_case(seed=23, M=3, N=257)
+    a = orc.matched_filter(x, s, fs)
+    F = orc.fft_length(x.shape[1], s.size)
+    k_lo, k_hi = orc.band_bins(F, fs)
+    k_c = orc.baseband_centre_bin(k_lo, k_hi)
+    rng = np.random.default_rng(24)
+    for Q in (2, 4):
+        delta = (Q * rng.integers(-9, 10, size=(5, 3))).astype(np.float64)
+        g = rng.uniform(0.5, 1.5, size=3)
+        b_td = orc.das_td(a, delta, g)
+        b_bb = orc.das_bb(orc.baseband_signal(a, k_c, F, Q), delta, k_c, F, Q, g)
+        j = np.arange(b_bb.shape[1])
+        np.testing.assert_allclose(b_bb * np.exp(2j * np.pi * k_c * Q * j / F)[None, :], b_td[:, ::Q],
+                                   rtol=0, atol=1e-12 * np.max(np.abs(b_td)))
+
+
+def test_envelope_decimate_bb_with_q1_is_envelope_decimate():
+    rng = np.random.default_rng(25)
+    b = rng.normal(size=(3, 203)) + 1j * rng.normal(size=(3, 203))
+    for R in (7, 10):
+        np.testing.assert_allclose(orc.envelope_decimate_bb(b, 203, R, 1),
+                                   orc.envelope_decimate(b, orc.lpf_taps(R), R), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("R,Q", [(10, 4), (6, 4), (8, 4), (10, 2), (7, 4)])
+def test_envelope_decimate_bb_constant_and_ramp(R, Q):
+    # unit DC gain per output bin; and where every bin's coarse offsets Q j - R i
+    # are symmetric about 0 (R i = 0 or Q/2 mod Q for all i, i.e. Q divides 2R)
+    # a linear envelope comes back exactly at the bin's full-rate time R i
+    N = 1000
+    Nb = (N + Q - 1) // Q
+    n_out = N // R
+    interior = slice(3, n_out - 3)
+    E = orc.envelope_decimate_bb(np.full((1, Nb), 2.5 + 0j), N, R, Q)
+    np.testing.assert_allclose(E[0, interior], 2.5, rtol=1e-14)
+    E = orc.envelope_decimate_bb((Q * np.arange(Nb, dtype=float))[None, :] + 0j, N, R, Q)
+    i = np.arange(n_out)
+    if (2 * R) % Q == 0:
+        np.testing.assert_allclose(E[0, interior], (R * i)[interior], rtol=1e-13)
+    else:  # offsets not symmetric: the ramp is shifted by less than Q/2 full-rate samples
+        assert np.max(np.abs(E[0, interior] - (R * i)[interior])) < Q / 2
+
+
+def test_baseband_energyscape_tracks_exact_delays():
+    # the baseband chain against the exact-delay (frequency-domain) energyscape:
+    # same peak, and within 1% of the peak everywhere (its interpolation and
+    # coarse-envelope error; the full-rate Catmull-Rom chain is at the same level)
+    n0, M, d_star = 2000, 8, 37
+    x, s, mic, dirs, k = _plane_wave_case(n0, M, 4096, d_star)
+    E_bb = orc.energyscape(x, s, mic, dirs, FS, C, path="bb")
+    E_fd = orc.energyscape(x, s, mic, dirs, FS, C, path="fd")
+    assert E_bb.shape == E_fd.shape
+    d_pk, i_pk = np.unravel_index(np.argmax(E_bb), E_bb.shape)
+    assert (d_pk, i_pk) == (d_star, n0 // orc.DEFAULT_DECIM)
+    assert np.max(np.abs(E_bb - E_fd)) < 1e-2 * E_fd.max()
+    cfg = synth.single_sensor()
+    E_bb = orc.energyscape(cfg["x"], cfg["chirp"], cfg["mic_xyz"], cfg["dirs"], FS, C, path="bb")
+    E_fd = orc.energyscape(cfg["x"], cfg["chirp"], cfg["mic_xyz"], cfg["dirs"], FS, C, path="fd")
+    assert np.unravel_index(np.argmax(E_bb), E_bb.shape) == np.unravel_index(np.argmax(E_fd), E_fd.shape)
+    assert np.max(np.abs(E_bb - E_fd)) < 1e-2 * E_fd.max()
