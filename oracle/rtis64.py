@@ -368,6 +368,7 @@ def energyscape(x_int16, chirp, mic_xyz, dirs, fs: float, c: float, path: str = 
     path: "td" (steps 1-5 with das_td), "fd" (das_fd), "bb" (steps 6-8; Q, no h)."""
     N = np.asarray(x_int16).shape[1]
     delta = steering_delays(mic_xyz, dirs, fs, c, delay_s)
+    h_given = h
     h = lpf_taps(R) if h is None else np.asarray(h, dtype=np.float64)
     if path == "td":
         a = matched_filter(x_int16, chirp, fs, band)
@@ -382,7 +383,7 @@ def energyscape(x_int16, chirp, mic_xyz, dirs, fs: float, c: float, path: str = 
         k_c = baseband_centre_bin(*band_bins(F, fs, band))
         z = baseband_signal(a, k_c, F, Q)
         b = das_bb(z, delta, k_c, F, Q, gain)
-        E = envelope_decimate_bb(b, N, R, Q)
+        E = envelope_decimate_bb(b, N, R, Q, None if h_given is None else h)
         return (E, dict(a=a, z=z, b=b, delta=delta, k_c=k_c)) if return_stages else E
     else:
         raise ValueError(path)
@@ -468,23 +469,26 @@ def das_bb_bruteforce(z, delta, k_c: int, F: int, Q: int = DEFAULT_BB_DECIM, gai
     return b
 
 
-def envelope_decimate_bb(b, n_samples: int, R: int = DEFAULT_DECIM, Q: int = DEFAULT_BB_DECIM):
+def envelope_decimate_bb(b, n_samples: int, R: int = DEFAULT_DECIM, Q: int = DEFAULT_BB_DECIM, h=None):
     """E[d][i] = sum_j h_i(Q j - R i) |b_d[j]| for i < floor(N/R).
 
     b sits on the coarse grid (full-rate times Q j).  Output bin i keeps the
-    full-rate position R i; its taps are lpf_window at the offsets Q j - R i
-    that fall in [-2R, 2R], renormalised to sum 1 (unit DC gain, as lpf_taps).
-    |b| = 0 outside [0, Nb).  With Q = 1 this is envelope_decimate with lpf_taps(R).
+    full-rate position R i; its taps are the low-pass at the offsets
+    t = Q j - R i inside its support, renormalised to sum 1 (unit DC gain, as
+    lpf_taps): lpf_window(t, R) by default, or h[t + (len(h)-1)/2] for a given
+    odd-length h.  |b| = 0 outside [0, Nb).  With Q = 1 this is envelope_decimate.
     """
     env = np.abs(np.asarray(b))
     D, Nb = env.shape
+    half = 2 * R if h is None else (len(h) - 1) // 2
     n_out = n_samples // R
     E = np.zeros((D, n_out))
     for i in range(n_out):
-        jlo = -((2 * R - R * i) // Q)          # ceil((R i - 2R) / Q)
-        jhi = (R * i + 2 * R) // Q
+        jlo = -((half - R * i) // Q)           # ceil((R i - half) / Q)
+        jhi = (R * i + half) // Q
         jj = np.arange(jlo, jhi + 1)
-        w = lpf_window(Q * jj - R * i, R)
+        t = Q * jj - R * i
+        w = lpf_window(t, R) if h is None else np.asarray(h, dtype=np.float64)[t + half]
         w = w / np.sum(w)
         ok = (jj >= 0) & (jj < Nb)
         E[:, i] = env[:, jj[ok]] @ w[ok]

@@ -430,6 +430,12 @@ def test_envelope_decimate_bb_with_q1_is_envelope_decimate():
     for R in (7, 10):
         np.testing.assert_allclose(orc.envelope_decimate_bb(b, 203, R, 1),
                                    orc.envelope_decimate(b, orc.lpf_taps(R), R), rtol=0, atol=1e-14)
+    # given taps (any odd length, unnormalised) are read at the offsets and renormalised
+    h = rng.uniform(0.1, 1.0, size=9)
+    np.testing.assert_allclose(orc.envelope_decimate_bb(b, 203, 5, 1, h),
+                               orc.envelope_decimate(b, h / h.sum(), 5), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(orc.envelope_decimate_bb(b, 203, 10, 4, orc.lpf_taps(10)),
+                               orc.envelope_decimate_bb(b, 203, 10, 4), rtol=0, atol=1e-14)
 
 
 @pytest.mark.parametrize("R,Q", [(10, 4), (6, 4), (8, 4), (10, 2), (7, 4)])
