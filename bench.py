@@ -626,6 +626,103 @@ def run_paper_design(args, rank, world, local):
     plan.close()
 
 
+def run_baseband(args, rank, world, local):
+    """The complex-baseband path (the analytic signal demodulated to 0 Hz and beamformed on
+    every 4th sample) against the full-rate time-domain path, one measurement per step each;
+    the baseband beamformer's roofline from its own stage entry point."""
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2208_10839_gb300 import Plan, _native as nat
+    from paper_2208_10839_gb300 import build as _b
+    _b.build()
+    dev = torch.device("cuda", local)
+    cfg = synth.hemisphere(seed_scene=1 + 1000 * rank)
+    mk = lambda path: Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"], path=path)
+    p_bb, p_td, p_fd = mk("bb"), mk("td"), mk("fd")
+    x = torch.from_numpy(cfg["x"]).to(dev)
+    E_bb = torch.empty((N_DIRS, p_bb.n_out), dtype=torch.float32, device=dev)
+    E_td, E_fd, E_st = torch.empty_like(E_bb), torch.empty_like(E_bb), torch.empty_like(E_bb)
+    z = p_bb.baseband_signal(x)
+    a, _ = p_td.matched_filter(x)
+    flush = L2Flush(dev)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            flush(1.0)
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(args.steps):
+            flush(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            ms.append((e0, e1))
+        torch.cuda.synchronize()
+        return [q.elapsed_time(r) for q, r in ms]
+
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        bb_ms = timed(lambda: nat.rtis_process(p_bb.handle, x, E_bb, sh))
+        td_ms = timed(lambda: nat.rtis_process(p_td.handle, x, E_td, sh))
+        bbk_ms = timed(lambda: nat.rtis_beamform_bb(p_bb.handle, z, E_st, sh))
+        tdk_ms = timed(lambda: nat.rtis_beamform_td(p_td.handle, a, E_st, sh))
+    nat.rtis_process(p_fd.handle, x, E_fd, sh)
+    torch.cuda.synchronize()
+    for p_ in (p_bb, p_td, p_fd):
+        assert p_.sync() == 0
+    peak = float(E_fd.abs().max())
+    err_fd = float((E_bb - E_fd).abs().max()) / peak
+    err_td_fd = float((E_td - E_fd).abs().max()) / peak
+    t_bb, t_td = sum(bb_ms) / 1e3, sum(td_ms) / 1e3
+    if world > 1:
+        t_bb, t_td = max_over_ranks([t_bb, t_td], dev)
+    clocks = clk.summary()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tf = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    Nb = N_SAMPLES // 4
+    # per (direction, coarse sample, mic): 4 Catmull-Rom taps on (re, im) = 16 flop, and the
+    # carrier rotation and accumulation, complex x complex + add = 8 flop
+    bb_flops = float(N_DIRS) * Nb * N_MICS * 24
+    td_flops = float(N_DIRS) * N_SAMPLES * N_MICS * 4 * 2 * 2
+    bbk_s, tdk_s = statistics.mean(bbk_ms) / 1e3, statistics.mean(tdk_ms) / 1e3
+    ach = bb_flops / bbk_s / 1e12
+    line = {
+        "metric": "energyscapes/s, complex-baseband path (demodulated, every 4th sample)",
+        "value": replica_rate(args.steps, world, t_bb), "unit": "energyscapes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_bb / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("matched filter + time-domain and frequency-domain DAS",
+                                                "matched filter + complex-baseband DAS (Q = 4)"),
+                   "l2": "flushed between steps (512 MiB write, then a 256 MiB read so write-backs finish), "
+                         "outside the timed events"},
+        "td_rtis_process": {"value": replica_rate(args.steps, world, t_td), "unit": "energyscapes/s",
+                            "ms_per_step": 1e3 * t_td / args.steps},
+        "speedup_bb_over_td_chain": t_td / t_bb,
+        "beamformer_ms": {"bb_beamform_kernel": bbk_s * 1e3, "td_beamform_kernel": tdk_s * 1e3,
+                          "speedup": tdk_s / bbk_s},
+        "max_abs_diff_over_peak_vs_exact_delay_fd": {"bb": err_fd, "td": err_td_fd},
+        "roofline": {"bound": "alu", "kernel": "bb_beamform_kernel", "achieved": ach, "peak": peak_tf,
+                     "unit": "TFLOP/s", "frac": ach / peak_tf, "traffic": None,
+                     "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x "
+                                   f"{SM_MAX_MHZ_NOMINAL:.0f} MHz",
+                     "algorithmic_flops_per_launch": bb_flops, "launch_ms": bbk_s * 1e3,
+                     "td_equivalent": {"flops": td_flops, "frac": td_flops / tdk_s / 1e12 / peak_tf}},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for p_ in (p_bb, p_td, p_fd):
+        p_.close()
+
+
 def run_hemisphere_batched(args, rank, world, local):
     """B measurements per step through rtis_process_many: per measurement the matched
     filter and the time-domain energyscape, and for the whole batch the frequency-domain
@@ -816,7 +913,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-dirs", type=int, default=128, help="directions in the oracle's timed sample")
-    ap.add_argument("--workload", default="hemisphere", choices=["hemisphere", "fd_gemm", "ring", "calibration", "paper_design", "stream"],
+    ap.add_argument("--workload", default="hemisphere", choices=["hemisphere", "fd_gemm", "ring", "calibration", "paper_design", "stream",
+                                                               "baseband"],
                     help="hemisphere: the energyscape chain (default); fd_gemm: the 1200-bin frequency-domain "
                          "beamforming GEMM (32 mics x 64 frames -> 2048 directions); ring: 8 sensors with "
                          "uneven lengths and direction sets in one autotuned, graph-replayed batch; calibration: "
@@ -849,6 +947,8 @@ def main():
         return run_calibration(args, rank, world, local)
     if args.workload == "paper_design":
         return run_paper_design(args, rank, world, local)
+    if args.workload == "baseband":
+        return run_baseband(args, rank, world, local)
     if args.workload == "stream":
         return run_stream(args, rank, world, local)
     if args.batch > 1:

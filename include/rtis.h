@@ -82,7 +82,7 @@ typedef enum rtis_status {
  *                RTIS_ERR_TIMEOUT and the context stays usable.
  */
 
-enum { RTIS_PATH_TD = 0, RTIS_PATH_FD = 1 };
+enum { RTIS_PATH_TD = 0, RTIS_PATH_FD = 1, RTIS_PATH_BB = 2 };
 enum { RTIS_PREC_FP32 = 0, RTIS_PREC_BF16 = 1, RTIS_PREC_FP16 = 2 };
 
 typedef struct rtis_options {
@@ -92,7 +92,7 @@ typedef struct rtis_options {
     const float* lpf_taps;       /* host [lpf_len]; NULL -> sinc(t/R) x Hann, sum 1 */
     double band_lo_hz;           /* matched-filter band (default 20e3) */
     double band_hi_hz;           /* (default 80e3) */
-    int path;                    /* RTIS_PATH_TD (default) or RTIS_PATH_FD */
+    int path;                    /* RTIS_PATH_TD (default), RTIS_PATH_FD or RTIS_PATH_BB */
     int precision;               /* storage of the analytic signal a on the TD path:
                                     RTIS_PREC_FP32 (default) or RTIS_PREC_BF16 (a rounded
                                     to BF16 pairs, half the staged bytes; products and sums
@@ -147,10 +147,22 @@ rtis_status rtis_plan_get_info(const rtis_plan* plan, rtis_plan_info* info);
 
 /*
  * rtis_process -- whole chain for one recording (Fig. 3): matched filter,
- * delay-and-sum on the plan's path (TD or FD), envelope, low-pass, subsample.
- * The FD path (opt.path = RTIS_PATH_FD) needs F <= 32768.  With
- * opt.precision = RTIS_PREC_BF16 the TD path beamforms from a BF16 copy of a
- * (relative error ~2^-9 per sample; energyscape within 1e-2 of the peak).
+ * delay-and-sum on the plan's path, envelope, low-pass, subsample.
+ *   RTIS_PATH_TD  Catmull-Rom fractional delays on the full-rate analytic signal.
+ *   RTIS_PATH_FD  exact phase ramps on the in-band spectrum; needs F <= 32768.
+ *   RTIS_PATH_BB  complex baseband: the paper subsamples before its filters
+ *                 (Sec. 4.3); this path subsamples after the matched filter.
+ *                 The analytic signal, demodulated by the mid-band bin
+ *                 k_c = floor((k_lo + k_hi)/2), is kept at every 4th sample:
+ *                 z_m[j] = a_m[4j] e^{-2 pi i k_c 4j/F}.  The beam is formed on
+ *                 that grid, b_d[j] = sum_m g_m e^{+2 pi i k_c delta_dm/F}
+ *                 I(z_m, j + delta_dm/4) with I the Catmull-Rom interpolation.
+ *                 The result is E[d][i] = sum_j h_i(4j - R i) |b_d[j]|, with h_i
+ *                 the plan's low-pass taps at those offsets, renormalised to
+ *                 sum 1.  It approximates the TD/FD energyscape to about 1e-2 of
+ *                 its peak, at 2.7x fewer multiply-adds.
+ * With opt.precision = RTIS_PREC_BF16 the TD path beamforms from a BF16 copy
+ * of a (relative error ~2^-9 per sample; energyscape within 1e-2 of the peak).
  *   d_in   device int16 [n_mics][n_samples], 8-byte aligned
  *   d_out  device float [n_dirs][n_out]
  */
@@ -202,6 +214,26 @@ rtis_status rtis_beamform_td(rtis_plan* plan, const float* d_a, float* d_out, vo
  *   d_out  device float [n_dirs][n_out]
  */
 rtis_status rtis_beamform_fd(rtis_plan* plan, const float* d_A, float* d_out, void* stream);
+
+/*
+ * rtis_baseband_signal -- the matched filter of a RTIS_PATH_BB plan, ending in
+ * the demodulated analytic signal on the coarse grid (see rtis_process):
+ *   d_in   device int16 [n_mics][n_samples], 8-byte aligned
+ *   d_z    device complex float [n_mics][n_samples/4], 8-byte aligned:
+ *          z_m[j] = a_m[4j] e^{-2 pi i k_c 4j/F}, k_c = floor((k_lo + k_hi)/2)
+ * RTIS_ERR_UNSUPPORTED on a plan of another path.
+ */
+rtis_status rtis_baseband_signal(rtis_plan* plan, const int16_t* d_in, float* d_z, void* stream);
+
+/*
+ * rtis_beamform_bb -- the baseband delay-and-sum with the fused envelope and
+ * coarse-grid low-pass of a RTIS_PATH_BB plan, from rtis_baseband_signal's z.
+ *   d_z    device complex float [n_mics][n_samples/4], 16-byte aligned;
+ *          n_samples/4 must be even (16-byte rows) -- else RTIS_ERR_UNSUPPORTED
+ *          (rtis_process has no such limit)
+ *   d_out  device float [n_dirs][n_out]
+ */
+rtis_status rtis_beamform_bb(rtis_plan* plan, const float* d_z, float* d_out, void* stream);
 
 /*
  * rtis_steering_table -- the plan's per-(direction, mic) fractional-delay

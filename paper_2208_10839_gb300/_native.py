@@ -27,7 +27,7 @@ RTIS_ERR_BUSY = 8
 RTIS_DEV_DELAY_RANGE = 0x1
 RTIS_DEV_TIMEOUT = 0x2
 RTIS_DEV_NONFINITE = 0x4
-RTIS_PATH_TD, RTIS_PATH_FD = 0, 1
+RTIS_PATH_TD, RTIS_PATH_FD, RTIS_PATH_BB = 0, 1, 2
 RTIS_PREC_FP32, RTIS_PREC_BF16, RTIS_PREC_FP16 = 0, 1, 2
 
 
@@ -80,6 +80,8 @@ _PROTOS = {
     "rtis_matched_filter": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "rtis_beamform_td": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_beamform_fd": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "rtis_baseband_signal": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "rtis_beamform_bb": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_steering_table": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_plan_sync": (C.c_int, [_VP, C.POINTER(C.c_uint)]),
     "rtis_set_calibration": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
@@ -207,6 +209,14 @@ def rtis_beamform_td(plan, d_a, d_out, stream=None):
 
 def rtis_beamform_fd(plan, d_A, d_out, stream=None):
     check(lib().rtis_beamform_fd(plan, ptr(d_A), ptr(d_out), stream_handle(stream)), "rtis_beamform_fd")
+
+
+def rtis_baseband_signal(plan, d_in, d_z, stream=None):
+    check(lib().rtis_baseband_signal(plan, ptr(d_in), ptr(d_z), stream_handle(stream)), "rtis_baseband_signal")
+
+
+def rtis_beamform_bb(plan, d_z, d_out, stream=None):
+    check(lib().rtis_beamform_bb(plan, ptr(d_z), ptr(d_out), stream_handle(stream)), "rtis_beamform_bb")
 
 
 def rtis_steering_table(plan, d_shift, d_weight, stream=None):

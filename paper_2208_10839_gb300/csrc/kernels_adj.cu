@@ -44,19 +44,9 @@ struct AdjArgs {
     int M, N, D, R, lpf_len, n_out, H, row, nbox, bins_per_tile, seg;
 };
 
-__device__ __forceinline__ uint64_t pack2a(float x, float y) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
-    return r;
-}
-__device__ __forceinline__ float2 unpack2a(uint64_t v) {
-    float x, y;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
-    return make_float2(x, y);
-}
-__device__ __forceinline__ void fma2a(uint64_t& acc, uint64_t ww, uint64_t v) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(ww), "l"(v));
-}
+using ptx::fma2;
+using ptx::pack2;
+using ptx::unpack2;
 
 // forward: one mic's contribution to a lane's T samples (as the forward kernel)
 template <bool ODD>
@@ -73,10 +63,10 @@ __device__ __forceinline__ void adj_fwd_mic(uint64_t (&acc)[kTdOutPerThread], co
     }
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        fma2a(acc[t], w0, v[t + ODD]);
-        fma2a(acc[t], w1, v[t + 1 + ODD]);
-        fma2a(acc[t], w2, v[t + 2 + ODD]);
-        fma2a(acc[t], w3, v[t + 3 + ODD]);
+        fma2(acc[t], w0, v[t + ODD]);
+        fma2(acc[t], w1, v[t + 1 + ODD]);
+        fma2(acc[t], w2, v[t + 2 + ODD]);
+        fma2(acc[t], w3, v[t + 3 + ODD]);
     }
 }
 
@@ -98,12 +88,12 @@ __device__ __forceinline__ float4 adj_corr_mic(const uint64_t (&gb)[kTdOutPerThr
 #pragma unroll
     for (int t = 0; t < T; ++t) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) fma2a(c[q][t & 1], gb[t], v[t + q + ODD]);
+        for (int q = 0; q < 4; ++q) fma2(c[q][t & 1], gb[t], v[t + q + ODD]);
     }
     float r[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const float2 e = unpack2a(c[q][0]), o = unpack2a(c[q][1]);
+        const float2 e = unpack2(c[q][0]), o = unpack2(c[q][1]);
         r[q] = (e.x + e.y) + (o.x + o.y);
     }
     return make_float4(r[0], r[1], r[2], r[3]);
@@ -220,9 +210,9 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
                     const float f2 = g * __shfl_sync(0xffffffffu, my_w.z, m);
                     const float f3 = g * __shfl_sync(0xffffffffu, my_w.w, m);
                     if (s0 & 1)
-                        adj_fwd_mic<true>(acc, p, pack2a(f0, f0), pack2a(f1, f1), pack2a(f2, f2), pack2a(f3, f3));
+                        adj_fwd_mic<true>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
                     else
-                        adj_fwd_mic<false>(acc, p, pack2a(f0, f0), pack2a(f1, f1), pack2a(f2, f2), pack2a(f3, f3));
+                        adj_fwd_mic<false>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
                 }
             } else {
                 // both mics of the stage, then one joint reduction of their (value, slope) sums
@@ -287,10 +277,10 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
                     int j = 2 * half - r_lo;  // tap of bin i_lo
                     for (int i = i_lo; i <= i_hi; ++i, j -= R) ge = fmaf(gs[i - iseg0], hs[j], ge);
                 }
-                const float2 v = unpack2a(acc[t]);
+                const float2 v = unpack2(acc[t]);
                 const float m2 = v.x * v.x + v.y * v.y;
                 const float sc = m2 > 0.f ? ge * rsqrtf(m2) : 0.f;
-                acc[t] = pack2a(sc * v.x, sc * v.y);
+                acc[t] = pack2(sc * v.x, sc * v.y);
                 // n -> n + 1
                 if (--r_lo < 0) {
                     r_lo += R;

@@ -42,7 +42,9 @@ __global__ void steering_table_kernel(const float* __restrict__ mic, const float
                                       int M, int D, double fs, double fs_over_c, int Jlim, double inv_F,
                                       int* __restrict__ shift, float4* __restrict__ wt,
                                       float2* __restrict__ dphase, float4* __restrict__ wraw,
-                                      float4* __restrict__ wder, unsigned* __restrict__ status) {
+                                      float4* __restrict__ wder, unsigned* __restrict__ status, int k_c, int Jlim_b,
+                                      int* __restrict__ bshift, float4* __restrict__ bwt,
+                                      float2* __restrict__ brot) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= M * D) return;
     const int d = idx / M;
@@ -85,23 +87,39 @@ __global__ void steering_table_kernel(const float* __restrict__ mic, const float
     const double dp = delta * inv_F;
     const float dp_hi = static_cast<float>(dp);
     dphase[idx] = make_float2(dp_hi, static_cast<float>(dp - dp_hi));
+    if (bshift) {
+        // baseband form: Catmull-Rom on the coarse grid at delta / 4, and the carrier's
+        // phase 2 pi k_c delta / F (cycles reduced to [0, 1) before the sine)
+        const double u = 0.25 * delta;
+        const double jb = floor(u);
+        const double nu = u - jb, nu2 = nu * nu, nu3 = nu2 * nu;
+        float4 bw = make_float4(static_cast<float>(0.5 * (-nu3 + 2.0 * nu2 - nu)),
+                                static_cast<float>(0.5 * (3.0 * nu3 - 5.0 * nu2 + 2.0)),
+                                static_cast<float>(0.5 * (-3.0 * nu3 + 4.0 * nu2 + nu)),
+                                static_cast<float>(0.5 * (nu3 - nu2)));
+        double cyc = static_cast<double>(k_c) * dp;
+        cyc -= floor(cyc);
+        double sn, cs;
+        sincospi(2.0 * cyc, &sn, &cs);
+        const double gm = static_cast<double>(gain[m]);
+        float2 r = make_float2(static_cast<float>(gm * cs), static_cast<float>(gm * sn));
+        int jbi = 0;
+        if (fabs(jb) <= static_cast<double>(Jlim_b)) {
+            jbi = static_cast<int>(jb);
+        } else {
+            atomicOr(status, RTIS_DEV_DELAY_RANGE);
+            bw = make_float4(0.f, 0.f, 0.f, 0.f);
+            r = make_float2(0.f, 0.f);
+        }
+        bshift[idx] = jbi;
+        bwt[idx] = bw;
+        brot[idx] = r;
+    }
 }
 
-// packed pair helpers: a 64-bit register holding (re, im) of one complex sample
-__device__ __forceinline__ uint64_t pack2(float x, float y) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
-    return r;
-}
-__device__ __forceinline__ float2 unpack2(uint64_t v) {
-    float x, y;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
-    return make_float2(x, y);
-}
-// acc += (w, w) * v   -- one packed FP32 FMA on (re, im)
-__device__ __forceinline__ void fma2(uint64_t& acc, uint64_t ww, uint64_t v) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(ww), "l"(v));
-}
+using ptx::fma2;
+using ptx::pack2;
+using ptx::unpack2;
 
 // One mic's contribution to a lane's T samples.  `p` points at the 16-byte
 // aligned pair holding the first tap (or the sample before it when ODD).
@@ -352,7 +370,8 @@ cudaError_t launch_steering_table(Plan& p, cudaStream_t st) {
     const int nt = 256;
     steering_table_kernel<<<(total + nt - 1) / nt, nt, 0, st>>>(p.d_mic, p.d_dirs, p.d_gain, p.d_delay, p.M, p.D,
                                                               p.fs, p.fs / p.c, p.Jlim, 1.0 / p.F, p.d_shift,
-                                                              p.d_wt, p.d_dphase, p.d_wraw, p.d_wder, p.d_status);
+                                                              p.d_wt, p.d_dphase, p.d_wraw, p.d_wder, p.d_status,
+                                                              p.k_c, p.bb_Jlim, p.d_bshift, p.d_bwt, p.d_brot);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) p.table_dirty = false;
     return e;

@@ -9,6 +9,8 @@
 //   inverse  The band lies below F/4, so with n = 4p + q:
 //            a_m[n] = w_F^{k_lo n} IDFT_P( A_m[k_lo + k'] w_F^{k' q} )[p]
 //            -- four P-point inverse FFTs per channel, one per phase q.
+//   baseband z_m[j] = a_m[4j] exp(-2 pi i k_c 4j / F)
+//            = w_F^{(k_c - k_lo) 4j} IDFT_P( A_m[k_lo + k'] )[j]: phase 0 alone.
 //
 // Each P-point FFT runs in shared memory as a mixed-radix Stockham
 // autosort FFT (radix 16 passes plus one smaller pass), each thread holding
@@ -66,7 +68,9 @@ __global__ void __launch_bounds__(kMfThreads) mf_inverse_kernel(const float2* __
                                                                 float2* __restrict__ a,
                                                                 float2* __restrict__ A_out,
                                                                 uint32_t* __restrict__ a16, int a_ms, int a_ks,
-                                                                size_t z_stride, size_t a_stride, size_t A_tstride) {
+                                                                size_t z_stride, size_t a_stride, size_t A_tstride,
+                                                                float2* __restrict__ zb, int Nb, int zb_stride,
+                                                                int k_c) {
     extern __shared__ float2 sbuf[];
     constexpr int P = 1 << LOGP;
     const int m = blockIdx.x, q = blockIdx.y;
@@ -101,10 +105,18 @@ __global__ void __launch_bounds__(kMfThreads) mf_inverse_kernel(const float2* __
         }
         sbuf[spad(kp)] = g;
     }
-    if (a == nullptr && a16 == nullptr) return;  // spectrum only (uniform across the block)
+    if (a == nullptr && a16 == nullptr && zb == nullptr) return;  // spectrum only (uniform across the block)
     __syncthreads();
     fft_smem<LOGP, true, kMfThreads>(sbuf, GlobalTwiddles{tw}, F);
     const unsigned fmask = static_cast<unsigned>(F - 1);
+    if (zb) {  // baseband (grid y = 1, q = 0): demodulate by k_c, keep every 4th sample
+        const unsigned sh = static_cast<unsigned>(k_lo - k_c);  // (k_lo - k_c) mod 2^32
+        for (int p = threadIdx.x; p < Nb; p += kMfThreads) {
+            const unsigned idx = (sh * (4u * static_cast<unsigned>(p))) & fmask;
+            zb[static_cast<size_t>(m) * zb_stride + p] = cmul(sbuf[spad(p)], conjf2(__ldg(tw + idx)));
+        }
+        return;
+    }
     for (int p = threadIdx.x; p < P; p += kMfThreads) {
         const int n = 4 * p + q;
         if (n < N) {
@@ -145,11 +157,38 @@ cudaError_t mf_inverse_t(const Plan& p, float2* d_a, float2* d_A, uint32_t* d_a1
     const int nq = (d_a || d_a16) ? 4 : 1;
     mf_inverse_kernel<LOGP><<<dim3(p.M, nq, mb.n), kMfThreads, sm, st>>>(
         mb.Z ? mb.Z : p.d_Z, p.d_C, p.d_tw, p.F, p.k_lo, p.Kb, p.N, d_a, d_A, d_a16, a_ms, a_ks, mb.z_stride,
-        mb.a_stride, mb.A_tstride);
+        mb.a_stride, mb.A_tstride, nullptr, 0, 0, 0);
+    return cudaGetLastError();
+}
+
+template <int LOGP>
+cudaError_t mf_inverse_bb_t(const Plan& p, float2* d_z, int stride, cudaStream_t st) {
+    const size_t sm = mf_smem<LOGP>();
+    cudaError_t e = cudaFuncSetAttribute(mf_inverse_kernel<LOGP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sm));
+    if (e != cudaSuccess) return e;
+    mf_inverse_kernel<LOGP><<<dim3(p.M, 1, 1), kMfThreads, sm, st>>>(p.d_Z, p.d_C, p.d_tw, p.F, p.k_lo, p.Kb, p.N,
+                                                                      nullptr, nullptr, nullptr, p.Kb, 1, 0, 0, 0,
+                                                                      d_z, p.Nb, stride, p.k_c);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t launch_mf_inverse_bb(const Plan& p, float2* d_z, int stride, cudaStream_t st) {
+    switch (p.logP) {
+        case 6: return mf_inverse_bb_t<6>(p, d_z, stride, st);
+        case 7: return mf_inverse_bb_t<7>(p, d_z, stride, st);
+        case 8: return mf_inverse_bb_t<8>(p, d_z, stride, st);
+        case 9: return mf_inverse_bb_t<9>(p, d_z, stride, st);
+        case 10: return mf_inverse_bb_t<10>(p, d_z, stride, st);
+        case 11: return mf_inverse_bb_t<11>(p, d_z, stride, st);
+        case 12: return mf_inverse_bb_t<12>(p, d_z, stride, st);
+        case 13: return mf_inverse_bb_t<13>(p, d_z, stride, st);
+        case 14: return mf_inverse_bb_t<14>(p, d_z, stride, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_mf_forward(const Plan& p, const int16_t* d_in, cudaStream_t st, const MfBatch& mb) {
     switch (p.logP) {

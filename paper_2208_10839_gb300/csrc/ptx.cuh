@@ -197,5 +197,28 @@ __host__ __device__ constexpr uint32_t idesc_f16(uint32_t fmt, uint32_t M, uint3
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
+// packed pairs: one 64-bit register holding two FP32 lanes, e.g. (re, im) of a
+// complex sample, for the f32x2 arithmetic of sm_100 and later
+__device__ __forceinline__ uint64_t pack2(float x, float y) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(uint64_t v) {
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+    return make_float2(x, y);
+}
+// acc += w * v, lane by lane (one packed FP32 FMA)
+__device__ __forceinline__ void fma2(uint64_t& acc, uint64_t w, uint64_t v) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(w), "l"(v));
+}
+// w * v, lane by lane
+__device__ __forceinline__ uint64_t mul2(uint64_t w, uint64_t v) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(w), "l"(v));
+    return r;
+}
+
 }  // namespace ptx
 }  // namespace rtis

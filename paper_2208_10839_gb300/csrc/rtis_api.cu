@@ -33,7 +33,8 @@ cudaError_t dev_alloc(T** ptr, size_t count, size_t* total) {
 void free_plan_buffers(Plan& p) {
     void* bufs[] = {p.d_mic, p.d_dirs, p.d_gain, p.d_delay, p.d_tw, p.d_C, p.d_h,
                     p.d_shift, p.d_wt, p.d_dphase, p.d_wraw, p.d_wder, p.d_adj, p.d_adj_red, p.d_Z, p.d_a, p.d_A, p.d_a16,
-                    p.d_X, p.d_Y, p.d_kbin, p.d_xmax, p.d_Zb, p.d_ab, p.d_status};
+                    p.d_X, p.d_Y, p.d_kbin, p.d_xmax, p.d_Zb, p.d_ab, p.d_status,
+                    p.d_bshift, p.d_bwt, p.d_brot, p.d_hb};
     for (void* b : bufs)
         if (b) cudaFree(b);
 }
@@ -151,6 +152,15 @@ const char* rtis_status_string(rtis_status s) {
 
 const char* rtis_last_error(void) { return rtis::g_last_error.c_str(); }
 
+// TMA view of the baseband signal z (in d_a): Nb complex samples per row, rows bb_stride apart
+static bool encode_bb_map(Plan& p, std::string* err) {
+    const uint64_t dims[2] = {static_cast<uint64_t>(p.Nb), static_cast<uint64_t>(p.M)};
+    const uint64_t strides[1] = {static_cast<uint64_t>(p.bb_stride) * 8};
+    const uint32_t box[2] = {static_cast<uint32_t>(rtis::kBbBox), 1};
+    return rtis::encode_tmap(&p.tmap_zb, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, p.d_a, dims, strides, box,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, err);
+}
+
 // TMA views of the per-measurement analytic signals of rtis_process_many
 static bool encode_batch_maps(Plan& p, std::string* err) {
     p.tmap_ab.resize(p.max_batch);
@@ -189,7 +199,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: need 0 <= band_lo_hz < band_hi_hz");
     if (!(opt.max_delay_s >= 0.0) || !(opt.position_slack_m >= 0.0))
         return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: max_delay_s and position_slack_m must be >= 0");
-    if (opt.path != RTIS_PATH_TD && opt.path != RTIS_PATH_FD)
+    if (opt.path != RTIS_PATH_TD && opt.path != RTIS_PATH_FD && opt.path != RTIS_PATH_BB)
         return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: unknown path");
     if (opt.precision != RTIS_PREC_FP32 && opt.precision != RTIS_PREC_BF16)
         return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: precision must be RTIS_PREC_FP32 or RTIS_PREC_BF16");
@@ -266,6 +276,33 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         return fail(RTIS_ERR_UNSUPPORTED,
                     "rtis_plan_create: frequency-domain path needs F <= 32768 and the envelope in shared memory");
     }
+    if (opt.path == RTIS_PATH_BB) {
+        // coarse grid: every 4th sample; |floor(delta/4)| <= bb_Jlim whenever |floor(delta)| <= Jlim
+        p.Nb = n_samples / rtis::kBbQ;
+        p.bb_stride = (p.Nb + 1) & ~1;
+        p.k_c = (k_lo + k_hi) / 2;
+        p.bb_Jlim = (p.Jlim + 3) / rtis::kBbQ + 1;
+        p.bb_H = p.bb_Jlim + 2;
+        const int half = (lpf_len - 1) / 2;
+        p.bb_ntap = (2 * half) / rtis::kBbQ + 1;
+        // a lane reads up to H + 1 + 31 T - 1 + Jlim_b + T + 3 elements into the row
+        p.bb_nbox = (p.bb_H + p.bb_Jlim + rtis::kBbWarpSamples + 4 + rtis::kBbBox - 1) / rtis::kBbBox;
+        p.bb_row = p.bb_nbox * rtis::kBbBox;
+        p.bb_bins_per_tile = (rtis::kBbQ * (rtis::kBbWarpSamples - 1 - p.bb_ntap)) / p.R + 1;
+        bool fits = p.bb_bins_per_tile >= 1 && rtis::bb_smem_bytes(p) <= 227 * 1024;
+        // every output bin's taps lie inside its warp's kBbWarpSamples coarse samples
+        for (int i0 = 0; fits && i0 < p.n_out; i0 += p.bb_bins_per_tile) {
+            const int jS = -((half - p.R * i0) >> 2);
+            for (int i = i0; fits && i < std::min(p.n_out, i0 + p.bb_bins_per_tile); ++i) {
+                const int jlo = -((half - p.R * i) >> 2);
+                fits = jlo - jS >= 0 && jlo - jS + p.bb_ntap <= rtis::kBbWarpSamples;
+            }
+        }
+        if (!fits) {
+            delete plan;
+            return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: baseband tiling does not fit (decim or halo too large)");
+        }
+    }
 
     // ---- host tables (FP64, rounded to float once) ----
     std::vector<double> cs(F), sn(F);
@@ -304,6 +341,22 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         }
         for (int j = 0; j < lpf_len; ++j) h[j] = static_cast<float>(hd[j] / sum);
     }
+    // baseband low-pass: the taps at the coarse offsets t = t0 + 4l (t0 = -half +
+    // ((4 - c) mod 4) for residue c = (R i - half) mod 4), renormalised per residue
+    std::vector<float> hb(opt.path == RTIS_PATH_BB ? 4 * p.bb_ntap : 0, 0.0f);
+    if (opt.path == RTIS_PATH_BB) {
+        const int half = (lpf_len - 1) / 2;
+        for (int c = 0; c < 4; ++c) {
+            const int t0 = -half + ((4 - c) & 3);
+            double sum = 0.0;
+            for (int l = 0; t0 + 4 * l <= half; ++l) sum += h[t0 + 4 * l + half];
+            if (!(std::fabs(sum) > 0.0)) {
+                delete plan;
+                return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: a coarse phase of the low-pass taps sums to 0");
+            }
+            for (int l = 0; t0 + 4 * l <= half; ++l) hb[c * p.bb_ntap + l] = static_cast<float>(h[t0 + 4 * l + half] / sum);
+        }
+    }
     std::vector<float> ones(n_mics, 1.0f), zeros(n_mics, 0.0f);
 
     // ---- device buffers, allocated once ----
@@ -335,6 +388,12 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         RTIS_ALLOC(p.d_Zb, static_cast<size_t>(p.max_batch) * n_mics * 2 * p.P)
         RTIS_ALLOC(p.d_ab, static_cast<size_t>(p.max_batch) * n_mics * n_samples)
     }
+    if (opt.path == RTIS_PATH_BB) {
+        RTIS_ALLOC(p.d_bshift, static_cast<size_t>(n_dirs) * n_mics)
+        RTIS_ALLOC(p.d_bwt, static_cast<size_t>(n_dirs) * n_mics)
+        RTIS_ALLOC(p.d_brot, static_cast<size_t>(n_dirs) * n_mics)
+        RTIS_ALLOC(p.d_hb, hb.size())
+    }
     RTIS_ALLOC(p.d_A, static_cast<size_t>(n_mics) * p.Kb)
     RTIS_ALLOC(p.d_Z, static_cast<size_t>(n_mics) * 2 * p.P)
     RTIS_ALLOC(p.d_a, static_cast<size_t>(n_mics) * n_samples)
@@ -361,6 +420,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     RTIS_UP(p.d_tw, tw.data(), F * sizeof(float2))
     RTIS_UP(p.d_C, C.data(), p.Kb * sizeof(float2))
     RTIS_UP(p.d_h, h.data(), lpf_len * sizeof(float))
+    if (!hb.empty()) RTIS_UP(p.d_hb, hb.data(), hb.size() * sizeof(float))
 #undef RTIS_UP
     if (e == cudaSuccess) e = cudaMemset(p.d_status, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = rtis::launch_steering_table(p, 0);
@@ -375,6 +435,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
                                   rtis::kTdBox, 1, &err) ||
         (p.a_bf16 && !rtis::encode_tmap_2d_u32(&p.tmap_a16, p.d_a16, static_cast<uint64_t>(n_samples),
                                                static_cast<uint64_t>(n_mics), rtis::kTdBox, 1, &err)) ||
+        (opt.path == RTIS_PATH_BB && !encode_bb_map(p, &err)) ||
         !encode_batch_maps(p, &err)) {
         rtis::free_plan_buffers(p);
         delete plan;
@@ -479,6 +540,41 @@ rtis_status rtis_beamform_td(rtis_plan* plan, const float* d_a, float* d_out, vo
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_beamform_td: launch");
 }
 
+rtis_status rtis_baseband_signal(rtis_plan* plan, const int16_t* d_in, float* d_z, void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_baseband_signal: injected launch failure");
+    if (!plan || !d_in || !d_z) return fail(RTIS_ERR_INVALID_ARG, "rtis_baseband_signal: NULL argument");
+    if (!rtis::aligned(d_in, 8) || !rtis::aligned(d_z, 8))
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_baseband_signal: d_in and d_z must be 8-byte aligned");
+    Plan& p = plan->p;
+    if (p.opt.path != RTIS_PATH_BB)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_baseband_signal: the plan was not created for RTIS_PATH_BB");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = rtis::launch_mf_forward(p, d_in, st);
+    if (e == cudaSuccess) e = rtis::launch_mf_inverse_bb(p, reinterpret_cast<float2*>(d_z), p.Nb, st);
+    return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_baseband_signal: launch");
+}
+
+rtis_status rtis_beamform_bb(rtis_plan* plan, const float* d_z, float* d_out, void* stream) {
+    if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_beamform_bb: injected launch failure");
+    if (!plan || !d_z || !d_out) return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_bb: NULL argument");
+    if (!rtis::aligned(d_z, 16)) return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_bb: d_z must be 16-byte aligned");
+    if (!rtis::aligned(d_out, 4)) return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_bb: d_out must be 4-byte aligned");
+    Plan& p = plan->p;
+    if (p.opt.path != RTIS_PATH_BB)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_beamform_bb: the plan was not created for RTIS_PATH_BB");
+    if (p.Nb % 2 != 0)
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_beamform_bb: rows of an odd number of coarse samples (N/4) are not 16-byte strided");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUtensorMap map;
+    std::string err;
+    if (!rtis::encode_tmap_2d_u64(&map, d_z, p.Nb, p.M, rtis::kBbBox, 1, &err))
+        return fail(RTIS_ERR_CUDA, "rtis_beamform_bb: " + err);
+    rtis_status s = ensure_table(p, st);
+    if (s != RTIS_OK) return s;
+    cudaError_t e = rtis::launch_bb_beamform(p, map, d_out, st);
+    return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_beamform_bb: launch");
+}
+
 rtis_status rtis_process(rtis_plan* plan, const int16_t* d_in, float* d_out, void* stream) {
     if (rtis::fault_mode() == rtis::kFaultLaunch) return rtis::fail(RTIS_ERR_CUDA, "rtis_process: injected launch failure");
     if (!plan || !d_in || !d_out) return fail(RTIS_ERR_INVALID_ARG, "rtis_process: NULL argument");
@@ -492,6 +588,9 @@ rtis_status rtis_process(rtis_plan* plan, const int16_t* d_in, float* d_out, voi
     if (p.opt.path == RTIS_PATH_FD) {
         if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, nullptr, p.d_A, st);
         if (e == cudaSuccess) e = rtis::launch_fd_energyscape(p, p.d_A, d_out, st);
+    } else if (p.opt.path == RTIS_PATH_BB) {
+        if (e == cudaSuccess) e = rtis::launch_mf_inverse_bb(p, p.d_a, p.bb_stride, st);
+        if (e == cudaSuccess) e = rtis::launch_bb_beamform(p, p.tmap_zb, d_out, st);
     } else {
         if (p.a_bf16) {
             if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, nullptr, nullptr, st, p.d_a16);

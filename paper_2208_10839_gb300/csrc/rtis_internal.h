@@ -24,6 +24,15 @@ constexpr int kTdStages = 4;                          // smem ring depth
 constexpr int kTdBox = 256;                           // TMA box width (8-byte elements)
 constexpr int kMaxMics = 32;                          // lanes hold per-mic steering
 
+// complex-baseband beamformer (kernels_bb.cu): the same CTA shape on a grid of
+// every 4th sample
+constexpr int kBbQ = 4;                               // full-rate samples per coarse sample
+constexpr int kBbOutPerThread = 14;                   // coarse samples per lane: T/2 odd, conflict-free 16-byte loads
+constexpr int kBbWarpSamples = 32 * kBbOutPerThread;
+constexpr int kBbMicsPerStage = 2;
+constexpr int kBbStages = 4;
+constexpr int kBbBox = 64;                            // TMA box width (8-byte elements)
+
 // |z| from |z|^2 = x^2 + y^2 as n2 rsqrt(n2) (a few ulp, no slow path); 0 for 0, and a
 // NaN stays NaN (n2 * 0) so non-finite inputs still show in the output
 __device__ __forceinline__ float magnitude_from_norm(float n2) { return n2 > 0.f ? n2 * rsqrtf(n2) : n2 * 0.f; }
@@ -76,6 +85,17 @@ struct Plan {
     std::vector<CUtensorMap> tmap_ab;  // TMA views of the d_ab rows (time-domain beamformer)
     unsigned* d_status = nullptr;
     size_t bytes = 0;
+
+    // complex-baseband path (RTIS_PATH_BB): z [M][Nb] lives in d_a
+    int Nb = 0, k_c = 0;        // coarse samples N/4; demodulation bin floor((k_lo + k_hi)/2)
+    int bb_stride = 0;          // row stride of z in elements (Nb rounded up to even: 16-byte rows)
+    int bb_H = 0, bb_Jlim = 0;  // coarse staging halo and accepted |floor(delta/4)|
+    int bb_row = 0, bb_nbox = 0, bb_bins_per_tile = 0, bb_ntap = 0;
+    int* d_bshift = nullptr;    // [D][M] floor(delta / 4)
+    float4* d_bwt = nullptr;    // [D][M] Catmull-Rom weights of delta/4 - floor(delta/4)
+    float2* d_brot = nullptr;   // [D][M] g_m (cos, sin)(2 pi k_c delta / F)
+    float* d_hb = nullptr;      // [4][bb_ntap] coarse low-pass taps by (R i - half) mod 4
+    CUtensorMap tmap_zb;        // TMA view of z as [M][Nb] 8-byte elements, rows bb_stride apart
 
     CUtensorMap tmap_a;         // TMA view of d_a as [M][N] 8-byte elements
     CUtensorMap tmap_a16;       // TMA view of d_a16 as [M][N] 4-byte elements (BF16 plans)
@@ -130,6 +150,13 @@ cudaError_t launch_mf_forward(const Plan& p, const int16_t* d_in, cudaStream_t s
 cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st, uint32_t* d_a16 = nullptr,
                               int a_ms = -1, int a_ks = 1, const MfBatch& mb = MfBatch());
 cudaError_t launch_steering_table(Plan& p, cudaStream_t st);
+// z_m[j] = a_m[4j] exp(-2 pi i k_c 4j / F), j < Nb, into d_z rows `stride` elements apart
+// (phase-0 inverse only; the half spectra come from launch_mf_forward)
+cudaError_t launch_mf_inverse_bb(const Plan& p, float2* d_z, int stride, cudaStream_t st);
+// zmap: TMA view of z as [M][Nb] 8-byte elements
+cudaError_t launch_bb_beamform(const Plan& p, const CUtensorMap& zmap, float* d_out, cudaStream_t st);
+size_t bb_smem_bytes(const Plan& p);
+int bb_tiles(const Plan& p);
 // bf16: tmap views BF16 pairs (4-byte elements) rather than complex floats
 cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, bool bf16, float* d_out, cudaStream_t st);
 size_t td_smem_bytes(const Plan& p);

@@ -7,7 +7,7 @@ import numpy as np
 
 from . import _native as nat
 
-_PATHS = {"td": nat.RTIS_PATH_TD, "fd": nat.RTIS_PATH_FD}
+_PATHS = {"td": nat.RTIS_PATH_TD, "fd": nat.RTIS_PATH_FD, "bb": nat.RTIS_PATH_BB}
 _PRECS = {"fp32": nat.RTIS_PREC_FP32, "bf16": nat.RTIS_PREC_BF16, "fp16": nat.RTIS_PREC_FP16}
 
 
@@ -82,6 +82,8 @@ class Plan:
         t = self._torch
         n = int(x.shape[0])
         want = (self.info_path,) if paths is None else tuple(paths)
+        if any(w not in ("td", "fd") for w in want):
+            raise ValueError("process_many runs the time- and frequency-domain forms (paths 'td', 'fd')")
         shape = (n, self.D, self.n_out)
         if "td" in want and out_td is None:
             out_td = t.empty(shape, dtype=t.float32, device=x.device)
@@ -110,6 +112,22 @@ class Plan:
         if out is None:
             out = self._torch.empty((self.D, self.n_out), dtype=self._torch.float32, device=A.device)
         nat.rtis_beamform_fd(self.handle, A, out, stream)
+        return out
+
+    def baseband_signal(self, x, out=None, stream=None):
+        """int16 [M][N] -> z complex64 [M][N/4]: the demodulated analytic signal on the coarse grid
+        (plans created with path="bb")."""
+        t = self._torch
+        if out is None:
+            out = t.empty((self.M, self.N // 4), dtype=t.complex64, device=x.device)
+        nat.rtis_baseband_signal(self.handle, x, out, stream)
+        return out
+
+    def beamform_bb(self, z, out=None, stream=None):
+        """z complex64 [M][N/4] (N/4 even) -> energyscape through the baseband delay-and-sum."""
+        if out is None:
+            out = self._torch.empty((self.D, self.n_out), dtype=self._torch.float32, device=z.device)
+        nat.rtis_beamform_bb(self.handle, z, out, stream)
         return out
 
     def set_calibration(self, mic_xyz=None, gain=None, delay_s=None, stream=None):
