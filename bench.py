@@ -713,6 +713,7 @@ def run_baseband(args, rank, world, local):
                      "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x "
                                    f"{SM_MAX_MHZ_NOMINAL:.0f} MHz",
                      "algorithmic_flops_per_launch": bb_flops, "launch_ms": bbk_s * 1e3,
+                     "tuned_variant_grid": [p_bb.info.bb_variant, p_bb.info.bb_grid],
                      "td_equivalent": {"flops": td_flops, "frac": td_flops / tdk_s / 1e12 / peak_tf}},
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,

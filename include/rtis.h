@@ -117,6 +117,11 @@ typedef struct rtis_plan_info {
     int td_variant;              /* time-domain beamformer stage layout chosen at creation */
     int td_grid;                 /* and its grid (CTAs) */
     float td_tuned_ms;           /* its time on this device when tuned */
+    int n_coarse;                /* RTIS_PATH_BB: n_samples/4 coarse samples per channel (else 0) */
+    int k_c;                     /* RTIS_PATH_BB: demodulation bin floor((k_lo + k_hi)/2) (else 0) */
+    int bb_variant;              /* RTIS_PATH_BB: baseband beamformer stage layout chosen at creation */
+    int bb_grid;                 /* and its grid (CTAs) */
+    float bb_tuned_ms;           /* its time on this device when tuned */
 } rtis_plan_info;
 
 /*

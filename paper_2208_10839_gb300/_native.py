@@ -54,6 +54,8 @@ class rtis_plan_info(C.Structure):
         ("decim", C.c_int), ("lpf_len", C.c_int), ("n_out", C.c_int),
         ("halo", C.c_int), ("max_shift", C.c_int), ("workspace_bytes", C.c_size_t),
         ("td_variant", C.c_int), ("td_grid", C.c_int), ("td_tuned_ms", C.c_float),
+        ("n_coarse", C.c_int), ("k_c", C.c_int), ("bb_variant", C.c_int), ("bb_grid", C.c_int),
+        ("bb_tuned_ms", C.c_float),
     ]
 
 

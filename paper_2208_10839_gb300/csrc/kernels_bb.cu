@@ -43,7 +43,7 @@ struct BbArgs {
     float* E;            // [D][n_out]
     unsigned* status;
     int M, Nb, D, R, half, n_out, bins_per_tile, n_dgroups, total_tiles, H, row, nbox, ntap;
-    uint32_t stage_area;  // bytes of the stage ring (>= the epilogue's envelope rows)
+    uint32_t stage_area;  // bytes of the stage ring; the envelope rows follow it
 };
 
 // one mic's contribution to a lane's T coarse samples; p points at the 16-byte
@@ -61,14 +61,24 @@ __device__ __forceinline__ void bb_mic(uint64_t (&ac)[kBbOutPerThread], uint64_t
         v[2 * k] = q.x;
         v[2 * k + 1] = q.y;
     }
+    // blocks of TB samples, tap by tap: consecutive instructions are independent
+    constexpr int TB = 7;
+    static_assert(T % TB == 0, "T must be a multiple of the block");
 #pragma unroll
-    for (int t = 0; t < T; ++t) {
-        uint64_t s = mul2(w0, v[t + ODD]);
-        fma2(s, w1, v[t + 1 + ODD]);
-        fma2(s, w2, v[t + 2 + ODD]);
-        fma2(s, w3, v[t + 3 + ODD]);
-        fma2(ac[t], rc, s);
-        fma2(as[t], rs, s);
+    for (int tb = 0; tb < T; tb += TB) {
+        uint64_t s[TB];
+#pragma unroll
+        for (int t = 0; t < TB; ++t) s[t] = mul2(w0, v[tb + t + ODD]);
+#pragma unroll
+        for (int t = 0; t < TB; ++t) fma2(s[t], w1, v[tb + t + 1 + ODD]);
+#pragma unroll
+        for (int t = 0; t < TB; ++t) fma2(s[t], w2, v[tb + t + 2 + ODD]);
+#pragma unroll
+        for (int t = 0; t < TB; ++t) fma2(s[t], w3, v[tb + t + 3 + ODD]);
+#pragma unroll
+        for (int t = 0; t < TB; ++t) fma2(ac[tb + t], rc, s[t]);
+#pragma unroll
+        for (int t = 0; t < TB; ++t) fma2(as[tb + t], rs, s[t]);
     }
 }
 
@@ -79,10 +89,12 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
     constexpr int T = kBbOutPerThread;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* stage = smem_raw;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + A.stage_area);
+    float* env_all = reinterpret_cast<float*>(smem_raw + A.stage_area);  // [8][kBbWarpSamples]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(env_all + kTdDirsPerCta * kBbWarpSamples);
     int* done = reinterpret_cast<int*>(bar + NS);
     int* issued = done + NS;
-    float* hs = reinterpret_cast<float*>(issued + NS);
+    int* next_issued = issued + NS;  // stages of this CTA's next tile already in flight
+    float* hs = reinterpret_cast<float*>(next_issued + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -91,6 +103,7 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
             done[b] = 0;
             issued[b] = 0;
         }
+        *next_issued = 0;
         ptx::fence_mbar_init();
         ptx::fence_proxy_async();
     }
@@ -99,6 +112,27 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
     const int M = A.M, row = A.row;
     const int nstages = (M + MS - 1) / MS;
     const uint32_t stage_bytes = static_cast<uint32_t>(MS * A.nbox * kBbBox * 8);
+    // TMA x of a tile's rows: an even element (16 bytes) at or before its first
+    // coarse sample jS = ceil((R i0 - half) / 4) minus the halo
+    auto tile_x0 = [&](int t) {
+        const int i0t = (t / A.n_dgroups) * A.bins_per_tile;
+        return (-((A.half - A.R * i0t) >> 2) - A.H) & ~1;
+    };
+    // stage st of a tile whose rows start at x, into ring slot g (global stage count):
+    // a whole warp issues it, lane 0 arming the barrier and every lane one box
+    auto issue_warp = [&](int g, int x, int st) {
+        const int b = g % NS;
+        if (lane == 0) {
+            issued[b] += 1;
+            ptx::mbar_arrive_expect_tx(&bar[b], stage_bytes);
+        }
+        __syncwarp();
+        for (int k = lane; k < MS * A.nbox; k += 32) {
+            const int mi = k / A.nbox, bx = k - mi * A.nbox;
+            unsigned char* dst = stage + (static_cast<size_t>(b * MS + mi) * row + static_cast<size_t>(bx) * kBbBox) * 8;
+            ptx::tma_load_2d(dst, &zmap, x + bx * kBbBox, st * MS + mi, &bar[b]);
+        }
+    };
     int g0 = 0;
     bool timed_out = false;
     for (int tile = blockIdx.x; tile < A.total_tiles; tile += gridDim.x) {
@@ -106,24 +140,17 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
         const int d = dg * kTdDirsPerCta + warp;
         const int i0 = (tile / A.n_dgroups) * A.bins_per_tile;
         const int jS = -((A.half - A.R * i0) >> 2);  // ceil((R i0 - half) / 4): first coarse sample
-        const int x0 = (jS - A.H) & ~1;              // TMA x: an even element (16 bytes)
+        const int x0 = tile_x0(tile);
+        const int next_tile = tile + gridDim.x;
 
-        auto issue = [&](int st) {
-            const int b = (g0 + st) % NS;
-            issued[b] += 1;
-            ptx::mbar_arrive_expect_tx(&bar[b], stage_bytes);
-            for (int mi = 0; mi < MS; ++mi) {
-                unsigned char* dst = stage + static_cast<size_t>(b * MS + mi) * row * 8;
-                for (int bx = 0; bx < A.nbox; ++bx)
-                    ptx::tma_load_2d(dst + static_cast<size_t>(bx) * kBbBox * 8, &zmap, x0 + bx * kBbBox,
-                                     st * MS + mi, &bar[b]);
-            }
-        };
-
-        __syncthreads();  // the previous tile's epilogue is done with the stage buffers
-        if (threadIdx.x == 0) {
-            ptx::prefetch_tmap(&zmap);
-            for (int st = 0; st < NS && st < nstages; ++st) issue(st);
+        __syncthreads();  // the previous tile's refills are all issued
+        if (warp == 0) {
+            if (lane == 0 && tile == static_cast<int>(blockIdx.x)) ptx::prefetch_tmap(&zmap);
+            // the first stages not already prefetched while the previous tile finished
+            const int pre = *next_issued;
+            for (int st = pre; st < NS && st < nstages; ++st) issue_warp(g0 + st, x0, st);
+            __syncwarp();
+            if (lane == 0) *next_issued = 0;
         }
 
         // lane m holds the steering entry of mic m for this warp's direction
@@ -179,18 +206,29 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
                                       pack2(rc, rc), pack2(rs, rs));
                 }
             }
-            // release buffer b; the CTA's last warp to get here refills it
+            // release buffer b; the CTA's last warp to get here refills it with the
+            // stage NS later: of this tile, or else of the CTA's next tile
             __syncwarp();
+            int last = 0;
             if (lane == 0) {
                 __threadfence_block();
                 const int prev = atomicAdd(&done[b], 1);
                 if (prev == kTdDirsPerCta - 1) {
                     done[b] = 0;
                     __threadfence_block();
-                    if (st + NS < nstages && !warp_timed_out) {
-                        ptx::fence_proxy_async();
-                        issue(st + NS);
-                    }
+                    last = 1;
+                }
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last && !warp_timed_out) {  // no refills once a wait has given up
+                const int nst = st + NS;
+                if (nst < nstages) {
+                    ptx::fence_proxy_async();
+                    issue_warp(g0 + nst, x0, nst);
+                } else if (next_tile < A.total_tiles && nst - nstages < nstages) {
+                    ptx::fence_proxy_async();
+                    issue_warp(g0 + nst, tile_x0(next_tile), nst - nstages);
+                    if (lane == 0) atomicAdd(next_issued, 1);
                 }
             }
         }
@@ -198,8 +236,9 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
 
         if (__syncthreads_or(timed_out)) break;  // uniform: leave the tile loop, drain below
 
-        // epilogue: |b| over the warp's coarse samples, then the coarse low-pass
-        float* env = reinterpret_cast<float*>(smem_raw) + warp * kBbWarpSamples;
+        // epilogue (its own shared memory: the ring may already hold the next tile's rows):
+        // |b| over the warp's coarse samples, then the coarse low-pass
+        float* env = env_all + warp * kBbWarpSamples;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const int j = jS + lane * T + t;
@@ -236,23 +275,31 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
     }
 }
 
-uint32_t bb_stage_area(const Plan& p) {
-    const size_t ring = static_cast<size_t>(kBbStages) * kBbMicsPerStage * p.bb_row * 8;
-    const size_t env = static_cast<size_t>(kTdDirsPerCta) * kBbWarpSamples * 4;
-    return static_cast<uint32_t>((std::max(ring, env) + 127) & ~static_cast<size_t>(127));
+// stage layouts the autotuner picks from: (mics per stage, stages in the ring)
+constexpr int kBbVariantMS[kBbVariants] = {2, 2, 4, 1};
+constexpr int kBbVariantNS[kBbVariants] = {4, 8, 4, 8};
+
+uint32_t bb_stage_area(const Plan& p, int variant) {
+    const size_t ring = static_cast<size_t>(kBbVariantMS[variant]) * kBbVariantNS[variant] * p.bb_row * 8;
+    return static_cast<uint32_t>((ring + 127) & ~static_cast<size_t>(127));
 }
 
-}  // namespace
-
-size_t bb_smem_bytes(const Plan& p) {
-    return bb_stage_area(p) + 8 * kBbStages + 8 * kBbStages + static_cast<size_t>(4) * p.bb_ntap * 4;
+size_t bb_smem_variant(const Plan& p, int variant) {
+    // ring, envelope rows, barriers + counters (<= 8 stages), next-tile count, taps
+    return bb_stage_area(p, variant) + static_cast<size_t>(kTdDirsPerCta) * kBbWarpSamples * 4 + 8 * 8 + 2 * 8 * 4 +
+           16 + static_cast<size_t>(4) * p.bb_ntap * 4;
 }
 
-int bb_tiles(const Plan& p) {
-    return ((p.D + kTdDirsPerCta - 1) / kTdDirsPerCta) * ((p.n_out + p.bb_bins_per_tile - 1) / p.bb_bins_per_tile);
+template <int MS, int NS>
+cudaError_t bb_launch_t(const CUtensorMap& zmap, const BbArgs& A, int grid, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(bb_beamform_kernel<MS, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    bb_beamform_kernel<MS, NS><<<grid, 32 * kTdDirsPerCta, smem, st>>>(zmap, A);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_bb_beamform(const Plan& p, const CUtensorMap& zmap, float* d_out, cudaStream_t st) {
+cudaError_t bb_launch(const Plan& p, const CUtensorMap& zmap, float* d_out, int variant, int grid, cudaStream_t st) {
     BbArgs A;
     std::memset(&A, 0, sizeof(A));
     A.shift = p.d_bshift;
@@ -274,17 +321,77 @@ cudaError_t launch_bb_beamform(const Plan& p, const CUtensorMap& zmap, float* d_
     A.row = p.bb_row;
     A.nbox = p.bb_nbox;
     A.ntap = p.bb_ntap;
-    A.stage_area = bb_stage_area(p);
-    const size_t smem = bb_smem_bytes(p);
-    cudaError_t e = cudaFuncSetAttribute(bb_beamform_kernel<kBbMicsPerStage, kBbStages>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
+    A.stage_area = bb_stage_area(p, variant);
+    const size_t smem = bb_smem_variant(p, variant);
+    switch (variant) {
+        case 0: return bb_launch_t<2, 4>(zmap, A, grid, smem, st);
+        case 1: return bb_launch_t<2, 8>(zmap, A, grid, smem, st);
+        case 2: return bb_launch_t<4, 4>(zmap, A, grid, smem, st);
+        case 3: return bb_launch_t<1, 8>(zmap, A, grid, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+size_t bb_smem_bytes(const Plan& p) {
+    size_t m = 0;
+    for (int v = 0; v < kBbVariants; ++v) m = std::max(m, bb_smem_variant(p, v));
+    return m;
+}
+
+int bb_tiles(const Plan& p) {
+    return ((p.D + kTdDirsPerCta - 1) / kTdDirsPerCta) * ((p.n_out + p.bb_bins_per_tile - 1) / p.bb_bins_per_tile);
+}
+
+// Times every stage layout with one CTA per tile and with two persistent CTAs
+// per SM on the plan's own (zeroed) workspace and keeps the fastest.
+cudaError_t bb_autotune(Plan& p, float* d_scratch_out) {
     int n_sm = 1, dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 1;
-    const int grid = std::min(A.total_tiles, 2 * n_sm);
-    bb_beamform_kernel<kBbMicsPerStage, kBbStages><<<grid, 32 * kTdDirsPerCta, smem, st>>>(zmap, A);
-    return cudaGetLastError();
+    const int tiles = bb_tiles(p);
+    const int grids[2] = {tiles, std::min(tiles, 2 * n_sm)};
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return e;
+    float best = 1e30f;
+    for (int v = 0; v < kBbVariants && e == cudaSuccess; ++v) {
+        for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
+            e = bb_launch(p, p.tmap_zb, d_scratch_out, v, grids[gi], 0);  // warm-up
+            float total = 0.f;
+            for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+                cudaEventRecord(e0, 0);
+                e = bb_launch(p, p.tmap_zb, d_scratch_out, v, grids[gi], 0);
+                cudaEventRecord(e1, 0);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                total += ms;
+            }
+            if (e == cudaSuccess && total < best) {
+                best = total;
+                p.bb_variant = v;
+                p.bb_grid = grids[gi];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p.bb_tuned_ms = best / 2.f;
+    return e;
+}
+
+cudaError_t launch_bb_beamform(const Plan& p, const CUtensorMap& zmap, float* d_out, cudaStream_t st) {
+    int grid = p.bb_grid;
+    if (grid <= 0) {
+        int n_sm = 1, dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 1;
+        grid = std::min(bb_tiles(p), 2 * n_sm);
+    }
+    return bb_launch(p, zmap, d_out, p.bb_variant, grid, st);
 }
 
 }  // namespace rtis

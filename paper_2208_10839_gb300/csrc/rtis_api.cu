@@ -450,6 +450,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         if (e == cudaSuccess && p.a_bf16) e = cudaMemset(p.d_a16, 0, static_cast<size_t>(n_mics) * n_samples * 4);
         if (e == cudaSuccess) e = cudaMalloc(&scratch, static_cast<size_t>(n_dirs) * p.n_out * sizeof(float));
         if (e == cudaSuccess) e = rtis::td_autotune(p, scratch);
+        if (e == cudaSuccess && opt.path == RTIS_PATH_BB) e = rtis::bb_autotune(p, scratch);
         if (scratch) cudaFree(scratch);
         if (e == cudaSuccess) e = cudaMemcpy(&bits, p.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {
@@ -499,6 +500,11 @@ rtis_status rtis_plan_get_info(const rtis_plan* plan, rtis_plan_info* info) {
     info->td_variant = p.td_variant;
     info->td_grid = p.td_grid;
     info->td_tuned_ms = p.td_tuned_ms;
+    info->n_coarse = p.Nb;
+    info->k_c = p.k_c;
+    info->bb_variant = p.bb_variant;
+    info->bb_grid = p.bb_grid;
+    info->bb_tuned_ms = p.bb_tuned_ms;
     return RTIS_OK;
 }
 

@@ -29,9 +29,8 @@ constexpr int kMaxMics = 32;                          // lanes hold per-mic stee
 constexpr int kBbQ = 4;                               // full-rate samples per coarse sample
 constexpr int kBbOutPerThread = 14;                   // coarse samples per lane: T/2 odd, conflict-free 16-byte loads
 constexpr int kBbWarpSamples = 32 * kBbOutPerThread;
-constexpr int kBbMicsPerStage = 2;
-constexpr int kBbStages = 4;
-constexpr int kBbBox = 64;                            // TMA box width (8-byte elements)
+constexpr int kBbBox = 96;                            // TMA box width (8-byte elements)
+constexpr int kBbVariants = 4;                        // stage layouts: (2, 4), (2, 8), (4, 4), (1, 8)
 
 // |z| from |z|^2 = x^2 + y^2 as n2 rsqrt(n2) (a few ulp, no slow path); 0 for 0, and a
 // NaN stays NaN (n2 * 0) so non-finite inputs still show in the output
@@ -91,6 +90,8 @@ struct Plan {
     int bb_stride = 0;          // row stride of z in elements (Nb rounded up to even: 16-byte rows)
     int bb_H = 0, bb_Jlim = 0;  // coarse staging halo and accepted |floor(delta/4)|
     int bb_row = 0, bb_nbox = 0, bb_bins_per_tile = 0, bb_ntap = 0;
+    int bb_variant = 0, bb_grid = 0;  // baseband stage layout and grid, autotuned at creation
+    float bb_tuned_ms = 0.f;
     int* d_bshift = nullptr;    // [D][M] floor(delta / 4)
     float4* d_bwt = nullptr;    // [D][M] Catmull-Rom weights of delta/4 - floor(delta/4)
     float2* d_brot = nullptr;   // [D][M] g_m (cos, sin)(2 pi k_c delta / F)
@@ -155,8 +156,9 @@ cudaError_t launch_steering_table(Plan& p, cudaStream_t st);
 cudaError_t launch_mf_inverse_bb(const Plan& p, float2* d_z, int stride, cudaStream_t st);
 // zmap: TMA view of z as [M][Nb] 8-byte elements
 cudaError_t launch_bb_beamform(const Plan& p, const CUtensorMap& zmap, float* d_out, cudaStream_t st);
-size_t bb_smem_bytes(const Plan& p);
+size_t bb_smem_bytes(const Plan& p);  // the largest stage layout's
 int bb_tiles(const Plan& p);
+cudaError_t bb_autotune(Plan& p, float* d_scratch_out);
 // bf16: tmap views BF16 pairs (4-byte elements) rather than complex floats
 cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, bool bf16, float* d_out, cudaStream_t st);
 size_t td_smem_bytes(const Plan& p);
