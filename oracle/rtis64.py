@@ -40,6 +40,15 @@ analytic signal, where the 60 kHz band allows it):
    (the envelope delayed on the coarse grid, the carrier's phase exactly)
 8. E[d][i] = sum_j h_Ri(Q j - R i) |b_d[j]|: the same windowed-sinc low-pass
    sampled at the coarse grid's offsets from R i, renormalised to unit DC gain
+
+PDM front end (the microphones record through a 1-bit sigma-delta ADC, Sec. 2;
+the GPU unpacks the bits and demodulates them with a low-pass filter before
+the matched filter, Sec. 4.3):
+
+0a. unpack: bit m of word k is mic m's k-th bit; b_m[k] = +1 for 1, -1 for 0
+0b. demodulate: x_m[n] = sum_j g[j] b_m[D n + j - c], c = (len(g) - 1) // 2,
+    b = 0 outside the record: an integer FIR evaluated at every D-th bit (by
+    default the CIC kernel, D = 10, order 4), rounded right shift, int16
 """
 from __future__ import annotations
 
@@ -53,7 +62,7 @@ __all__ = [
     "steering_delays", "das_td", "das_td_bruteforce", "das_fd", "lpf_taps", "envelope_decimate",
     "energyscape", "steering_matrix", "fd_gemm", "DEFAULT_BAND", "DEFAULT_DECIM",
     "DEFAULT_BB_DECIM", "baseband_centre_bin", "baseband_signal", "das_bb", "das_bb_bruteforce", "lpf_window",
-    "envelope_decimate_bb",
+    "envelope_decimate_bb", "pdm_unpack", "cic_taps", "pdm_demodulate",
 ]
 
 DEFAULT_BAND = (20e3, 80e3)   # chirp band: the 80 -> 20 kHz sweep
@@ -493,6 +502,45 @@ def envelope_decimate_bb(b, n_samples: int, R: int = DEFAULT_DECIM, Q: int = DEF
         ok = (jj >= 0) & (jj < Nb)
         E[:, i] = env[:, jj[ok]] @ w[ok]
     return E
+
+
+# --------------------------------------------------------------------------
+# PDM front end (Sec. 2: 1-bit sigma-delta microphones; Sec. 4.3: bit
+# unpacking and a demodulating low-pass before the matched filter)
+# --------------------------------------------------------------------------
+def pdm_unpack(words, n_mics: int):
+    """uint32 words [K] -> bits [n_mics][K] (0/1): bit m of word k is mic m's k-th bit."""
+    w = np.asarray(words, dtype=np.uint64)
+    return np.stack([((w >> np.uint64(m)) & np.uint64(1)).astype(np.int64) for m in range(n_mics)])
+
+
+def cic_taps(decim: int = 10, order: int = 4):
+    """Integer impulse response of an order-K CIC decimator: the length-D boxcar
+    convolved with itself K times (length K (D - 1) + 1, sum D^K)."""
+    h = np.ones(1, dtype=np.int64)
+    for _ in range(order):
+        h = np.convolve(h, np.ones(decim, dtype=np.int64))
+    return h
+
+
+def pdm_demodulate(bits, taps, decim: int, n_samples: int, shift: int = 0):
+    """x_m[n] = sum_j g[j] b_m[D n + j - c] with b = 2 bits - 1 (0 outside [0, K)),
+    c = (len(g) - 1) // 2, then (x + 2^(shift-1)) >> shift for shift > 0 (an
+    arithmetic shift: rounds halves up), clamped to int16.  All integer."""
+    b = 2 * np.asarray(bits, dtype=np.int64) - 1
+    g = np.asarray(taps, dtype=np.int64)
+    M, K = b.shape
+    L = g.shape[0]
+    c = (L - 1) // 2
+    pad = np.zeros((M, K + decim * n_samples + 2 * L), dtype=np.int64)
+    pad[:, L:L + K] = b
+    x = np.zeros((M, n_samples), dtype=np.int64)
+    idx = decim * np.arange(n_samples, dtype=np.int64) - c + L     # index of tap j = 0 in pad
+    for j in range(L):
+        x += g[j] * pad[:, idx + j]
+    if shift > 0:
+        x = (x + (1 << (shift - 1))) >> shift
+    return np.clip(x, -32768, 32767).astype(np.int16)
 
 
 # --------------------------------------------------------------------------

@@ -7,3 +7,4 @@ envelope); both the CUDA library's tests/benchmarks and the FP64 oracle
 consume what it produces.
 """
 from .scene import *  # noqa: F401,F403
+from .pdm import *  # noqa: F401,F403

@@ -474,3 +474,98 @@ def test_baseband_energyscape_tracks_exact_delays():
     E_fd = orc.energyscape(cfg["x"], cfg["chirp"], cfg["mic_xyz"], cfg["dirs"], FS, C, path="fd")
     assert np.unravel_index(np.argmax(E_bb), E_bb.shape) == np.unravel_index(np.argmax(E_fd), E_fd.shape)
     assert np.max(np.abs(E_bb - E_fd)) < 1e-2 * E_fd.max()
+
+
+# -------------------------------------------------------------- PDM front end
+def test_pdm_unpack_bruteforce_and_pack_roundtrip():
+    rng = np.random.default_rng(31)
+    words = rng.integers(0, 2 ** 32, size=57, dtype=np.uint64).astype(np.uint32)
+    for M in (1, 5, 32):
+        bits = orc.pdm_unpack(words, M)
+        assert bits.shape == (M, 57)
+        for m in range(M):
+            for k in range(57):
+                assert bits[m, k] == (int(words[k]) >> m) & 1
+    bits = rng.integers(0, 2, size=(7, 40))
+    packed = np.array([sum(int(bits[m, k]) << m for m in range(7)) for k in range(40)], dtype=np.uint32)
+    np.testing.assert_array_equal(synth.pdm_pack(bits), packed)
+    np.testing.assert_array_equal(orc.pdm_unpack(packed, 7), bits)
+
+
+def test_cic_taps_are_the_recursive_cic_impulse_response():
+    for D, K in ((10, 4), (8, 3), (4, 1)):
+        h = orc.cic_taps(D, K)
+        assert h.shape == (K * (D - 1) + 1,) and h.sum() == D ** K
+        np.testing.assert_array_equal(h, h[::-1])
+        x = np.zeros(200, dtype=np.int64)
+        x[0] = 1
+        for _ in range(K):                   # integrators
+            x = np.cumsum(x)
+        for _ in range(K):                   # combs with lag D (not decimated)
+            x = x - np.concatenate([np.zeros(D, dtype=np.int64), x[:-D]])
+        np.testing.assert_array_equal(x[:h.size], h)
+        assert not x[h.size:].any()
+
+
+def test_pdm_demodulate_is_the_decimated_recursive_cic():
+    # integrators at the bit rate, sampled every D bits at the phase the centred
+    # FIR implies (x[n] = f[D n + L - 1 - c] for the causal FIR f), combs at the low rate
+    rng = np.random.default_rng(32)
+    D, K, M, n_out = 10, 4, 3, 150
+    bits = rng.integers(0, 2, size=(M, 1400))
+    g = orc.cic_taps(D, K)
+    L, c = g.size, (g.size - 1) // 2
+    x = orc.pdm_demodulate(bits, g, D, n_out)
+    b = np.zeros((M, D * n_out + 2 * L), dtype=np.int64)
+    b[:, :1400] = 2 * bits - 1
+    I = b.copy()
+    for _ in range(K):
+        I = np.cumsum(I, axis=1)
+    n = np.arange(-K, n_out)
+    t = D * n + L - 1 - c
+    Is = np.where(t >= 0, I[:, np.clip(t, 0, None)], 0)
+    for _ in range(K):
+        Is = Is[:, 1:] - Is[:, :-1]
+    np.testing.assert_array_equal(x, Is.astype(np.int16))
+
+
+def test_pdm_demodulate_patterns_and_rounding():
+    g = orc.cic_taps(10, 4)
+    ones = np.ones((2, 3000), dtype=np.int64)
+    x = orc.pdm_demodulate(ones, g, 10, 300)
+    assert np.all(x[:, 2:-2] == 10000)                  # full scale +1
+    assert np.all(orc.pdm_demodulate(0 * ones, g, 10, 300)[:, 2:-2] == -10000)
+    alt = np.tile([1, 0], (1, 1500))
+    assert np.all(orc.pdm_demodulate(alt, g, 10, 300)[:, 2:-2] == 0)   # nulled by the even boxcar
+    # rounding right shift: (x + 2^(s-1)) >> s, halves go up (towards +inf)
+    taps = np.array([1, 2, 1])
+    bits = np.array([[1, 1, 0, 0, 1, 0, 1, 1, 1, 0]])
+    raw = orc.pdm_demodulate(bits, taps, 1, 10).astype(np.int64)
+    b = np.concatenate([[0], 2 * bits[0] - 1, [0]])
+    np.testing.assert_array_equal(raw[0], [b[n] + 2 * b[n + 1] + b[n + 2] for n in range(10)])
+    for s in (1, 2):
+        got = orc.pdm_demodulate(bits, taps, 1, 10, shift=s).astype(np.int64)
+        np.testing.assert_array_equal(got[0], [math.floor(v / 2 ** s + 0.5) for v in raw[0]])
+
+
+def test_sigma_delta_tone_through_the_cic_demodulator():
+    # a 0.5 full-scale 50 kHz tone: the demodulated amplitude is the CIC's gain at
+    # 50 kHz (sin(pi f D/fb) / (D sin(pi f/fb)))^4 x 0.5 x 10^4, and the in-band noise
+    # of the second-order modulator at 10x oversampling stays 45 dB below
+    D = synth.PDM_DECIM
+    fb = synth.FS * D
+    K = 4096 * D
+    u = 0.5 * np.sin(2 * np.pi * 50e3 * np.arange(K) / fb)[None, :]
+    x = orc.pdm_demodulate(synth.sigma_delta2(u), orc.cic_taps(D, 4), D, 4096).astype(np.float64)[0]
+    n = np.arange(4096)[100:-100]
+    w = 2 * np.pi * 50e3 / synth.FS
+    A = np.stack([np.sin(w * n), np.cos(w * n)], 1)
+    coef, *_ = np.linalg.lstsq(A, x[100:-100], rcond=None)
+    gain = (math.sin(math.pi * 50e3 * D / fb) / (D * math.sin(math.pi * 50e3 / fb))) ** 4
+    assert abs(np.hypot(*coef) / (0.5 * 1e4 * gain) - 1) < 0.01
+    res = x[100:-100] - A @ coef
+    R = np.fft.rfft(res)
+    f = np.fft.rfftfreq(res.size, 1 / synth.FS)
+    inb = (f >= 20e3) & (f <= 80e3)
+    snr = 10 * np.log10((np.hypot(*coef) ** 2 / 2 * res.size) / (2 * np.sum(np.abs(R[inb]) ** 2) / res.size))
+    assert snr > 45
