@@ -724,6 +724,91 @@ def run_baseband(args, rank, world, local):
         p_.close()
 
 
+def run_pdm(args, rank, world, local):
+    """The PDM front end ahead of the time-domain chain: each step demodulates one
+    hemisphere measurement's 1-bit stream (32 mics x 163840 ticks, one uint32 word per
+    tick) into int16 and runs rtis_process on it."""
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2208_10839_gb300 import Plan, _native as nat
+    from paper_2208_10839_gb300 import build as _b
+    _b.build()
+    dev = torch.device("cuda", local)
+    cfg = synth.hemisphere_pdm(seed_scene=1 + 1000 * rank)
+    D = cfg["decim"]
+    plan = Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"])
+    words = torch.from_numpy(cfg["words"].view(np.int32)).to(dev)
+    K = int(words.numel())
+    x = torch.empty((N_MICS, N_SAMPLES), dtype=torch.int16, device=dev)
+    E = torch.empty((N_DIRS, plan.n_out), dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            flush(1.0)
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(args.steps):
+            flush(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            ms.append((e0, e1))
+        torch.cuda.synchronize()
+        return [q.elapsed_time(r) for q, r in ms]
+
+    def demod():
+        nat.rtis_pdm_demodulate(words, K, N_MICS, N_SAMPLES, D, None, 0, x, sh)
+
+    def chain():
+        demod()
+        nat.rtis_process(plan.handle, x, E, sh)
+
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        chain_ms = timed(chain)
+        demod_ms = timed(demod)
+        td_ms = timed(lambda: nat.rtis_process(plan.handle, x, E, sh))
+    torch.cuda.synchronize()
+    assert plan.sync() == 0
+    t_chain = sum(chain_ms) / 1e3
+    if world > 1:
+        (t_chain,) = max_over_ranks([t_chain], dev)
+    dm = statistics.mean(demod_ms) / 1e3
+    bytes_alg = K * 4 + N_MICS * N_SAMPLES * 2        # the words once, the int16 recording once
+    peaks = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6773.0))
+    line = {
+        "metric": "energyscapes/s from 1-bit PDM words (demodulation + time-domain chain)",
+        "value": replica_rate(args.steps, world, t_chain), "unit": "energyscapes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_chain / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32 (demodulation), f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("int16; matched filter + time-domain and frequency-domain DAS",
+                                                "second-order sigma-delta PDM at 4.5 MHz (uint32 word per tick); "
+                                                "order-4 CIC demodulation by 10 + time-domain chain"),
+                   "l2": "flushed between steps (512 MiB write, then a 256 MiB read so write-backs finish), "
+                         "outside the timed events"},
+        "pdm_demod": {"kernel": "pdm_demod_kernel", "ms": dm * 1e3, "bound": "hbm",
+                      "achieved_gbs": bytes_alg / dm / 1e9, "peak_gbs": hbm, "frac": bytes_alg / dm / 1e9 / hbm,
+                      "algorithmic_bytes": bytes_alg,
+                      "note": "1.7 MB per launch: launch- and latency-bound at this size"},
+        "td_rtis_process_ms": statistics.mean(td_ms),
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def run_hemisphere_batched(args, rank, world, local):
     """B measurements per step through rtis_process_many: per measurement the matched
     filter and the time-domain energyscape, and for the whole batch the frequency-domain
@@ -915,7 +1000,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-dirs", type=int, default=128, help="directions in the oracle's timed sample")
     ap.add_argument("--workload", default="hemisphere", choices=["hemisphere", "fd_gemm", "ring", "calibration", "paper_design", "stream",
-                                                               "baseband"],
+                                                               "baseband", "pdm"],
                     help="hemisphere: the energyscape chain (default); fd_gemm: the 1200-bin frequency-domain "
                          "beamforming GEMM (32 mics x 64 frames -> 2048 directions); ring: 8 sensors with "
                          "uneven lengths and direction sets in one autotuned, graph-replayed batch; calibration: "
@@ -950,6 +1035,8 @@ def main():
         return run_paper_design(args, rank, world, local)
     if args.workload == "baseband":
         return run_baseband(args, rank, world, local)
+    if args.workload == "pdm":
+        return run_pdm(args, rank, world, local)
     if args.workload == "stream":
         return run_stream(args, rank, world, local)
     if args.batch > 1:

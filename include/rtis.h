@@ -411,6 +411,28 @@ rtis_status rtis_baseline_process(rtis_baseline* b, const int16_t* d_in, float* 
 void rtis_baseline_destroy(rtis_baseline* b);
 
 /*
+ * rtis_pdm_demodulate -- the PDM front end: the microphones record through a
+ * 1-bit sigma-delta ADC (Sec. 2) and the bits are unpacked and low-pass
+ * filtered before the matched filter (Sec. 4.3).  Produces the int16 PCM
+ * recording that rtis_process takes:
+ *   b_m[k] = +1 for bit m of word k set, -1 for clear, 0 for k outside [0, n_words)
+ *   x_m[n] = sat16((sum_j g[j] b_m[decim n + j - c] + r) >> shift),
+ *            c = (n_taps - 1)/2, r = 2^(shift-1) for shift > 0 (halves round up)
+ * The arithmetic is integer, so the result is exact.
+ *   d_words  device uint32 [n_words], one word per bit-clock tick, bit m = mic m
+ *            (4-byte aligned; bits above n_mics are ignored)
+ *   taps     host int32 [n_taps], n_taps <= 256, sum |g| <= 2^30; or NULL for the
+ *            order-4 CIC kernel (the length-decim boxcar convolved 4 times, sum
+ *            decim^4: 10^4 at decim = 10, so no shift is needed)
+ *   decim    bit ticks per output sample, 1..64 (10: 4.5 MHz bits -> 450 kHz)
+ *   shift    right shift 0..30
+ *   d_x      device int16 [n_mics][n_samples], 2-byte aligned
+ * Stream-ordered; needs no plan and allocates nothing.
+ */
+rtis_status rtis_pdm_demodulate(const uint32_t* d_words, long long n_words, int n_mics, int n_samples, int decim,
+                                const int32_t* taps, int n_taps, int shift, int16_t* d_x, void* stream);
+
+/*
  * rtis_matched_filter_noalloc -- the matched filter of rtis_matched_filter
  * for callers that may not allocate device memory: code that runs where
  * cudaMalloc is not allowed or not wanted (a real-time loop that must never

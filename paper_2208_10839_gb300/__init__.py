@@ -7,6 +7,7 @@ This package is the thin Python binding of that ABI.
 from . import _native  # noqa: F401
 from ._native import RtisError, lib  # noqa: F401
 from .calibrate import Calibrator  # noqa: F401
-from .plan import Batch, FdGemm, Plan, energyscape, process_batch  # noqa: F401
+from .plan import Batch, FdGemm, Plan, energyscape, pdm_demodulate, process_batch  # noqa: F401
 
-__all__ = ["Plan", "Batch", "Calibrator", "FdGemm", "energyscape", "process_batch", "RtisError", "lib"]
+__all__ = ["Plan", "Batch", "Calibrator", "FdGemm", "energyscape", "pdm_demodulate", "process_batch", "RtisError",
+           "lib"]

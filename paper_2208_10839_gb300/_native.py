@@ -83,6 +83,8 @@ _PROTOS = {
     "rtis_beamform_td": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_beamform_fd": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_baseband_signal": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "rtis_pdm_demodulate": (C.c_int, [_VP, C.c_longlong, C.c_int, C.c_int, C.c_int, _VP, C.c_int, C.c_int, _VP,
+                                      _VP]),
     "rtis_beamform_bb": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_steering_table": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rtis_plan_sync": (C.c_int, [_VP, C.POINTER(C.c_uint)]),
@@ -215,6 +217,13 @@ def rtis_beamform_fd(plan, d_A, d_out, stream=None):
 
 def rtis_baseband_signal(plan, d_in, d_z, stream=None):
     check(lib().rtis_baseband_signal(plan, ptr(d_in), ptr(d_z), stream_handle(stream)), "rtis_baseband_signal")
+
+
+def rtis_pdm_demodulate(d_words, n_words, n_mics, n_samples, decim, taps, shift, d_x, stream=None):
+    """taps: None (order-4 CIC) or a C-contiguous int32 NumPy array (host)."""
+    tp, nt = (None, 0) if taps is None else (taps.ctypes.data, int(taps.shape[0]))
+    check(lib().rtis_pdm_demodulate(ptr(d_words), int(n_words), int(n_mics), int(n_samples), int(decim), tp, nt,
+                                    int(shift), ptr(d_x), stream_handle(stream)), "rtis_pdm_demodulate")
 
 
 def rtis_beamform_bb(plan, d_z, d_out, stream=None):

@@ -36,6 +36,9 @@ constexpr int kBbVariants = 4;                        // stage layouts: (2, 4), 
 // NaN stays NaN (n2 * 0) so non-finite inputs still show in the output
 __device__ __forceinline__ float magnitude_from_norm(float n2) { return n2 > 0.f ? n2 * rsqrtf(n2) : n2 * 0.f; }
 
+// PDM demodulation (kernels_pdm.cu)
+constexpr int kPdmMaxTaps = 256;
+
 // ----------------------------------------------------------------------------
 // plan
 // ----------------------------------------------------------------------------
@@ -156,6 +159,9 @@ cudaError_t launch_steering_table(Plan& p, cudaStream_t st);
 cudaError_t launch_mf_inverse_bb(const Plan& p, float2* d_z, int stride, cudaStream_t st);
 // zmap: TMA view of z as [M][Nb] 8-byte elements
 cudaError_t launch_bb_beamform(const Plan& p, const CUtensorMap& zmap, float* d_out, cudaStream_t st);
+// x [n_mics][n_samples] int16 from n_words PDM words (taps: host, n_taps <= kPdmMaxTaps)
+cudaError_t launch_pdm_demod(const uint32_t* d_words, long long n_words, int n_mics, int n_samples, int decim,
+                             const int32_t* taps, int n_taps, int shift, int16_t* d_x, cudaStream_t st);
 size_t bb_smem_bytes(const Plan& p);  // the largest stage layout's
 int bb_tiles(const Plan& p);
 cudaError_t bb_autotune(Plan& p, float* d_scratch_out);

@@ -130,6 +130,15 @@ class Plan:
         nat.rtis_beamform_bb(self.handle, z, out, stream)
         return out
 
+    def process_pdm(self, words, decim=10, taps=None, shift=0, out=None, stream=None):
+        """PDM words (int32/uint32 device tensor [n_words], bit m = mic m) -> energyscape:
+        rtis_pdm_demodulate into the plan's int16 input buffer, then process()."""
+        t = self._torch
+        if getattr(self, "_pdm_x", None) is None or self._pdm_x.device != words.device:
+            self._pdm_x = t.empty((self.M, self.N), dtype=t.int16, device=words.device)
+        pdm_demodulate(words, self.M, self.N, decim, taps, shift, out=self._pdm_x, stream=stream)
+        return self.process(self._pdm_x, out=out, stream=stream)
+
     def set_calibration(self, mic_xyz=None, gain=None, delay_s=None, stream=None):
         """Device float tensors [M][3], [M], [M] (seconds); None keeps the current value."""
         t = self._torch
@@ -159,6 +168,18 @@ class Plan:
     def sync(self) -> int:
         """Waits for the device; returns (and clears) the device status bits."""
         return nat.rtis_plan_sync(self.handle)
+
+
+def pdm_demodulate(words, n_mics, n_samples, decim=10, taps=None, shift=0, out=None, stream=None):
+    """PDM front end: words (int32 or uint32 device tensor [n_words], bit m of word k =
+    mic m's k-th bit) -> int16 [n_mics][n_samples], the integer demodulating FIR
+    (order-4 CIC when taps is None) at every `decim`-th bit."""
+    import torch
+    if out is None:
+        out = torch.empty((n_mics, n_samples), dtype=torch.int16, device=words.device)
+    g = None if taps is None else np.ascontiguousarray(taps, dtype=np.int32)
+    nat.rtis_pdm_demodulate(words, int(words.numel()), n_mics, n_samples, decim, g, shift, out, stream)
+    return out
 
 
 class FdGemm:

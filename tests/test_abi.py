@@ -140,3 +140,32 @@ def test_stream_and_baseline_argument_checks(nat):
     assert lib.rtis_baseline_create(C.byref(out), None) == nat.RTIS_ERR_INVALID_ARG
     assert lib.rtis_baseline_process(None, None, None, None) == nat.RTIS_ERR_INVALID_ARG
     assert nat.rtis_status_string(nat.RTIS_ERR_BUSY) == "no free slot"
+
+
+def test_pdm_and_baseband_argument_checks(nat):
+    # every check runs on the host before any launch
+    lib = nat.lib()
+    import ctypes as C
+    fake = 1 << 20   # an aligned non-NULL address that is never dereferenced
+    taps = (C.c_int32 * 3)(1, 2, 1)
+    ok = dict(d_words=fake, n_words=100, n_mics=4, n_samples=10, decim=10, taps=None, n_taps=0, shift=0, d_x=fake)
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        return lib.rtis_pdm_demodulate(a["d_words"], a["n_words"], a["n_mics"], a["n_samples"], a["decim"],
+                                       a["taps"], a["n_taps"], a["shift"], a["d_x"], None)
+    E = nat.RTIS_ERR_INVALID_ARG
+    assert call(d_x=None) == E
+    assert call(d_words=None) == E
+    assert call(d_words=fake + 2) == E                     # words 4-byte aligned
+    assert call(d_x=fake + 1) == E                         # int16 output 2-byte aligned
+    assert call(n_mics=0) == E and call(n_mics=33) == E
+    assert call(n_samples=0) == E and call(n_words=-1) == E
+    assert call(decim=0) == E and call(decim=65) == E
+    assert call(shift=-1) == E and call(shift=31) == E
+    assert call(taps=C.cast(taps, C.c_void_p), n_taps=0) == E
+    assert call(taps=C.cast(taps, C.c_void_p), n_taps=257) == E
+    big = (C.c_int32 * 2)(1 << 30, 1)                      # sum |g| above 2^30
+    assert call(taps=C.cast(big, C.c_void_p), n_taps=2) == E
+    assert lib.rtis_baseband_signal(None, None, None, None) == E
+    assert lib.rtis_beamform_bb(None, None, None, None) == E
