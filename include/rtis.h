@@ -122,6 +122,10 @@ typedef struct rtis_plan_info {
     int bb_variant;              /* RTIS_PATH_BB: baseband beamformer stage layout chosen at creation */
     int bb_grid;                 /* and its grid (CTAs) */
     float bb_tuned_ms;           /* its time on this device when tuned */
+    float td_layout_ms[16];      /* the time-domain autotuner's measurements: mean ms of layout v with
+                                    one CTA per tile at [2v], with the resident persistent grid at
+                                    [2v + 1]; 0 where not tried */
+    float bb_layout_ms[16];      /* the same for the baseband beamformer (RTIS_PATH_BB) */
 } rtis_plan_info;
 
 /*

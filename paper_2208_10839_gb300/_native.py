@@ -55,7 +55,7 @@ class rtis_plan_info(C.Structure):
         ("halo", C.c_int), ("max_shift", C.c_int), ("workspace_bytes", C.c_size_t),
         ("td_variant", C.c_int), ("td_grid", C.c_int), ("td_tuned_ms", C.c_float),
         ("n_coarse", C.c_int), ("k_c", C.c_int), ("bb_variant", C.c_int), ("bb_grid", C.c_int),
-        ("bb_tuned_ms", C.c_float),
+        ("bb_tuned_ms", C.c_float), ("td_layout_ms", C.c_float * 16), ("bb_layout_ms", C.c_float * 16),
     ]
 
 

@@ -276,8 +276,8 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
 }
 
 // stage layouts the autotuner picks from: (mics per stage, stages in the ring)
-constexpr int kBbVariantMS[kBbVariants] = {2, 2, 4, 1};
-constexpr int kBbVariantNS[kBbVariants] = {4, 8, 4, 8};
+constexpr int kBbVariantMS[kBbVariants] = {2, 2, 4, 1, 4, 2};
+constexpr int kBbVariantNS[kBbVariants] = {4, 8, 4, 8, 5, 10};
 
 uint32_t bb_stage_area(const Plan& p, int variant) {
     const size_t ring = static_cast<size_t>(kBbVariantMS[variant]) * kBbVariantNS[variant] * p.bb_row * 8;
@@ -285,8 +285,8 @@ uint32_t bb_stage_area(const Plan& p, int variant) {
 }
 
 size_t bb_smem_variant(const Plan& p, int variant) {
-    // ring, envelope rows, barriers + counters (<= 8 stages), next-tile count, taps
-    return bb_stage_area(p, variant) + static_cast<size_t>(kTdDirsPerCta) * kBbWarpSamples * 4 + 8 * 8 + 2 * 8 * 4 +
+    // ring, envelope rows, barriers + counters (<= 10 stages), next-tile count, taps
+    return bb_stage_area(p, variant) + static_cast<size_t>(kTdDirsPerCta) * kBbWarpSamples * 4 + 10 * (8 + 4 + 4) +
            16 + static_cast<size_t>(4) * p.bb_ntap * 4;
 }
 
@@ -328,17 +328,15 @@ cudaError_t bb_launch(const Plan& p, const CUtensorMap& zmap, float* d_out, int 
         case 1: return bb_launch_t<2, 8>(zmap, A, grid, smem, st);
         case 2: return bb_launch_t<4, 4>(zmap, A, grid, smem, st);
         case 3: return bb_launch_t<1, 8>(zmap, A, grid, smem, st);
+        case 4: return bb_launch_t<4, 5>(zmap, A, grid, smem, st);
+        case 5: return bb_launch_t<2, 10>(zmap, A, grid, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
-size_t bb_smem_bytes(const Plan& p) {
-    size_t m = 0;
-    for (int v = 0; v < kBbVariants; ++v) m = std::max(m, bb_smem_variant(p, v));
-    return m;
-}
+size_t bb_smem_bytes(const Plan& p) { return bb_smem_variant(p, 0); }  // the smallest layout's
 
 int bb_tiles(const Plan& p) {
     return ((p.D + kTdDirsPerCta - 1) / kTdDirsPerCta) * ((p.n_out + p.bb_bins_per_tile - 1) / p.bb_bins_per_tile);
@@ -358,6 +356,7 @@ cudaError_t bb_autotune(Plan& p, float* d_scratch_out) {
     if (e != cudaSuccess) return e;
     float best = 1e30f;
     for (int v = 0; v < kBbVariants && e == cudaSuccess; ++v) {
+        if (bb_smem_variant(p, v) > 227 * 1024) continue;
         for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
             e = bb_launch(p, p.tmap_zb, d_scratch_out, v, grids[gi], 0);  // warm-up
             float total = 0.f;
@@ -370,6 +369,7 @@ cudaError_t bb_autotune(Plan& p, float* d_scratch_out) {
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
                 total += ms;
             }
+            if (e == cudaSuccess) p.bb_variant_ms[2 * v + gi] = total / 2.f;
             if (e == cudaSuccess && total < best) {
                 best = total;
                 p.bb_variant = v;

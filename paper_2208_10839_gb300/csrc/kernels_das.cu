@@ -475,6 +475,7 @@ cudaError_t td_autotune(Plan& p, float* d_scratch_out) {
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
                 total += ms;
             }
+            if (e == cudaSuccess) p.td_variant_ms[2 * v + gi] = total / 2.f;
             if (e == cudaSuccess && total < best) {
                 best = total;
                 p.td_variant = v;

@@ -505,6 +505,10 @@ rtis_status rtis_plan_get_info(const rtis_plan* plan, rtis_plan_info* info) {
     info->bb_variant = p.bb_variant;
     info->bb_grid = p.bb_grid;
     info->bb_tuned_ms = p.bb_tuned_ms;
+    for (int i = 0; i < 16; ++i) {
+        info->td_layout_ms[i] = p.td_variant_ms[i];
+        info->bb_layout_ms[i] = p.bb_variant_ms[i];
+    }
     return RTIS_OK;
 }
 

@@ -30,7 +30,7 @@ constexpr int kBbQ = 4;                               // full-rate samples per c
 constexpr int kBbOutPerThread = 14;                   // coarse samples per lane: T/2 odd, conflict-free 16-byte loads
 constexpr int kBbWarpSamples = 32 * kBbOutPerThread;
 constexpr int kBbBox = 96;                            // TMA box width (8-byte elements)
-constexpr int kBbVariants = 4;                        // stage layouts: (2, 4), (2, 8), (4, 4), (1, 8)
+constexpr int kBbVariants = 6;  // stage layouts: (2, 4), (2, 8), (4, 4), (1, 8), (4, 5), (2, 10)
 
 // |z| from |z|^2 = x^2 + y^2 as n2 rsqrt(n2) (a few ulp, no slow path); 0 for 0, and a
 // NaN stays NaN (n2 * 0) so non-finite inputs still show in the output
@@ -52,6 +52,7 @@ struct Plan {
     int td_bins_per_tile = 0, td_row = 0, td_nbox = 0;
     int td_variant = 0, td_grid = 0;  // beamformer stage layout and grid, autotuned at creation
     float td_tuned_ms = 0.f;
+    float td_variant_ms[2 * 8] = {};  // autotuner: mean ms per (layout, grid choice), 0 if not tried
     double fs = 0, c = 0;
     rtis_options opt{};
 
@@ -95,6 +96,7 @@ struct Plan {
     int bb_row = 0, bb_nbox = 0, bb_bins_per_tile = 0, bb_ntap = 0;
     int bb_variant = 0, bb_grid = 0;  // baseband stage layout and grid, autotuned at creation
     float bb_tuned_ms = 0.f;
+    float bb_variant_ms[2 * 8] = {};
     int* d_bshift = nullptr;    // [D][M] floor(delta / 4)
     float4* d_bwt = nullptr;    // [D][M] Catmull-Rom weights of delta/4 - floor(delta/4)
     float2* d_brot = nullptr;   // [D][M] g_m (cos, sin)(2 pi k_c delta / F)
@@ -162,7 +164,7 @@ cudaError_t launch_bb_beamform(const Plan& p, const CUtensorMap& zmap, float* d_
 // x [n_mics][n_samples] int16 from n_words PDM words (taps: host, n_taps <= kPdmMaxTaps)
 cudaError_t launch_pdm_demod(const uint32_t* d_words, long long n_words, int n_mics, int n_samples, int decim,
                              const int32_t* taps, int n_taps, int shift, int16_t* d_x, cudaStream_t st);
-size_t bb_smem_bytes(const Plan& p);  // the largest stage layout's
+size_t bb_smem_bytes(const Plan& p);  // the smallest stage layout's
 int bb_tiles(const Plan& p);
 cudaError_t bb_autotune(Plan& p, float* d_scratch_out);
 // bf16: tmap views BF16 pairs (4-byte elements) rather than complex floats
