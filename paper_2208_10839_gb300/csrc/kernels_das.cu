@@ -339,15 +339,29 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
         }
         __syncwarp();
         if (dir_ok) {
+            // each lane takes bins lane, lane + 32, lane + 64 of a group of 96 in one pass over
+            // the taps (each tap loaded once for three bins); lanes past the tile's last bin
+            // compute that bin again and discard it
             float* Erow = S.E + static_cast<size_t>(d) * S.n_out;
-            for (int il = lane; il < S.bins_per_tile; il += 32) {
-                const int i = i0 + il;
-                if (i >= S.n_out) break;
-                const float* e = env + S.R * il;
-                float acc_e = 0.f;
-                for (int j = 0; j < S.lpf_len; ++j) acc_e = fmaf(hs[j], e[j], acc_e);
-                if (!isfinite(acc_e)) atomicOr(bt.status, RTIS_DEV_NONFINITE);
-                Erow[i] = acc_e;
+            const int nb = min(S.bins_per_tile, S.n_out - i0);
+            for (int base = 0; base < nb; base += 96) {
+                const int il0 = base + lane, il1 = il0 + 32, il2 = il0 + 64;
+                const float* e0 = env + S.R * min(il0, nb - 1);
+                const float* e1 = env + S.R * min(il1, nb - 1);
+                const float* e2 = env + S.R * min(il2, nb - 1);
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 4
+                for (int j = 0; j < S.lpf_len; ++j) {
+                    const float h = hs[j];
+                    a0 = fmaf(h, e0[j], a0);
+                    a1 = fmaf(h, e1[j], a1);
+                    a2 = fmaf(h, e2[j], a2);
+                }
+                if (il0 < nb) Erow[i0 + il0] = a0;
+                if (il1 < nb) Erow[i0 + il1] = a1;
+                if (il2 < nb) Erow[i0 + il2] = a2;
+                if ((il0 < nb && !isfinite(a0)) || (il1 < nb && !isfinite(a1)) || (il2 < nb && !isfinite(a2)))
+                    atomicOr(bt.status, RTIS_DEV_NONFINITE);
             }
         }
     }
