@@ -139,3 +139,18 @@ def test_baseband_signal_and_stage_split(torch_cuda):
     with Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], 8192) as p:
         with pytest.raises(RtisError):
             p.baseband_signal(x)
+
+
+def test_autotuner_timings_are_reported(torch_cuda):
+    # the autotuners keep every layout's time; the chosen layout is the fastest tried
+    from paper_2208_10839_gb300 import Plan
+    cfg = synth.single_sensor(n_samples=8192, n_dirs=64)
+    with Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], 8192, path="bb") as p:
+        i = p.info
+        td = [v for v in i.td_layout_ms]
+        bb = [v for v in i.bb_layout_ms]
+    for times, variant, tuned in ((td, i.td_variant, i.td_tuned_ms), (bb, i.bb_variant, i.bb_tuned_ms)):
+        tried = [v for v in times if v > 0]
+        assert len(tried) >= 4
+        assert min(tried) == pytest.approx(tuned, rel=1e-6)
+        assert min(times[2 * variant], times[2 * variant + 1] or 1e30) == pytest.approx(tuned, rel=1e-6)
