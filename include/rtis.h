@@ -101,6 +101,12 @@ typedef struct rtis_options {
     double position_slack_m;     /* bound on calibrated mic displacement (default 0.01) */
     int max_batch;               /* most measurements one rtis_process_many call takes through
                                     the batched FD GEMM (0: none, <= 64); sizes its buffers */
+    int td_layout;               /* time-domain beamformer stage layout: 0 = autotune at creation
+                                    (default), k = layout k-1 of rtis_plan_info.td_layout_ms */
+    int bb_layout;               /* the same for the baseband beamformer (RTIS_PATH_BB) */
+    int grid_mode;               /* with a forced layout: 0 or 1 = one CTA per tile, 2 = the CTAs
+                                    resident at once looping over the tiles.  Every layout and grid
+                                    gives the same results bit for bit (only the staging differs) */
 } rtis_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -44,6 +44,9 @@ class rtis_options(C.Structure):
         ("max_delay_s", C.c_double),
         ("position_slack_m", C.c_double),
         ("max_batch", C.c_int),
+        ("td_layout", C.c_int),
+        ("bb_layout", C.c_int),
+        ("grid_mode", C.c_int),
     ]
 
 

@@ -337,6 +337,9 @@ cudaError_t bb_launch(const Plan& p, const CUtensorMap& zmap, float* d_out, int 
 }  // namespace
 
 size_t bb_smem_bytes(const Plan& p) { return bb_smem_variant(p, 0); }  // the smallest layout's
+bool bb_variant_fits(const Plan& p, int variant) {
+    return variant >= 0 && variant < kBbVariants && bb_smem_variant(p, variant) <= 227 * 1024;
+}
 
 int bb_tiles(const Plan& p) {
     return ((p.D + kTdDirsPerCta - 1) / kTdDirsPerCta) * ((p.n_out + p.bb_bins_per_tile - 1) / p.bb_bins_per_tile);
@@ -356,7 +359,7 @@ cudaError_t bb_autotune(Plan& p, float* d_scratch_out) {
     if (e != cudaSuccess) return e;
     float best = 1e30f;
     for (int v = 0; v < kBbVariants && e == cudaSuccess; ++v) {
-        if (bb_smem_variant(p, v) > 227 * 1024) continue;
+        if (!bb_variant_fits(p, v)) continue;
         for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
             e = bb_launch(p, p.tmap_zb, d_scratch_out, v, grids[gi], 0);  // warm-up
             float total = 0.f;

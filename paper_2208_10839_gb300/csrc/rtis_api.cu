@@ -207,6 +207,9 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: max_batch must be in [0, 64]");
     if (opt.precision == RTIS_PREC_BF16 && opt.path != RTIS_PATH_TD)
         return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: BF16 storage applies to the time-domain path only");
+    if (opt.td_layout < 0 || opt.td_layout > rtis::kTdVariants || opt.bb_layout < 0 ||
+        opt.bb_layout > rtis::kBbVariants || opt.grid_mode < 0 || opt.grid_mode > 2)
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: td_layout, bb_layout or grid_mode out of range");
     if (!rtis::all_finite(mic_xyz, 3 * static_cast<size_t>(n_mics)) ||
         !rtis::all_finite(directions, 3 * static_cast<size_t>(n_dirs)) ||
         !rtis::all_finite(chirp, chirp_len) || (opt.lpf_taps && !rtis::all_finite(opt.lpf_taps, lpf_len)))
@@ -449,8 +452,27 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         e = cudaMemset(p.d_a, 0, static_cast<size_t>(n_mics) * n_samples * sizeof(float2));
         if (e == cudaSuccess && p.a_bf16) e = cudaMemset(p.d_a16, 0, static_cast<size_t>(n_mics) * n_samples * 4);
         if (e == cudaSuccess) e = cudaMalloc(&scratch, static_cast<size_t>(n_dirs) * p.n_out * sizeof(float));
-        if (e == cudaSuccess) e = rtis::td_autotune(p, scratch);
-        if (e == cudaSuccess && opt.path == RTIS_PATH_BB) e = rtis::bb_autotune(p, scratch);
+        int n_sm = 1, dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 1;
+        if (opt.td_layout > 0) {  // forced: no autotuning (every TD layout stages the same bytes)
+            p.td_variant = opt.td_layout - 1;
+            p.td_grid = opt.grid_mode == 2 ? std::min(rtis::td_tiles(p), 2 * n_sm) : rtis::td_tiles(p);
+        } else if (e == cudaSuccess) {
+            e = rtis::td_autotune(p, scratch);
+        }
+        if (opt.path == RTIS_PATH_BB && opt.bb_layout > 0) {
+            if (!rtis::bb_variant_fits(p, opt.bb_layout - 1)) {
+                cudaFree(scratch);
+                rtis::free_plan_buffers(p);
+                delete plan;
+                return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: the forced bb_layout does not fit shared memory");
+            }
+            p.bb_variant = opt.bb_layout - 1;
+            p.bb_grid = opt.grid_mode == 2 ? std::min(rtis::bb_tiles(p), 2 * n_sm) : rtis::bb_tiles(p);
+        } else if (e == cudaSuccess && opt.path == RTIS_PATH_BB) {
+            e = rtis::bb_autotune(p, scratch);
+        }
         if (scratch) cudaFree(scratch);
         if (e == cudaSuccess) e = cudaMemcpy(&bits, p.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {

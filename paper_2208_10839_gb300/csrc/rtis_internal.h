@@ -165,6 +165,7 @@ cudaError_t launch_bb_beamform(const Plan& p, const CUtensorMap& zmap, float* d_
 cudaError_t launch_pdm_demod(const uint32_t* d_words, long long n_words, int n_mics, int n_samples, int decim,
                              const int32_t* taps, int n_taps, int shift, int16_t* d_x, cudaStream_t st);
 size_t bb_smem_bytes(const Plan& p);  // the smallest stage layout's
+bool bb_variant_fits(const Plan& p, int variant);
 int bb_tiles(const Plan& p);
 cudaError_t bb_autotune(Plan& p, float* d_scratch_out);
 // bf16: tmap views BF16 pairs (4-byte elements) rather than complex floats

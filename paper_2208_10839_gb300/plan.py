@@ -19,7 +19,7 @@ class Plan:
 
     def __init__(self, mic_xyz, fs, chirp, directions, n_samples, *, c=343.0, decim=10, lpf_taps=None,
                  band=(20e3, 80e3), path="td", precision="fp32", max_delay_s=10e-6, position_slack_m=0.01,
-                 max_batch=0):
+                 max_batch=0, td_layout=None, bb_layout=None, grid="tile"):
         import torch  # device memory and streams only
         self._torch = torch
         o = nat.default_options()
@@ -36,6 +36,11 @@ class Plan:
         o.max_delay_s = float(max_delay_s)
         o.position_slack_m = float(position_slack_m)
         o.max_batch = int(max_batch)
+        # beamformer stage layouts: None = autotuned at creation; an index forces that layout,
+        # with one CTA per tile (grid="tile") or the resident CTAs looping (grid="persistent")
+        o.td_layout = 0 if td_layout is None else int(td_layout) + 1
+        o.bb_layout = 0 if bb_layout is None else int(bb_layout) + 1
+        o.grid_mode = {"tile": 1, "persistent": 2}[grid]
         self.handle = nat.rtis_plan_create(mic_xyz, fs, chirp, directions, n_samples, o)
         self.info_path = path
         self.info = nat.rtis_plan_get_info(self.handle)

@@ -76,6 +76,10 @@ def _args():
     (dict(band=(20e3, 150e3)), 4),        # band above fs/4
     (dict(precision=2), 4),               # FP16 storage is not offered
     (dict(precision=1, path=1), 4),       # BF16 storage on the frequency-domain path
+    (dict(path=3), 1),                    # no such path
+    (dict(td_layout=4), 1),               # 3 time-domain layouts
+    (dict(bb_layout=7), 1),               # 6 baseband layouts
+    (dict(grid_mode=3), 1),
 ])
 def test_plan_create_rejects(nat, kw, status):
     mic, ch, dirs = _args()
@@ -95,6 +99,9 @@ def test_plan_create_rejects(nat, kw, status):
         o.precision = kw["precision"]
     if "path" in kw:
         o.path = kw["path"]
+    for f in ("td_layout", "bb_layout", "grid_mode"):
+        if f in kw:
+            setattr(o, f, kw[f])
     with pytest.raises(nat.RtisError) as ei:
         nat.rtis_plan_create(mic, kw.get("fs", 450e3), ch, dirs, kw.get("n_samples", 4096), o)
     assert ei.value.status == status

@@ -154,3 +154,33 @@ def test_autotuner_timings_are_reported(torch_cuda):
         assert len(tried) >= 4
         assert min(tried) == pytest.approx(tuned, rel=1e-6)
         assert min(times[2 * variant], times[2 * variant + 1] or 1e30) == pytest.approx(tuned, rel=1e-6)
+
+
+def test_every_layout_and_grid_gives_the_same_energyscape(torch_cuda):
+    # forced layouts and grids (the persistent grid loops over many tiles, the baseband
+    # one prefetching the next tile's rows) against the autotuned plan: bit for bit,
+    # since every layout sums the mics in the same order; the autotuned plan itself
+    # is held to the oracle by the other tests
+    torch = torch_cuda
+    from paper_2208_10839_gb300 import Plan
+    cfg = synth.hemisphere(n_dirs=1024, n_samples=8192)
+    x = torch.from_numpy(cfg["x"]).cuda()
+    args = (cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], 8192)
+    ref = {}
+    for path in ("td", "bb"):
+        with Plan(*args, path=path) as p:
+            ref[path] = p.process(x).cpu().numpy()
+            assert p.sync() == 0
+    for grid in ("tile", "persistent"):
+        for v in range(3):
+            with Plan(*args, td_layout=v, grid=grid) as p:
+                assert (p.info.td_variant, p.info.td_grid > 0) == (v, True)
+                E = p.process(x).cpu().numpy()
+                assert p.sync() == 0
+            assert np.array_equal(E, ref["td"]), ("td", v, grid)
+        for v in range(6):
+            with Plan(*args, path="bb", bb_layout=v, grid=grid) as p:
+                assert p.info.bb_variant == v
+                E = p.process(x).cpu().numpy()
+                assert p.sync() == 0
+            assert np.array_equal(E, ref["bb"]), ("bb", v, grid)
