@@ -9,9 +9,11 @@
 // The taps g are integers, so the sum is exact and the result is the same
 // integer on every device.  One CTA takes kPdmOut output samples of every mic:
 // the (kPdmOut - 1) D + L words they read carry all 32 mics, so they are
-// staged once in shared memory (with a validity mask for the record's edges);
-// warp w then computes mics w, w + 8, w + 16, w + 24, lane = output sample, so
-// the int16 stores of a warp are 64 contiguous bytes of one mic's row.
+// staged once in shared memory (0 outside the record, with a validity mask).
+// Lane = mic: every lane of a warp reads the same word (a shared-memory
+// broadcast) and takes its own bit; warp w computes outputs w, w + 8, ... of
+// the tile.  The results go through shared memory, so that each int16 row
+// segment is written as one contiguous store.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -21,7 +23,7 @@
 namespace rtis {
 namespace {
 
-constexpr int kPdmOut = 64;      // output samples per CTA
+constexpr int kPdmOut = 16;      // output samples per CTA (1024 CTAs at 16384 samples)
 constexpr int kPdmThreads = 256;
 
 struct PdmArgs {
@@ -37,6 +39,7 @@ __global__ void __launch_bounds__(kPdmThreads) pdm_demod_kernel(const __grid_con
     const int span = (kPdmOut - 1) * A.D + A.L;
     uint32_t* sv = sw + span;
     __shared__ int32_t gs[kPdmMaxTaps];
+    __shared__ int16_t xs[32][kPdmOut + 2];  // [mic][output], rows padded
     const int n0 = blockIdx.x * kPdmOut;
     const long long k0 = static_cast<long long>(n0) * A.D - A.c;  // word of tap 0 for output n0
     for (int i = threadIdx.x; i < span; i += kPdmThreads) {
@@ -49,20 +52,31 @@ __global__ void __launch_bounds__(kPdmThreads) pdm_demod_kernel(const __grid_con
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int32_t rnd = A.shift > 0 ? (1 << (A.shift - 1)) : 0;
+    for (int t = warp; t < kPdmOut; t += kPdmThreads / 32) {
+        const uint32_t* w = sw + t * A.D;
+        const uint32_t* v = sv + t * A.D;
+        int32_t acc = 0;
+#pragma unroll 4
+        for (int j = 0; j < A.L; ++j) {
+            // +1 / -1 from this lane's bit, 0 outside the record (same word for the whole warp)
+            const int32_t b = (static_cast<int32_t>((w[j] >> lane) & 1u) * 2 - 1) & static_cast<int32_t>(v[j]);
+            acc += gs[j] * b;
+        }
+        const int32_t y = (acc + rnd) >> A.shift;
+        xs[lane][t] = static_cast<int16_t>(max(-32768, min(32767, y)));
+    }
+    __syncthreads();
+    // rows out: warp w writes mics w, w + 8, ...; a lane two consecutive samples
     for (int m = warp; m < A.M; m += kPdmThreads / 32) {
-        for (int t = lane; t < kPdmOut; t += 32) {
+        for (int t = 2 * lane; t < kPdmOut; t += 64) {  // kPdmOut <= 64: one pass
             const int n = n0 + t;
-            if (n >= A.N) break;
-            const uint32_t* w = sw + t * A.D;
-            const uint32_t* v = sv + t * A.D;
-            int32_t acc = 0;
-            for (int j = 0; j < A.L; ++j) {
-                // +1 / -1 from the bit, 0 outside the record
-                const int32_t b = (static_cast<int32_t>((w[j] >> m) & 1u) * 2 - 1) & static_cast<int32_t>(v[j]);
-                acc += gs[j] * b;
+            int16_t* dst = A.x + static_cast<size_t>(m) * A.N + n;
+            if (n + 1 < A.N && ((reinterpret_cast<uintptr_t>(dst) & 3) == 0)) {
+                *reinterpret_cast<short2*>(dst) = make_short2(xs[m][t], xs[m][t + 1]);
+            } else {
+                if (n < A.N) dst[0] = xs[m][t];
+                if (n + 1 < A.N) dst[1] = xs[m][t + 1];
             }
-            const int32_t y = (acc + rnd) >> A.shift;
-            A.x[static_cast<size_t>(m) * A.N + n] = static_cast<int16_t>(max(-32768, min(32767, y)));
         }
     }
 }
