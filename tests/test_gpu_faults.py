@@ -2,7 +2,6 @@
 made to run out (the injected stall withholds one TMA copy per CTA), a
 non-finite input, and an injected launch failure.  After each, the context
 stays usable and the next call gives the normal result."""
-import numpy as np
 import pytest
 
 import synth
