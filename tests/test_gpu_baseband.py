@@ -184,3 +184,20 @@ def test_every_layout_and_grid_gives_the_same_energyscape(torch_cuda):
                 E = p.process(x).cpu().numpy()
                 assert p.sync() == 0
             assert np.array_equal(E, ref["bb"]), ("bb", v, grid)
+
+
+@pytest.mark.parametrize("M,N,D,decim", [(1, 4096, 1, 10), (4, 64000, 5, 10), (32, 4104, 3, 9), (13, 2052, 21, 4)])
+def test_baseband_edge_shapes(torch_cuda, M, N, D, decim):
+    # one mic and one direction; near the longest record (F = 65536); N/4 odd (padded
+    # rows of z); R a multiple of 4 (a single low-pass residue)
+    torch = torch_cuda
+    from paper_2208_10839_gb300 import Plan
+    mic = synth.mic_array(M + 100, M)
+    dirs = synth.fibonacci_hemisphere(D)
+    chirp = synth.chirp().astype(np.float32)
+    x = synth.random_measurement(N + 7 * D, M, N, -20000, 20000)
+    with Plan(mic, synth.FS, chirp, dirs, N, path="bb", decim=decim) as p:
+        E = p.process(torch.from_numpy(x).cuda()).cpu().numpy()
+        assert p.sync() == 0
+    ref = orc.energyscape(x, chirp, mic, dirs, synth.FS, synth.C_SOUND, path="bb", R=decim)
+    assert_close(E, ref)

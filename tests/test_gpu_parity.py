@@ -141,6 +141,7 @@ def test_process_single_sensor_config(torch_cuda):
     (32, 6000, 9, 7, 29),            # other decimation / low-pass length
     (32, 2048, 40, 10, 1),           # single-tap (no) low-pass
     (17, 1000, 33, 3, 13),           # short record, tile covers all of it
+    (4, 64000, 5, 10, None),         # near the longest record (F = 65536)
 ])
 def test_process_edge_shapes(torch_cuda, M, N, D, decim, taps):
     torch = torch_cuda
