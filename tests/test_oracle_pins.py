@@ -569,3 +569,55 @@ def test_sigma_delta_tone_through_the_cic_demodulator():
     inb = (f >= 20e3) & (f <= 80e3)
     snr = 10 * np.log10((np.hypot(*coef) ** 2 / 2 * res.size) / (2 * np.sum(np.abs(R[inb]) ** 2) / res.size))
     assert snr > 45
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_envelope_decimate_bb_bruteforce(seed):
+    # the coarse-grid low-pass written as a loop over output bins and full-rate offsets t:
+    # taps where Q divides t + R i, renormalised over the taps that exist
+    rng = np.random.default_rng(40 + seed)
+    Q = int(rng.choice([2, 4]))
+    R = int(rng.integers(1, 13))
+    N = int(rng.integers(40, 300)) * Q
+    Nb = N // Q
+    b = rng.normal(size=(2, Nb)) + 1j * rng.normal(size=(2, Nb))
+    L = 2 * int(rng.integers(0, 9)) + 1
+    h = rng.uniform(0.1, 1.0, size=L)
+    half = (L - 1) // 2
+    E = orc.envelope_decimate_bb(b, N, R, Q, h)
+    for d in range(2):
+        for i in range(N // R):
+            num = den = 0.0
+            for t in range(-half, half + 1):
+                if (R * i + t) % Q == 0:
+                    j = (R * i + t) // Q
+                    den += h[t + half]
+                    if 0 <= j < Nb:
+                        num += h[t + half] * abs(b[d, j])
+            assert abs(E[d, i] - num / den) <= 1e-12 * max(1.0, abs(num / den))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_pdm_demodulate_bruteforce(seed):
+    # random words, taps (including negative), decimation and shift against a plain loop
+    rng = np.random.default_rng(50 + seed)
+    M = int(rng.integers(1, 6))
+    D = int(rng.integers(1, 9))
+    N = int(rng.integers(1, 40))
+    K = N * D - int(rng.integers(0, D + 1))
+    bits = rng.integers(0, 2, size=(M, K))
+    L = int(rng.integers(1, 12))
+    g = rng.integers(-50, 200, size=L)
+    shift = int(rng.integers(0, 4))
+    x = orc.pdm_demodulate(bits, g, D, N, shift)
+    c = (L - 1) // 2
+    for m in range(M):
+        for n in range(N):
+            acc = 0
+            for j in range(L):
+                k = D * n + j - c
+                if 0 <= k < K:
+                    acc += int(g[j]) * (2 * int(bits[m, k]) - 1)
+            if shift:
+                acc = (acc + (1 << (shift - 1))) >> shift
+            assert x[m, n] == max(-32768, min(32767, acc))
