@@ -176,3 +176,20 @@ def test_pdm_and_baseband_argument_checks(nat):
     assert call(taps=C.cast(big, C.c_void_p), n_taps=2) == E
     assert lib.rtis_baseband_signal(None, None, None, None) == E
     assert lib.rtis_beamform_bb(None, None, None, None) == E
+
+
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: the header compiles as strict C99 (and as C++), no torch types
+    import shutil
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "use.c"
+    src.write_text('#include "rtis.h"\nint main(void) { rtis_options o; rtis_options_default(&o); return o.path; }\n')
+    for cc, args in (("gcc", ["-std=c99", "-pedantic"]), ("g++", ["-std=c++17", "-x", "c++"])):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not found")
+        r = subprocess.run([cc, *args, "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                            "-I", os.path.join(root, "include"), str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    header = open(os.path.join(root, "include", "rtis.h")).read()
+    assert "torch" not in header and "at::" not in header
