@@ -171,6 +171,39 @@ def oracle_sample_time(cfg, n_dirs_sample: int, seed: int = 0):
     return (t1 - t0) + (t2 - t1) * D / n_dirs_sample, (t1 - t0), (t2 - t1)
 
 
+def _oracle_worker(job):
+    """One spawn worker of oracle_pool_rate: time the oracle on its own measurement."""
+    seed, n_dirs_sample = job
+    import synth
+    cfg = synth.hemisphere(seed_scene=1 + seed)
+    return oracle_sample_time(cfg, n_dirs_sample, seed=seed)[0]
+
+
+def oracle_pool_rate(n_dirs_sample: int, procs: int = 0):
+    """Energyscapes/s of the FP64 oracle on all host cores, the way the paper's CPU workers run:
+    `procs` spawned processes (default: the cores this process may use), each timing one
+    measurement on a bounded direction sample (scaled to all directions), all at once; the rate is
+    procs / the slowest worker's time.  Spawned, not forked, so it is safe after CUDA is up."""
+    import multiprocessing as mp
+    procs = procs or len(os.sched_getaffinity(0))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        times = pool.map(_oracle_worker, [(k, n_dirs_sample) for k in range(procs)], chunksize=1)
+    return procs / max(times), procs
+
+
+def all_cores_baseline(n_dirs_sample: int):
+    """The cpu_baseline_all_cores entry of a bench line; a failure of the process pool is
+    reported in the entry rather than ending the benchmark."""
+    try:
+        rate, procs = oracle_pool_rate(n_dirs_sample)
+    except Exception as exc:  # noqa: BLE001 -- a host-side extra must not cost the GPU measurement
+        return {"unavailable": f"oracle process pool failed: {type(exc).__name__}: {exc}"[:300]}
+    return {"value": rate, "unit": "energyscapes/s", "cores": procs, "kind": "oracle",
+            "sample": f"FP64 oracle in {procs} spawned processes at once, one measurement each: matched filter "
+                      f"on all 32 channels + both DAS forms on {n_dirs_sample} of {N_DIRS} directions, scaled to "
+                      f"{N_DIRS}; rate = processes / slowest"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -984,6 +1017,7 @@ def run_hemisphere_batched(args, rank, world, local):
                                           f"({t_mf:.2f} s) + time- and frequency-domain DAS/envelope on "
                                           f"{args.cpu_dirs} of {N_DIRS} directions ({t_das:.2f} s), scaled to "
                                           f"{N_DIRS} directions"}
+        line["cpu_baseline_all_cores"] = all_cores_baseline(args.cpu_pool_dirs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -998,6 +1032,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-pool-dirs", type=int, default=16,
+                    help="directions each all-cores oracle worker times (scaled to all directions)")
     ap.add_argument("--cpu-dirs", type=int, default=128, help="directions in the oracle's timed sample")
     ap.add_argument("--workload", default="hemisphere", choices=["hemisphere", "fd_gemm", "ring", "calibration", "paper_design", "stream",
                                                                "baseband", "pdm"],
@@ -1231,6 +1267,7 @@ def main():
                                           f"({t_mf:.2f} s) + time- and frequency-domain DAS/envelope on "
                                           f"{args.cpu_dirs} of {N_DIRS} directions ({t_das:.2f} s), scaled to "
                                           f"{N_DIRS} directions"}
+        line["cpu_baseline_all_cores"] = all_cores_baseline(args.cpu_pool_dirs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -27,3 +27,11 @@ def test_reference_arm_prints_one_contract_line():
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"]
+
+
+def test_all_cores_oracle_baseline_runs_in_spawned_workers():
+    import bench
+    rate, procs = bench.oracle_pool_rate(2, procs=2)
+    assert procs == 2 and rate > 0
+    entry = bench.all_cores_baseline(2)
+    assert entry["kind"] == "oracle" and entry["cores"] >= 1 and entry["value"] > 0
