@@ -186,8 +186,9 @@ def oracle_pool_rate(n_dirs_sample: int, procs: int = 0):
     procs / the slowest worker's time.  Spawned, not forked, so it is safe after CUDA is up."""
     import multiprocessing as mp
     procs = procs or len(os.sched_getaffinity(0))
-    with mp.get_context("spawn").Pool(procs) as pool:
-        times = pool.map(_oracle_worker, [(k, n_dirs_sample) for k in range(procs)], chunksize=1)
+    with mp.get_context("spawn").Pool(procs) as pool:  # leaving the block terminates the workers
+        jobs = pool.map_async(_oracle_worker, [(k, n_dirs_sample) for k in range(procs)], chunksize=1)
+        times = jobs.get(timeout=600)  # a worker that died would otherwise leave map() waiting
     return procs / max(times), procs
 
 
