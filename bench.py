@@ -153,8 +153,10 @@ class L2Flush:
         self.sink = self.r.sum()
 
 
-def oracle_sample_time(cfg, n_dirs_sample: int, seed: int = 0):
-    """Seconds the FP64 oracle needs for one step (both energyscapes), from a direction sample."""
+def oracle_sample(cfg, n_dirs_sample: int, seed: int = 0):
+    """The FP64 oracle on a seeded sample of directions: (seconds for one step scaled to all
+    directions, matched-filter seconds, sampled-DAS seconds, sampled direction indices, TD rows,
+    FD rows)."""
     import oracle
     rng = np.random.default_rng(seed)
     pick = np.sort(rng.choice(cfg["dirs"].shape[0], n_dirs_sample, replace=False))
@@ -164,11 +166,30 @@ def oracle_sample_time(cfg, n_dirs_sample: int, seed: int = 0):
     t1 = time.perf_counter()
     delta = oracle.steering_delays(cfg["mic_xyz"], cfg["dirs"][pick], cfg["fs"], cfg["c"])
     h = oracle.lpf_taps()
-    oracle.envelope_decimate(oracle.das_td(a, delta), h)
-    oracle.envelope_decimate(oracle.das_fd(A, k_lo, F, cfg["n_samples"], delta), h)
+    e_td = oracle.envelope_decimate(oracle.das_td(a, delta), h)
+    e_fd = oracle.envelope_decimate(oracle.das_fd(A, k_lo, F, cfg["n_samples"], delta), h)
     t2 = time.perf_counter()
     D = cfg["dirs"].shape[0]
-    return (t1 - t0) + (t2 - t1) * D / n_dirs_sample, (t1 - t0), (t2 - t1)
+    return (t1 - t0) + (t2 - t1) * D / n_dirs_sample, (t1 - t0), (t2 - t1), pick, e_td, e_fd
+
+
+def oracle_sample_time(cfg, n_dirs_sample: int, seed: int = 0):
+    """Seconds the FP64 oracle needs for one step (both energyscapes), from a direction sample."""
+    return oracle_sample(cfg, n_dirs_sample, seed)[:3]
+
+
+def oracle_error_entry(pick, pairs):
+    """The bench line's error against the FP64 oracle on the sampled directions.  pairs: name ->
+    (oracle rows [n][n_out], the GPU energyscape [D][n_out] as a tensor or array).  Reported, not
+    a pass/fail: the tests hold the tolerance."""
+    out = {"directions_sampled": int(len(pick)), "fp32_tolerance_over_peak": 1e-4}
+    for name, (ref, E) in pairs.items():
+        got = np.asarray(E.cpu().numpy() if hasattr(E, "cpu") else E, dtype=np.float64)[pick]
+        ref = np.asarray(ref, dtype=np.float64)
+        peak = float(ref.max())
+        out[name] = {"max_abs_err_over_peak": float(np.max(np.abs(got - ref)) / peak),
+                     "peak_index_match": bool(np.argmax(got) == np.argmax(ref))}
+    return out
 
 
 def _oracle_worker(job):
@@ -1012,7 +1033,12 @@ def run_hemisphere_batched(args, rank, world, local):
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_es, t_mf, t_das = oracle_sample_time(cfg, args.cpu_dirs)
+        t_es, t_mf, t_das, pick, o_td, o_fd = oracle_sample(cfg, args.cpu_dirs)
+        try:
+            line["error_vs_oracle"] = oracle_error_entry(pick, {"td": (o_td, E_td[0] if E_td.dim() == 3 else E_td),
+                                                                "fd": (o_fd, E_fd[0] if E_fd.dim() == 3 else E_fd)})
+        except Exception as exc:  # noqa: BLE001 -- a reporting extra must not cost the GPU measurement
+            line["error_vs_oracle"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:300]}
         line["cpu_baseline"] = {"value": 1.0 / t_es, "unit": "energyscapes/s", "cores": 1, "kind": "oracle",
                                 "sample": f"FP64 oracle, one process: matched filter on all 32 channels "
                                           f"({t_mf:.2f} s) + time- and frequency-domain DAS/envelope on "
@@ -1262,7 +1288,12 @@ def main():
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_es, t_mf, t_das = oracle_sample_time(cfg, args.cpu_dirs)
+        t_es, t_mf, t_das, pick, o_td, o_fd = oracle_sample(cfg, args.cpu_dirs)
+        try:
+            line["error_vs_oracle"] = oracle_error_entry(pick, {"td": (o_td, E_td[0] if E_td.dim() == 3 else E_td),
+                                                                "fd": (o_fd, E_fd[0] if E_fd.dim() == 3 else E_fd)})
+        except Exception as exc:  # noqa: BLE001 -- a reporting extra must not cost the GPU measurement
+            line["error_vs_oracle"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:300]}
         line["cpu_baseline"] = {"value": 1.0 / t_es, "unit": "energyscapes/s", "cores": 1, "kind": "oracle",
                                 "sample": f"FP64 oracle, one process: matched filter on all 32 channels "
                                           f"({t_mf:.2f} s) + time- and frequency-domain DAS/envelope on "

@@ -35,3 +35,24 @@ def test_all_cores_oracle_baseline_runs_in_spawned_workers():
     assert procs == 2 and rate > 0
     entry = bench.all_cores_baseline(2)
     assert entry["kind"] == "oracle" and entry["cores"] >= 1 and entry["value"] > 0
+
+
+def test_error_vs_oracle_entry_aligns_sampled_rows():
+    # the bench's oracle sample rows line up with the full energyscape's rows: the oracle
+    # against itself gives zero error and the same peak; a perturbed copy shows its error
+    import numpy as np
+
+    import bench
+    import oracle
+    import synth
+    cfg = synth.single_sensor(n_samples=4096, n_dirs=20)
+    _, _, _, pick, o_td, o_fd = bench.oracle_sample(cfg, 6, seed=3)
+    full_td = oracle.energyscape(cfg["x"], cfg["chirp"], cfg["mic_xyz"], cfg["dirs"], cfg["fs"], cfg["c"])
+    full_fd = oracle.energyscape(cfg["x"], cfg["chirp"], cfg["mic_xyz"], cfg["dirs"], cfg["fs"], cfg["c"], path="fd")
+    e = bench.oracle_error_entry(pick, {"td": (o_td, full_td), "fd": (o_fd, full_fd)})
+    assert e["directions_sampled"] == 6
+    for k in ("td", "fd"):
+        assert e[k]["max_abs_err_over_peak"] < 1e-12 and e[k]["peak_index_match"]
+    bumped = full_td.copy()
+    bumped[pick[2], 7] += 1e-3 * o_td.max()
+    assert abs(bench.oracle_error_entry(pick, {"td": (o_td, bumped)})["td"]["max_abs_err_over_peak"] - 1e-3) < 1e-9
