@@ -455,7 +455,9 @@ rtis_status rtis_pdm_demodulate(const uint32_t* d_words, long long n_words, int 
  * one static device array of RTIS_NOALLOC_SCRATCH_BYTES, which every GPU
  * that loads this library holds until the process exits.  The first call on
  * a device looks up that array's device address (cudaGetSymbolAddress, with
- * that device current); make that first call before any stream capture.
+ * that device current) and keeps it for that device's context; make that
+ * first call before any stream capture.  A call after cudaDeviceReset sees a
+ * new context and looks the address up again (again a first call).
  * All calls share the array and it keeps the last call's contents (each call
  * rewrites everything it reads), so calls whose work overlaps on the GPU --
  * on different streams, or from different threads -- race and corrupt each

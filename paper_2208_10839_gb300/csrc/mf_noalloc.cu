@@ -6,6 +6,8 @@
 #include <mutex>
 #include <string>
 
+#include <cudaTypedefs.h>
+
 #include "rtis_internal.h"
 
 // Scratch shared by every call on a device: twiddles [F], chirp spectrum
@@ -19,6 +21,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_addr_mutex;
 void* g_addr[kMaxDevices] = {};
+unsigned long long g_ctx[kMaxDevices] = {};
 
 // tw[j] = exp(-2 pi i j / F), from an FP64 sincospi of the exact ratio 2j/F
 __global__ void noalloc_twiddles(float2* __restrict__ tw, int F) {
@@ -29,35 +32,75 @@ __global__ void noalloc_twiddles(float2* __restrict__ tw, int F) {
     tw[j] = make_float2(static_cast<float>(c), static_cast<float>(-s));
 }
 
-// C[k'] = 2 conj(S[k]) / F with S[k] = sum_l s[l] exp(-2 pi i k l / F), k = k_lo + k'
+// C[k'] = 2 conj(S[k]) / F with S[k] = sum_l s[l] exp(-2 pi i k l / F), k = k_lo + k':
+// one warp per bin, the lanes striding over l, FP64 sums reduced across the warp
+constexpr int kChirpWarps = 8;
 __global__ void noalloc_chirp_spectrum(const float* __restrict__ chirp, int L, const float2* __restrict__ tw,
                                        int F, int k_lo, int Kb, float2* __restrict__ C) {
-    const int kp = blockIdx.x * blockDim.x + threadIdx.x;
-    if (kp >= Kb) return;
+    const int kp = blockIdx.x * kChirpWarps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (kp >= Kb) return;  // warp-uniform
     const unsigned k = static_cast<unsigned>(k_lo + kp);
     const unsigned mask = static_cast<unsigned>(F - 1);
     double re = 0.0, im = 0.0;
-    for (int l = 0; l < L; ++l) {
+    for (int l = lane; l < L; l += 32) {
         const float2 w = tw[(k * static_cast<unsigned>(l)) & mask];
         const double s = chirp[l];
         re += s * w.x;
         im += s * w.y;
     }
-    C[kp] = make_float2(static_cast<float>(2.0 * re / F), static_cast<float>(-2.0 * im / F));
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) C[kp] = make_float2(static_cast<float>(2.0 * re / F), static_cast<float>(-2.0 * im / F));
 }
 
+// The unique id of the calling thread's current context (0 when there is none yet, or
+// when the driver cannot say).  A cudaDeviceReset ends the device's primary context;
+// the next one has a new id, and the module holding g_mf_scratch may load elsewhere.
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+        fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(fn);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current == nullptr || get_id == nullptr || get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// The device address of g_mf_scratch on the current device: looked up with
+// cudaGetSymbolAddress (that device current; a host-side lookup that allocates nothing)
+// once per device and context, then cached.  A call that finds a different context
+// than the cached one (the device was reset in between) looks the address up again.
 rtis_status scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "rtis_matched_filter_noalloc: cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail(RTIS_ERR_UNSUPPORTED, "rtis_matched_filter_noalloc: device index");
     std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (g_addr[dev] == nullptr) {
+    const unsigned long long ctx = current_context_id();
+    if (g_addr[dev] == nullptr || ctx == 0 || ctx != g_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_mf_scratch);
-        if (e != cudaSuccess || p == nullptr)
+        if (e != cudaSuccess || p == nullptr) {
+            g_addr[dev] = nullptr;
             return cuda_fail(e, "rtis_matched_filter_noalloc: cudaGetSymbolAddress of the static scratch");
+        }
         g_addr[dev] = p;
+        g_ctx[dev] = current_context_id();  // the lookup made the primary context current if it was not
     }
     *out = g_addr[dev];
     return RTIS_OK;
@@ -128,7 +171,8 @@ extern "C" rtis_status rtis_matched_filter_noalloc(const int16_t* d_in, int n_mi
     noalloc_twiddles<<<static_cast<int>((F + 255) / 256), 256, 0, st>>>(p.d_tw, p.F);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "rtis_matched_filter_noalloc: twiddle launch");
-    noalloc_chirp_spectrum<<<(Kb + 127) / 128, 128, 0, st>>>(d_chirp, chirp_len, p.d_tw, p.F, k_lo, Kb, p.d_C);
+    noalloc_chirp_spectrum<<<(Kb + kChirpWarps - 1) / kChirpWarps, 32 * kChirpWarps, 0, st>>>(
+        d_chirp, chirp_len, p.d_tw, p.F, k_lo, Kb, p.d_C);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "rtis_matched_filter_noalloc: chirp spectrum launch");
     e = launch_mf_forward(p, d_in, st);

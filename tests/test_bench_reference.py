@@ -26,7 +26,15 @@ def test_reference_arm_prints_one_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
-    assert d["config"]["workload"]
+    assert d["config"]["workload"] == bench.WORKLOAD
+    for k in ("n_mics", "n_samples", "n_dirs"):
+        assert d["config"][k] == getattr(bench, k.upper()), k
+    # ms_per_step is the measured step; value scales the sampled DAS time to all directions
+    vb = d["value_basis"]
+    assert vb["scale_factor"] == bench.N_DIRS / vb["dirs_per_step"]
+    t_full = vb["matched_filter_s_per_step"] + vb["scale_factor"] * vb["das_s_per_step"]
+    assert abs(d["value"] - 1.0 / t_full) <= 1e-9 * d["value"]
+    assert d["ms_per_step"] < 1e3 * t_full
 
 
 def test_all_cores_oracle_baseline_runs_in_spawned_workers():
