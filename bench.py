@@ -43,7 +43,7 @@ FP32_LANES_PER_SM = 128     # FP32 FMA lanes per SM (4 SMSPs x 32)
 SM_MAX_MHZ_NOMINAL = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each beamformer (ncu capture of this
 # workload, see profiles/); set to None whenever that kernel changes until it is re-captured
-TD_TRAFFIC_BYTES = 5554432
+TD_TRAFFIC_BYTES = None  # re-captured after the warp-specialised rewrite (see profiles/)
 FD_TRAFFIC_BYTES = 1774336
 # td_adjoint_kernel on the calibration workload (32 x 16384 x 2048)
 ADJ_TRAFFIC_BYTES = 20086784

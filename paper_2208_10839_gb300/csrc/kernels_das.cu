@@ -36,6 +36,12 @@ namespace {
 
 constexpr uint32_t kWaitPolls = 1u << 22;   // bounded mbarrier wait (~ seconds)
 constexpr uint32_t kStallPolls = 1u << 12;  // the injected-stall test's short bound
+// the time-domain beamformer's ring waits sleep up to kRingHintNs per poll
+// instead of spinning (a poll that spins takes issue slots from the warps
+// that have data); bounds: kRingPolls x kRingHintNs ~ 1.3 s, and the stall
+// test's kStallPolls x kRingHintNs ~ 80 ms
+constexpr uint32_t kRingHintNs = 20000;
+constexpr uint32_t kRingPolls = 1u << 16;
 
 __global__ void steering_table_kernel(const float* __restrict__ mic, const float* __restrict__ dirs,
                                       const float* __restrict__ gain, const float* __restrict__ delay_s,
@@ -185,81 +191,221 @@ __device__ __forceinline__ void td_mic_bf16(uint64_t (&acc)[kTdOutPerThread], co
     }
 }
 
+// The low-pass and subsampling of one warp's beam, straight from the lanes'
+// accumulators, for R = 10 and the 41-tap filter (half = 20): lane l holds the
+// tile samples p = 30 l + t (t < 30), and output bin il of the tile sits at
+// p = 10 il + 20 with taps h[p - 10 il], p - 10 il in [0, 40].  Each lane forms
+// the partial sums P_k = sum_t h[t - 10 k] |b[30 l + t]| of the seven bins
+// il = 3 l + k (k = -4 .. 2) its samples touch, and owns bins 3 l, 3 l + 1,
+// 3 l + 2: E(3l) = P_0 + P_-3 of lane l+1, E(3l+1) = P_1 + P_-2 of lane l+1,
+// E(3l+2) = P_2 + P_-1 of lane l+1 + P_-4 of lane l+2.  No shared memory, no
+// barrier.
+constexpr int kFastR = 10, kFastTaps = 41;
+static_assert(kTdOutPerThread == 3 * kFastR, "the register epilogue assumes 30 samples per lane");
+__device__ __forceinline__ void td_epilogue_fast(const uint64_t (&acc)[kTdOutPerThread], int lane, int n_start, int N,
+                                                 const float* __restrict__ h, float* __restrict__ Erow, int i0,
+                                                 int nb, unsigned* status) {
+    constexpr int T = kTdOutPerThread;
+    float env[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int n = n_start + lane * T + t;
+        const float2 v = ptx::unpack2(acc[t]);
+        env[t] = (n >= 0 && n < N) ? magnitude_from_norm(v.x * v.x + v.y * v.y) : 0.f;
+    }
+    float hr[kFastTaps];
+#pragma unroll
+    for (int j = 0; j < kFastTaps; ++j) hr[j] = __ldg(h + j);
+    float P[7];  // P[k + 4], k = -4 .. 2
+#pragma unroll
+    for (int k = -4; k <= 2; ++k) {
+        float a = 0.f;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int j = t - kFastR * k;
+            if (j >= 0 && j < kFastTaps) a = fmaf(hr[j], env[t], a);
+        }
+        P[k + 4] = a;
+    }
+    const float n1m3 = __shfl_down_sync(0xffffffffu, P[1], 1);  // P_-3 of lane + 1
+    const float n1m2 = __shfl_down_sync(0xffffffffu, P[2], 1);  // P_-2 of lane + 1
+    const float n1m1 = __shfl_down_sync(0xffffffffu, P[3], 1);  // P_-1 of lane + 1
+    const float n2m4 = __shfl_down_sync(0xffffffffu, P[0], 2);  // P_-4 of lane + 2
+    const float e0 = P[4] + n1m3;
+    const float e1 = P[5] + n1m2;
+    const float e2 = (P[6] + n1m1) + n2m4;
+    const int il = 3 * lane;
+    if (il < nb) Erow[i0 + il] = e0;
+    if (il + 1 < nb) Erow[i0 + il + 1] = e1;
+    if (il + 2 < nb) Erow[i0 + il + 2] = e2;
+    if ((il < nb && !isfinite(e0)) || (il + 1 < nb && !isfinite(e1)) || (il + 2 < nb && !isfinite(e2)))
+        atomicOr(status, RTIS_DEV_NONFINITE);
+}
+
+// Any R and filter length: |b| of the warp's tile samples into the warp's own
+// row of shared memory, then each lane filters bins lane, lane + 32, lane + 64
+// of each group of 96 in one pass over the taps.
+__device__ __forceinline__ void td_epilogue_generic(const uint64_t (&acc)[kTdOutPerThread], int lane, int n_start,
+                                                    const TdSensor& S, float* __restrict__ env, float* __restrict__ Erow,
+                                                    int i0, int nb, unsigned* status) {
+    constexpr int T = kTdOutPerThread;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int n = n_start + lane * T + t;
+        const float2 v = ptx::unpack2(acc[t]);
+        env[lane * T + t] = (n >= 0 && n < S.N) ? magnitude_from_norm(v.x * v.x + v.y * v.y) : 0.f;
+    }
+    __syncwarp();
+    for (int base = 0; base < nb; base += 96) {
+        const int il0 = base + lane, il1 = il0 + 32, il2 = il0 + 64;
+        const float* e0 = env + S.R * min(il0, nb - 1);
+        const float* e1 = env + S.R * min(il1, nb - 1);
+        const float* e2 = env + S.R * min(il2, nb - 1);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < S.lpf_len; ++j) {
+            const float h = __ldg(S.h + j);
+            a0 = fmaf(h, e0[j], a0);
+            a1 = fmaf(h, e1[j], a1);
+            a2 = fmaf(h, e2[j], a2);
+        }
+        if (il0 < nb) Erow[i0 + il0] = a0;
+        if (il1 < nb) Erow[i0 + il1] = a1;
+        if (il2 < nb) Erow[i0 + il2] = a2;
+        if ((il0 < nb && !isfinite(a0)) || (il1 < nb && !isfinite(a1)) || (il2 < nb && !isfinite(a2)))
+            atomicOr(status, RTIS_DEV_NONFINITE);
+    }
+    __syncwarp();  // the row is rewritten by the warp's next tile
+}
+
+// Five warpgroups, one CTA per SM: warps 0..15 beamform one direction each,
+// warp 16 is the producer and warps 17..19 only hand their registers back.
+// At launch every thread holds 96 registers (640 x 96 fit the SM); the
+// producer warpgroup then drops to kTdProducerRegs and the consumers rise to
+// kTdConsumerRegs, within the block's launch allocation
+// (512 x 112 + 128 x 24 <= 640 x 96).
 // Persistent over a flat list of tiles that may span several sensors (each
 // with its own geometry, record length and direction set).  Tile t of sensor
-// s covers 8 directions (direction group t % n_dgroups) x one range tile.
-// Stages are released without CTA barriers: after a warp finishes a stage it
-// bumps that buffer's counter, and the last of the CTA's warps to do so
-// issues the TMA refill.  Barrier phases run on across tiles.  Waits are
-// bounded; a timeout sets the status word, stops the CTA's compute, and the
-// CTA drains its copies before exit.
-template <int MS, int NS, bool BF>
-__global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
+// s covers 16 directions (direction group t % n_dgroups) x one range tile.
+// The producer  The producer walks the CTA's tiles and stages, waits until a
+// buffer's previous contents were released by all eight consumers (its
+// "empty" mbarrier), then re-arms the buffer's "full" mbarrier and issues the
+// TMA boxes (one lane per box).  The ring runs on across tile boundaries, so
+// the next tile's first stages land while the consumers are still in this
+// tile's epilogue, and nothing waits at a CTA barrier after the start.
+// Every wait is bounded: a timeout sets the status word and the CTA's abort
+// flag, the producer stops issuing, and the producer lets every copy it
+// issued land before it exits.
+template <int MS, int NS, bool BF, bool FAST>
+__global__ void __launch_bounds__(kTdThreads, 1)
     td_beamform_kernel(const __grid_constant__ TdMaps maps, const __grid_constant__ TdBatch bt) {
-    constexpr int NT = 32 * kTdDirsPerCta;
+    constexpr int NW = kTdWarps;  // consumer warps
     constexpr int T = kTdOutPerThread;
     constexpr int ES = BF ? 4 : 8;  // bytes per staged sample
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* stage = smem_raw;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + static_cast<size_t>(NS) * MS * bt.row_max * 8);
-    int* done = reinterpret_cast<int*>(bar + NS);
-    int* issued = done + NS;
-    float* hs = reinterpret_cast<float*>(issued + NS);
+    const size_t ring_bytes = static_cast<size_t>(NS) * MS * bt.row_max * 8;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + ring_bytes);
+    uint64_t* empty = full + NS;
+    int* abort_flag = reinterpret_cast<int*>(empty + NS);
+    int* issued = abort_flag + 1;  // [NS]: uses of each buffer issued so far (producer only)
+    float* env_all = reinterpret_cast<float*>(smem_raw + ring_bytes + kTdBarrierBytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int b = 0; b < NS; ++b) {
-            ptx::mbar_init(&bar[b], 1);
-            done[b] = 0;
+            ptx::mbar_init(&full[b], 1);
+            ptx::mbar_init(&empty[b], NW);
             issued[b] = 0;
         }
+        *abort_flag = 0;
         ptx::fence_mbar_init();
         ptx::fence_proxy_async();
     }
+    __syncthreads();
+    volatile int* vabort = abort_flag;
+    const uint32_t polls = bt.stall ? kStallPolls : kRingPolls;
 
-    int g0 = 0;  // stages consumed by this CTA before the current tile
-    bool timed_out = false;
-    const uint32_t polls = bt.stall ? kStallPolls : kWaitPolls;
-    bool first_tile = true;
+    if (warp >= NW) {
+        // ---------------- producer warpgroup: warp NW issues, the other three leave ----------------
+        ptx::setmaxnreg_dec<kTdProducerRegs>();
+        if (warp != NW) return;
+        int g = 0;  // stages issued (or skipped) by this CTA so far
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < bt.total_tiles && !stop; tile += gridDim.x) {
+            int si = 0;
+            while (si + 1 < bt.n_sensors && tile >= bt.s[si + 1].tile_base) ++si;
+            const TdSensor& S = bt.s[si];
+            const CUtensorMap* tmap = &maps.m[si];
+            const int local = tile - S.tile_base;
+            const int i0 = (local / S.n_dgroups) * S.bins_per_tile;
+            const int n_start = S.R * i0 - ((S.lpf_len - 1) >> 1);
+            // TMA x coordinate: x0 * ES a multiple of 16 bytes
+            const int x0 = BF ? ((n_start - S.H) & ~3) : ((n_start - S.H) & ~1);
+            const int nstages = (S.M + MS - 1) / MS;
+            const uint32_t stage_bytes = static_cast<uint32_t>(MS * S.nbox * kTdBox * ES);
+            if (lane == 0) ptx::prefetch_tmap(tmap);
+            for (int st = 0; st < nstages; ++st, ++g) {
+                const int b = g % NS;
+                const int use = g / NS;
+                const bool skip = bt.stall && g == 0;  // injected stall: withhold the CTA's first copy
+                int ok = 1;
+                if (lane == 0) {
+                    if (*vabort) {
+                        ok = 0;
+                    } else if (use > 0 && !ptx::mbar_wait_hinted(&empty[b], static_cast<uint32_t>((use - 1) & 1), polls,
+                                                                 kRingHintNs)) {
+                        ok = 0;
+                        atomicOr(bt.status, RTIS_DEV_TIMEOUT);
+                        *vabort = 1;
+                    }
+                    if (ok && !skip) {
+                        ptx::fence_proxy_async();
+                        ptx::mbar_arrive_expect_tx(&full[b], stage_bytes);
+                        issued[b] = use + 1;
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    stop = true;
+                    break;
+                }
+                if (!skip) {
+                    for (int j = lane; j < MS * S.nbox; j += 32) {
+                        const int mi = j / S.nbox;
+                        const int bx = j - mi * S.nbox;
+                        unsigned char* dst = stage + (static_cast<size_t>(b * MS + mi) * S.row + bx * kTdBox) * ES;
+                        ptx::tma_load_2d(dst, tmap, x0 + bx * kTdBox, st * MS + mi, &full[b]);
+                    }
+                }
+            }
+        }
+        // every copy this CTA issued lands before the CTA can exit
+        if (lane == 0) {
+            for (int b = 0; b < NS; ++b)
+                if (issued[b] > 0)
+                    ptx::mbar_wait_hinted(&full[b], static_cast<uint32_t>((issued[b] - 1) & 1), polls, kRingHintNs);
+        }
+        return;
+    }
+
+    // ---------------- consumers: warp = direction within the tile ----------------
+    ptx::setmaxnreg_inc<kTdConsumerRegs>();
+    int g = 0;
     for (int tile = blockIdx.x; tile < bt.total_tiles; tile += gridDim.x) {
         int si = 0;
         while (si + 1 < bt.n_sensors && tile >= bt.s[si + 1].tile_base) ++si;
         const TdSensor& S = bt.s[si];
-        const CUtensorMap* tmap = &maps.m[si];
         const int local = tile - S.tile_base;
         const int dg = local % S.n_dgroups;
-        const int d = dg * kTdDirsPerCta + warp;
+        const int d = dg * NW + warp;
         const int i0 = (local / S.n_dgroups) * S.bins_per_tile;
-        const int half = (S.lpf_len - 1) >> 1;
-        const int n_start = S.R * i0 - half;
-        // TMA x coordinate: x0 * ES a multiple of 16 bytes
+        const int n_start = S.R * i0 - ((S.lpf_len - 1) >> 1);
         const int x0 = BF ? ((n_start - S.H) & ~3) : ((n_start - S.H) & ~1);
         const int M = S.M, row = S.row;
         const int nstages = (M + MS - 1) / MS;
-        const uint32_t stage_bytes = static_cast<uint32_t>(MS * S.nbox * kTdBox * ES);
 
-        auto issue = [&](int st) {
-            const int b = (g0 + st) % NS;
-            issued[b] += 1;
-            ptx::mbar_arrive_expect_tx(&bar[b], stage_bytes);
-            for (int mi = 0; mi < MS; ++mi) {
-                unsigned char* dst = stage + static_cast<size_t>(b * MS + mi) * row * ES;
-                for (int bx = 0; bx < S.nbox; ++bx)
-                    ptx::tma_load_2d(dst + static_cast<size_t>(bx) * kTdBox * ES, tmap, x0 + bx * kTdBox,
-                                     st * MS + mi, &bar[b]);
-            }
-        };
-
-        __syncthreads();  // the previous tile's epilogue is done with the stage buffers and taps
-        if (threadIdx.x == 0) {
-            ptx::prefetch_tmap(tmap);
-            for (int st = 0; st < NS && st < nstages; ++st)
-                if (!(bt.stall && first_tile && st == 0)) issue(st);  // injected stall: withhold one copy
-        }
-        first_tile = false;
-        for (int j = threadIdx.x; j < S.lpf_len; j += NT) hs[j] = S.h[j];
-
-        // lane m of each warp holds the steering entry of mic m for this warp's direction
+        // lane m holds the steering entry of mic m for this warp's direction
         const bool dir_ok = d < S.D;
         int my_shift = 0;
         float4 my_w = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -273,17 +419,19 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
         for (int t = 0; t < T; ++t) acc[t] = 0ull;
         const int lane_base = n_start - x0 + lane * T - 1;  // smem index of a[n_start + lane*T - 1]
 
-        for (int st = 0; st < nstages; ++st) {
-            const int b = (g0 + st) % NS;
-            if (!timed_out) {
-                const uint32_t par = static_cast<uint32_t>(((g0 + st) / NS) & 1);
-                if (!ptx::mbar_wait_bounded(&bar[b], par, polls)) {
-                    timed_out = true;
-                    atomicOr(bt.status, RTIS_DEV_TIMEOUT);
-                }
+        bool failed = false;
+        for (int st = 0; st < nstages; ++st, ++g) {
+            const int b = g % NS;
+            const uint32_t par = static_cast<uint32_t>((g / NS) & 1);
+            bool ok = !*vabort && ptx::mbar_wait_hinted(&full[b], par, polls, kRingHintNs);
+            if (!__all_sync(0xffffffffu, ok)) {
+                failed = true;
+                break;
             }
-            const bool warp_timed_out = __any_sync(0xffffffffu, timed_out);
-            if (dir_ok && !warp_timed_out) {
+            // every warp runs the mic loop: a direction past the set's end has zero
+            // weights and shift, so it reads inside the staged row and sums zeros (a
+            // branch around the loop costs the compiler's scheduling of it ~15 %)
+            {
 #pragma unroll
                 for (int mi = 0; mi < MS; ++mi) {
                     const int m = st * MS + mi;
@@ -310,70 +458,26 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
                     }
                 }
             }
-            // release buffer b; the CTA's last warp to get here refills it
             __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&empty[b]);  // the producer may refill buffer b
+        }
+        if (failed) {
             if (lane == 0) {
-                __threadfence_block();
-                const int prev = atomicAdd(&done[b], 1);
-                if (prev == kTdDirsPerCta - 1) {
-                    done[b] = 0;
-                    __threadfence_block();
-                    if (st + NS < nstages && !warp_timed_out) {  // no refills once a wait has given up
-                        ptx::fence_proxy_async();
-                        issue(st + NS);
-                    }
-                }
+                if (!*vabort) atomicOr(bt.status, RTIS_DEV_TIMEOUT);
+                *vabort = 1;
             }
+            break;
         }
-        g0 += nstages;
-
-        if (__syncthreads_or(timed_out)) break;  // uniform: leave the tile loop, drain below
-
-        // epilogue: envelope of this warp's beam over the tile, then low-pass + subsample
-        float* env = reinterpret_cast<float*>(smem_raw) + warp * kTdWarpSamples;
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            const int n = n_start + lane * T + t;
-            const float2 v = unpack2(acc[t]);
-            env[lane * T + t] = (n >= 0 && n < S.N) ? magnitude_from_norm(v.x * v.x + v.y * v.y) : 0.f;
+        // every warp runs the epilogue too (branch-free around acc, as for the mic loop);
+        // a direction past the set's end stores nothing (nb = 0)
+        {
+            float* Erow = S.E + static_cast<size_t>(dir_ok ? d : 0) * S.n_out;
+            const int nb = dir_ok ? min(S.bins_per_tile, S.n_out - i0) : 0;
+            if constexpr (FAST)
+                td_epilogue_fast(acc, lane, n_start, S.N, S.h, Erow, i0, nb, bt.status);
+            else
+                td_epilogue_generic(acc, lane, n_start, S, env_all + warp * kTdWarpSamples, Erow, i0, nb, bt.status);
         }
-        __syncwarp();
-        if (dir_ok) {
-            // each lane takes bins lane, lane + 32, lane + 64 of a group of 96 in one pass over
-            // the taps (each tap loaded once for three bins); lanes past the tile's last bin
-            // compute that bin again and discard it
-            float* Erow = S.E + static_cast<size_t>(d) * S.n_out;
-            const int nb = min(S.bins_per_tile, S.n_out - i0);
-            for (int base = 0; base < nb; base += 96) {
-                const int il0 = base + lane, il1 = il0 + 32, il2 = il0 + 64;
-                const float* e0 = env + S.R * min(il0, nb - 1);
-                const float* e1 = env + S.R * min(il1, nb - 1);
-                const float* e2 = env + S.R * min(il2, nb - 1);
-                float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-#pragma unroll 4
-                for (int j = 0; j < S.lpf_len; ++j) {
-                    const float h = hs[j];
-                    a0 = fmaf(h, e0[j], a0);
-                    a1 = fmaf(h, e1[j], a1);
-                    a2 = fmaf(h, e2[j], a2);
-                }
-                if (il0 < nb) Erow[i0 + il0] = a0;
-                if (il1 < nb) Erow[i0 + il1] = a1;
-                if (il2 < nb) Erow[i0 + il2] = a2;
-                if ((il0 < nb && !isfinite(a0)) || (il1 < nb && !isfinite(a1)) || (il2 < nb && !isfinite(a2)))
-                    atomicOr(bt.status, RTIS_DEV_NONFINITE);
-            }
-        }
-    }
-
-    if (__syncthreads_or(timed_out)) {
-        // give copies still in flight a bounded chance to land, then leave
-        if (threadIdx.x == 0) {
-            for (int b = 0; b < NS; ++b)
-                if (issued[b] > 0)
-                    ptx::mbar_wait_bounded(&bar[b], static_cast<uint32_t>((issued[b] - 1) & 1), polls);
-        }
-        __syncthreads();
     }
 }
 
@@ -391,23 +495,45 @@ cudaError_t launch_steering_table(Plan& p, cudaStream_t st) {
     return e;
 }
 
-size_t td_smem_bytes(int row_max, int lpf_max) {
-    // stage ring (the same bytes for every (mics per stage, stages) variant), then
-    // barriers and counters for up to 8 stages, then the low-pass taps
-    return static_cast<size_t>(kTdStages) * kTdMicsPerStage * row_max * 8 + 8 * (8 + 4 + 4) +
-           static_cast<size_t>(lpf_max) * 4;
-}
-size_t td_smem_bytes(const Plan& p) { return td_smem_bytes(p.td_row, p.lpf_len); }
+bool td_fast_epilogue(int R, int lpf_len) { return R == kFastR && lpf_len == kFastTaps; }
 
 namespace {
-template <int MS, int NS, bool BF>
+constexpr int kTdLayouts[kTdVariants][2] = {{2, 8}, {4, 4}, {2, 10}, {4, 5}, {1, 8}};
+}  // namespace
+int td_variant_ms(int v) { return kTdLayouts[v][0]; }
+int td_variant_ns(int v) { return kTdLayouts[v][1]; }
+
+size_t td_smem_bytes(int row_max, bool fast, int variant) {
+    // stage ring, then barriers, flags and counters, then (any other low-pass) one
+    // envelope row per consumer warp
+    return static_cast<size_t>(td_variant_ms(variant)) * td_variant_ns(variant) * row_max * 8 + kTdBarrierBytes +
+           (fast ? 0 : static_cast<size_t>(kTdWarps) * kTdWarpSamples * 4);
+}
+bool td_variant_fits(int row_max, bool fast, int variant) {
+    return variant >= 0 && variant < kTdVariants && td_smem_bytes(row_max, fast, variant) <= 227 * 1024;
+}
+size_t td_smem_bytes(const Plan& p) { return td_smem_bytes(p.td_row, td_fast_epilogue(p.R, p.lpf_len), kTdVariants - 1); }
+
+namespace {
+template <int MS, int NS, bool BF, bool FAST>
 cudaError_t td_launch_t(const TdMaps& maps, const TdBatch& bt, int grid, size_t smem, cudaStream_t st) {
-    static_assert(MS * NS == kTdMicsPerStage * kTdStages, "variants share one shared-memory size");
-    cudaError_t e = cudaFuncSetAttribute(td_beamform_kernel<MS, NS, BF>,
+    static_assert(16 * NS + 4 * (NS + 1) <= kTdBarrierBytes, "barrier area");
+    cudaError_t e = cudaFuncSetAttribute(td_beamform_kernel<MS, NS, BF, FAST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    td_beamform_kernel<MS, NS, BF><<<grid, 32 * kTdDirsPerCta, smem, st>>>(maps, bt);
+    td_beamform_kernel<MS, NS, BF, FAST><<<grid, kTdThreads, smem, st>>>(maps, bt);
     return cudaGetLastError();
+}
+template <bool BF, bool FAST>
+cudaError_t td_launch_v(const TdMaps& maps, const TdBatch& bt, int variant, int grid, size_t smem, cudaStream_t st) {
+    switch (variant) {
+        case 0: return td_launch_t<2, 8, BF, FAST>(maps, bt, grid, smem, st);
+        case 1: return td_launch_t<4, 4, BF, FAST>(maps, bt, grid, smem, st);
+        case 2: return td_launch_t<2, 10, BF, FAST>(maps, bt, grid, smem, st);
+        case 3: return td_launch_t<4, 5, BF, FAST>(maps, bt, grid, smem, st);
+        case 4: return td_launch_t<1, 8, BF, FAST>(maps, bt, grid, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 }  // namespace
 
@@ -426,35 +552,29 @@ void td_fill_sensor(const Plan& p, float* d_out, int tile_base, TdSensor* s) {
     s->row = p.td_row;
     s->nbox = p.td_nbox;
     s->bins_per_tile = p.td_bins_per_tile;
-    s->n_dgroups = (p.D + kTdDirsPerCta - 1) / kTdDirsPerCta;
+    s->n_dgroups = (p.D + kTdWarps - 1) / kTdWarps;
     s->tile_base = tile_base;
 }
 
 int td_tiles(const Plan& p) {
-    return ((p.D + kTdDirsPerCta - 1) / kTdDirsPerCta) * ((p.n_out + p.td_bins_per_tile - 1) / p.td_bins_per_tile);
+    return ((p.D + kTdWarps - 1) / kTdWarps) * ((p.n_out + p.td_bins_per_tile - 1) / p.td_bins_per_tile);
 }
 
 cudaError_t launch_td_batch(const TdMaps& maps, const TdBatch& bt, int variant, int grid, cudaStream_t st) {
-    const size_t smem = td_smem_bytes(bt.row_max, bt.lpf_max);
-    if (bt.bf16) {
-        switch (variant) {
-            case 0: return td_launch_t<2, 4, true>(maps, bt, grid, smem, st);
-            case 1: return td_launch_t<4, 2, true>(maps, bt, grid, smem, st);
-            case 2: return td_launch_t<1, 8, true>(maps, bt, grid, smem, st);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    switch (variant) {
-        case 0: return td_launch_t<2, 4, false>(maps, bt, grid, smem, st);
-        case 1: return td_launch_t<4, 2, false>(maps, bt, grid, smem, st);
-        case 2: return td_launch_t<1, 8, false>(maps, bt, grid, smem, st);
-        default: return cudaErrorInvalidValue;
-    }
+    bool fast = true;
+    for (int i = 0; i < bt.n_sensors; ++i) fast = fast && td_fast_epilogue(bt.s[i].R, bt.s[i].lpf_len);
+    if (!td_variant_fits(bt.row_max, fast, variant)) return cudaErrorInvalidValue;
+    const size_t smem = td_smem_bytes(bt.row_max, fast, variant);
+    grid = std::max(1, std::min(grid, bt.total_tiles));
+    if (bt.bf16) return fast ? td_launch_v<true, true>(maps, bt, variant, grid, smem, st)
+                             : td_launch_v<true, false>(maps, bt, variant, grid, smem, st);
+    return fast ? td_launch_v<false, true>(maps, bt, variant, grid, smem, st)
+                : td_launch_v<false, false>(maps, bt, variant, grid, smem, st);
 }
 
-// Times every stage layout with one CTA per tile and with two persistent CTAs
-// per SM on the plan's own workspace (the timing does not depend on the data)
-// and keeps the fastest.
+// Times every stage layout that fits shared memory with one CTA per tile and
+// with one persistent CTA per SM on the plan's own workspace (the timing does
+// not depend on the data) and keeps the fastest.
 cudaError_t td_autotune(Plan& p, float* d_scratch_out) {
     TdMaps maps;
     maps.m[0] = p.a_bf16 ? p.tmap_a16 : p.tmap_a;
@@ -470,13 +590,16 @@ cudaError_t td_autotune(Plan& p, float* d_scratch_out) {
     int n_sm = 1, dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 1;
-    const int grids[2] = {bt.total_tiles, std::min(bt.total_tiles, 2 * n_sm)};
+    // [2v]: one CTA per tile; [2v + 1]: one persistent CTA per SM
+    const int grids[2] = {bt.total_tiles, std::min(bt.total_tiles, n_sm)};
+    const bool fast = td_fast_epilogue(p.R, p.lpf_len);
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e != cudaSuccess) return e;
     float best = 1e30f;
     for (int v = 0; v < kTdVariants && e == cudaSuccess; ++v) {
+        if (!td_variant_fits(p.td_row, fast, v)) continue;
         for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
             e = launch_td_batch(maps, bt, v, grids[gi], 0);  // warm-up
             float total = 0.f;

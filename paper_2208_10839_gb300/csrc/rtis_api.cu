@@ -455,9 +455,15 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         int n_sm = 1, dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 1;
-        if (opt.td_layout > 0) {  // forced: no autotuning (every TD layout stages the same bytes)
+        if (opt.td_layout > 0) {  // forced: no autotuning
+            if (!rtis::td_variant_fits(p.td_row, rtis::td_fast_epilogue(p.R, p.lpf_len), opt.td_layout - 1)) {
+                cudaFree(scratch);
+                rtis::free_plan_buffers(p);
+                delete plan;
+                return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: the forced td_layout does not fit shared memory");
+            }
             p.td_variant = opt.td_layout - 1;
-            p.td_grid = opt.grid_mode == 2 ? std::min(rtis::td_tiles(p), 2 * n_sm) : rtis::td_tiles(p);
+            p.td_grid = opt.grid_mode == 2 ? std::min(rtis::td_tiles(p), n_sm) : rtis::td_tiles(p);
         } else if (e == cudaSuccess) {
             e = rtis::td_autotune(p, scratch);
         }

@@ -72,12 +72,14 @@ rtis_status autotune(rtis_batch* b, const int16_t* const* d_in, float* const* d_
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return cuda_fail(cudaGetLastError(), "rtis_batch: event create");
     float best = 1e30f;
-    // grids: 1 or 2 persistent CTAs per SM, or one CTA per tile
-    const int grids[3] = {std::min(b->bt.total_tiles, b->n_sm), std::min(b->bt.total_tiles, 2 * b->n_sm),
-                          b->bt.total_tiles};
+    // grids: one persistent CTA per SM, or one CTA per tile
+    const int grids[2] = {std::min(b->bt.total_tiles, b->n_sm), b->bt.total_tiles};
+    bool fast = true;
+    for (int i = 0; i < b->bt.n_sensors; ++i) fast = fast && rtis::td_fast_epilogue(b->bt.s[i].R, b->bt.s[i].lpf_len);
     cudaError_t err = cudaSuccess;
     for (int v = 0; v < rtis::kTdVariants && err == cudaSuccess; ++v) {
-        for (int mi = 0; mi < 3 && err == cudaSuccess; ++mi) {
+        if (!rtis::td_variant_fits(b->bt.row_max, fast, v)) continue;
+        for (int mi = 0; mi < 2 && err == cudaSuccess; ++mi) {
             const int grid = grids[mi];
             err = enqueue(b, d_in, d_out, v, grid, st);  // warm-up (also sets function attributes)
             if (err != cudaSuccess) break;
@@ -111,6 +113,7 @@ rtis_status build_tables(rtis_plan* const* plans, int n, rtis::TdMaps* maps, rti
     if (!plans || n < 1 || n > rtis::kTdMaxSensors) return fail(RTIS_ERR_INVALID_ARG, "batch: need 1 <= n <= 16 plans");
     std::memset(bt, 0, sizeof(*bt));
     int tiles = 0, row_max = 0, lpf_max = 0;
+    bool fast = true;
     for (int i = 0; i < n; ++i) {
         if (!plans[i]) return fail(RTIS_ERR_INVALID_ARG, "batch: NULL plan");
         const rtis::Plan& p = plans[i]->p;
@@ -121,6 +124,7 @@ rtis_status build_tables(rtis_plan* const* plans, int n, rtis::TdMaps* maps, rti
         tiles += rtis::td_tiles(p);
         row_max = std::max(row_max, p.td_row);
         lpf_max = std::max(lpf_max, p.lpf_len);
+        fast = fast && rtis::td_fast_epilogue(p.R, p.lpf_len);
     }
     bt->n_sensors = n;
     bt->bf16 = plans[0]->p.a_bf16 ? 1 : 0;
@@ -128,7 +132,7 @@ rtis_status build_tables(rtis_plan* const* plans, int n, rtis::TdMaps* maps, rti
     bt->total_tiles = tiles;
     bt->row_max = row_max;
     bt->lpf_max = lpf_max;
-    if (rtis::td_smem_bytes(row_max, lpf_max) > 227 * 1024)
+    if (!rtis::td_variant_fits(row_max, fast, rtis::kTdVariants - 1))
         return fail(RTIS_ERR_UNSUPPORTED, "batch: staged halo too large");
     return RTIS_OK;
 }

@@ -18,10 +18,13 @@ namespace rtis {
 // ----------------------------------------------------------------------------
 constexpr int kTdOutPerThread = 30;                   // even: 16-byte pair loads, conflict-free
 constexpr int kTdWarpSamples = 32 * kTdOutPerThread;  // samples one warp beamforms
-constexpr int kTdDirsPerCta = 8;                      // one warp per direction
-constexpr int kTdMicsPerStage = 2;                    // mics per TMA stage
-constexpr int kTdStages = 4;                          // smem ring depth
+constexpr int kTdDirsPerCta = 8;                      // baseband and adjoint kernels: one warp per direction
+constexpr int kTdWarps = 16;                          // time-domain beamformer: directions (consumer warps) per CTA
 constexpr int kTdBox = 256;                           // TMA box width (8-byte elements)
+constexpr int kTdBarrierBytes = 256;                  // full/empty mbarriers, abort flag, issue counters
+constexpr int kTdThreads = 32 * (kTdWarps + 4);       // consumer warps + a producer warpgroup, one CTA per SM
+constexpr int kTdConsumerRegs = 112;                  // after setmaxnreg: 512 x 112 + 128 x 24 <= 640 x 96
+constexpr int kTdProducerRegs = 24;
 constexpr int kMaxMics = 32;                          // lanes hold per-mic steering
 
 // complex-baseband beamformer (kernels_bb.cu): the same CTA shape on a grid of
@@ -170,8 +173,12 @@ int bb_tiles(const Plan& p);
 cudaError_t bb_autotune(Plan& p, float* d_scratch_out);
 // bf16: tmap views BF16 pairs (4-byte elements) rather than complex floats
 cudaError_t launch_td_beamform(const Plan& p, const CUtensorMap& tmap, bool bf16, float* d_out, cudaStream_t st);
+// the smallest layout's shared memory (what a plan needs at least)
 size_t td_smem_bytes(const Plan& p);
-size_t td_smem_bytes(int row_max, int lpf_max);
+// fast: every sensor uses R = 10 and the 41-tap low-pass (the register epilogue)
+size_t td_smem_bytes(int row_max, bool fast, int variant);
+bool td_variant_fits(int row_max, bool fast, int variant);
+bool td_fast_epilogue(int R, int lpf_len);
 cudaError_t launch_fd_energyscape(const Plan& p, const float2* d_A, float* d_out, cudaStream_t st);
 // energyscapes of T measurements from their steered spectra Y [D][Kb][T]; out [T][D][n_out]
 cudaError_t launch_fd_energyscape_from_y(const Plan& p, const float2* d_Y, int T, float* d_out, cudaStream_t st);
@@ -179,7 +186,9 @@ size_t fdes_smem_bytes(const Plan& p);
 
 // persistent multi-sensor time-domain beamformer
 constexpr int kTdMaxSensors = 16;
-constexpr int kTdVariants = 3;  // (mics per stage, stages): (2, 4), (4, 2), (1, 8)
+constexpr int kTdVariants = 5;  // (mics per stage, stages): (2, 8), (4, 4), (2, 10), (4, 5), (1, 8)
+int td_variant_ms(int variant);  // mics per stage of a layout
+int td_variant_ns(int variant);  // its ring depth
 struct TdSensor {
     const int* shift;
     const float4* wt;

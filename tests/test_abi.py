@@ -77,7 +77,7 @@ def _args():
     (dict(precision=2), 4),               # FP16 storage is not offered
     (dict(precision=1, path=1), 4),       # BF16 storage on the frequency-domain path
     (dict(path=3), 1),                    # no such path
-    (dict(td_layout=4), 1),               # 3 time-domain layouts
+    (dict(td_layout=6), 1),               # 5 time-domain layouts
     (dict(bb_layout=7), 1),               # 6 baseband layouts
     (dict(grid_mode=3), 1),
 ])

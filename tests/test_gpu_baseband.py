@@ -172,7 +172,7 @@ def test_every_layout_and_grid_gives_the_same_energyscape(torch_cuda):
             ref[path] = p.process(x).cpu().numpy()
             assert p.sync() == 0
     for grid in ("tile", "persistent"):
-        for v in range(3):
+        for v in range(5):
             with Plan(*args, td_layout=v, grid=grid) as p:
                 assert (p.info.td_variant, p.info.td_grid > 0) == (v, True)
                 E = p.process(x).cpu().numpy()
