@@ -477,6 +477,41 @@ rtis_status rtis_matched_filter_noalloc(const int16_t* d_in, int n_mics, int n_s
                                         int chirp_len, double fs, double band_lo_hz, double band_hi_hz,
                                         float* d_a, float* d_A, void* stream);
 
+/*
+ * Kernel tracing (CUDA-event timing of the library's own launches).
+ * rtis_plan_set_tracing(plan, 1) creates RTIS_TRACE_MAX pairs of CUDA events
+ * (once; 0 destroys them).  While tracing is on, every call on the plan that
+ * launches kernels (rtis_process, rtis_process_many, rtis_matched_filter,
+ * rtis_beamform_td, rtis_beamform_fd, rtis_beamform_bb, rtis_backward, and the
+ * steering-table refresh they may trigger) starts a new list and records an
+ * event pair around each of its kernel launches on the caller's stream, in
+ * launch order.  Calls on a stream that is being captured are not traced.
+ * rtis_plan_get_trace waits for the last traced call's final event and copies
+ * up to `capacity` entries {kernel id, launch index in the call, milliseconds};
+ * *n_out is the number of entries recorded (a call with more than
+ * RTIS_TRACE_MAX launches keeps the first RTIS_TRACE_MAX).  Errors:
+ * RTIS_ERR_INVALID_ARG (NULL plan, or get_trace while tracing is off),
+ * RTIS_ERR_CUDA (event creation or timing failed).
+ */
+#define RTIS_TRACE_MAX 32
+typedef enum {
+    RTIS_KERNEL_STEERING_TABLE = 1,
+    RTIS_KERNEL_MF_FORWARD = 2,
+    RTIS_KERNEL_MF_INVERSE = 3,
+    RTIS_KERNEL_TD_BEAMFORM = 4,
+    RTIS_KERNEL_FD_GEMM = 5,           /* the per-channel |X| maxima and the tcgen05 GEMM */
+    RTIS_KERNEL_FD_ENERGYSCAPE = 6,
+    RTIS_KERNEL_BB_BEAMFORM = 7,
+    RTIS_KERNEL_ADJOINT = 8            /* the adjoint and its two reductions */
+} rtis_kernel_id;
+typedef struct rtis_trace_entry {
+    int kernel;                  /* rtis_kernel_id */
+    int index;                   /* position among the call's launches */
+    float ms;                    /* CUDA-event time of the launch */
+} rtis_trace_entry;
+rtis_status rtis_plan_set_tracing(rtis_plan* plan, int enable);
+rtis_status rtis_plan_get_trace(rtis_plan* plan, rtis_trace_entry* out, int capacity, int* n_out);
+
 const char* rtis_status_string(rtis_status s);
 const char* rtis_last_error(void);
 

@@ -67,6 +67,16 @@ class rtis_batch_info(C.Structure):
                 ("grid", C.c_int), ("tuned_ms", C.c_float)]
 
 
+class rtis_trace_entry(C.Structure):
+    _fields_ = [("kernel", C.c_int), ("index", C.c_int), ("ms", C.c_float)]
+
+
+# rtis_kernel_id (include/rtis.h): the kernels a traced call can launch
+KERNEL_NAMES = {1: "steering_table", 2: "mf_forward", 3: "mf_inverse", 4: "td_beamform", 5: "fd_gemm",
+                6: "fd_energyscape", 7: "bb_beamform", 8: "adjoint"}
+TRACE_MAX = 32
+
+
 class RtisError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         super().__init__(f"{where}: status {status} ({message})")
@@ -114,6 +124,8 @@ _PROTOS = {
     "rtis_batch_get_info": (C.c_int, [_VP, C.POINTER(rtis_batch_info)]),
     "rtis_batch_sync": (C.c_int, [_VP, C.POINTER(C.c_uint)]),
     "rtis_batch_destroy": (None, [_VP]),
+    "rtis_plan_set_tracing": (C.c_int, [_VP, C.c_int]),
+    "rtis_plan_get_trace": (C.c_int, [_VP, C.POINTER(rtis_trace_entry), C.c_int, C.POINTER(C.c_int)]),
     "rtis_status_string": (C.c_char_p, [C.c_int]),
     "rtis_last_error": (C.c_char_p, []),
 }
@@ -373,6 +385,18 @@ def rtis_plan_sync(plan) -> int:
     if st not in (RTIS_OK, RTIS_ERR_DEVICE, RTIS_ERR_TIMEOUT, RTIS_ERR_NONFINITE):
         check(st, "rtis_plan_sync")
     return bits.value  # device status bits (RTIS_DEV_*); 0 when all went well
+
+
+def rtis_plan_set_tracing(plan, enable: bool) -> None:
+    check(lib().rtis_plan_set_tracing(plan, 1 if enable else 0), "rtis_plan_set_tracing")
+
+
+def rtis_plan_get_trace(plan):
+    """The last traced call's launches: [(kernel name, milliseconds)] in launch order (waits for them)."""
+    buf = (rtis_trace_entry * TRACE_MAX)()
+    n = C.c_int(0)
+    check(lib().rtis_plan_get_trace(plan, buf, TRACE_MAX, C.byref(n)), "rtis_plan_get_trace")
+    return [(KERNEL_NAMES.get(buf[i].kernel, str(buf[i].kernel)), float(buf[i].ms)) for i in range(min(n.value, TRACE_MAX))]
 
 
 def rtis_status_string(status: int) -> str:

@@ -34,7 +34,6 @@
 namespace rtis {
 namespace {
 
-constexpr uint32_t kWaitPolls = 1u << 22;   // bounded mbarrier wait (~ seconds)
 constexpr uint32_t kStallPolls = 1u << 12;  // the injected-stall test's short bound
 // the time-domain beamformer's ring waits sleep up to kRingHintNs per poll
 // instead of spinning (a poll that spins takes issue slots from the warps

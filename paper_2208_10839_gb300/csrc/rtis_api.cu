@@ -13,6 +13,15 @@
 
 #include "rtis_internal.h"
 
+// one kernel launch (expression returning cudaError_t) bracketed by the plan's trace events
+#define RTIS_TRACED(plan, stream, kind, expr)                                   \
+    ([&]() -> cudaError_t {                                                     \
+        const int trace_slot_ = rtis::trace_begin((plan), (stream), (kind));    \
+        const cudaError_t trace_err_ = (expr);                                  \
+        rtis::trace_end((plan), (stream), trace_slot_);                         \
+        return trace_err_;                                                      \
+    }())
+
 namespace rtis {
 
 namespace {
@@ -40,7 +49,39 @@ void free_plan_buffers(Plan& p) {
 }
 
 bool aligned(const void* ptr, size_t a) { return (reinterpret_cast<uintptr_t>(ptr) % a) == 0; }
+
+void destroy_trace_events(Plan& p) {
+    for (cudaEvent_t& ev : p.trace_ev)
+        if (ev) {
+            cudaEventDestroy(ev);
+            ev = nullptr;
+        }
+    p.trace_on = false;
+    p.trace_live = false;
+    p.trace_n = 0;
+}
 }  // namespace
+
+void trace_call(Plan& p, cudaStream_t st) {
+    p.trace_live = false;
+    if (!p.trace_on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    p.trace_n = 0;
+    p.trace_live = true;
+}
+
+int trace_begin(Plan& p, cudaStream_t st, int kind) {
+    if (!p.trace_live || p.trace_n >= RTIS_TRACE_MAX) return -1;
+    const int slot = p.trace_n++;
+    p.trace_kind[slot] = kind;
+    cudaEventRecord(p.trace_ev[2 * slot], st);
+    return slot;
+}
+
+void trace_end(Plan& p, cudaStream_t st, int slot) {
+    if (slot >= 0) cudaEventRecord(p.trace_ev[2 * slot + 1], st);
+}
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -505,6 +546,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
 void rtis_plan_destroy(rtis_plan* plan) {
     if (!plan) return;
     cudaDeviceSynchronize();
+    rtis::destroy_trace_events(plan->p);
     rtis::free_plan_buffers(plan->p);
     delete plan;
 }
@@ -542,7 +584,7 @@ rtis_status rtis_plan_get_info(const rtis_plan* plan, rtis_plan_info* info) {
 
 static rtis_status ensure_table(Plan& p, cudaStream_t st) {
     if (!p.table_dirty) return RTIS_OK;
-    cudaError_t e = rtis::launch_steering_table(p, st);
+    cudaError_t e = RTIS_TRACED(p, st, RTIS_KERNEL_STEERING_TABLE, rtis::launch_steering_table(p, st));
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "steering table launch");
 }
 
@@ -554,9 +596,11 @@ rtis_status rtis_matched_filter(rtis_plan* plan, const int16_t* d_in, float* d_a
         return fail(RTIS_ERR_INVALID_ARG, "rtis_matched_filter: outputs must be 8-byte aligned");
     Plan& p = plan->p;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = rtis::launch_mf_forward(p, d_in, st);
+    rtis::trace_call(p, st);
+    cudaError_t e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_FORWARD, rtis::launch_mf_forward(p, d_in, st));
     if (e != cudaSuccess) return cuda_fail(e, "rtis_matched_filter: forward launch");
-    e = rtis::launch_mf_inverse(p, reinterpret_cast<float2*>(d_a), reinterpret_cast<float2*>(d_A), st);
+    e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_INVERSE,
+                    rtis::launch_mf_inverse(p, reinterpret_cast<float2*>(d_a), reinterpret_cast<float2*>(d_A), st));
     if (e != cudaSuccess) return cuda_fail(e, "rtis_matched_filter: inverse launch");
     return RTIS_OK;
 }
@@ -572,9 +616,11 @@ rtis_status rtis_beamform_td(rtis_plan* plan, const float* d_a, float* d_out, vo
     std::string err;
     if (!rtis::encode_tmap_2d_u64(&map, d_a, p.N, p.M, rtis::kTdBox, 1, &err))
         return fail(RTIS_ERR_CUDA, "rtis_beamform_td: " + err);
+    rtis::trace_call(p, st);
     rtis_status s = ensure_table(p, st);
     if (s != RTIS_OK) return s;
-    cudaError_t e = rtis::launch_td_beamform(p, map, false, d_out, st);  // the caller's complex-float a
+    cudaError_t e = RTIS_TRACED(p, st, RTIS_KERNEL_TD_BEAMFORM,
+                                rtis::launch_td_beamform(p, map, false, d_out, st));  // the caller's complex-float a
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_beamform_td: launch");
 }
 
@@ -587,8 +633,11 @@ rtis_status rtis_baseband_signal(rtis_plan* plan, const int16_t* d_in, float* d_
     if (p.opt.path != RTIS_PATH_BB)
         return fail(RTIS_ERR_UNSUPPORTED, "rtis_baseband_signal: the plan was not created for RTIS_PATH_BB");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = rtis::launch_mf_forward(p, d_in, st);
-    if (e == cudaSuccess) e = rtis::launch_mf_inverse_bb(p, reinterpret_cast<float2*>(d_z), p.Nb, st);
+    rtis::trace_call(p, st);
+    cudaError_t e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_FORWARD, rtis::launch_mf_forward(p, d_in, st));
+    if (e == cudaSuccess)
+        e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_INVERSE,
+                        rtis::launch_mf_inverse_bb(p, reinterpret_cast<float2*>(d_z), p.Nb, st));
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_baseband_signal: launch");
 }
 
@@ -607,9 +656,10 @@ rtis_status rtis_beamform_bb(rtis_plan* plan, const float* d_z, float* d_out, vo
     std::string err;
     if (!rtis::encode_tmap_2d_u64(&map, d_z, p.Nb, p.M, rtis::kBbBox, 1, &err))
         return fail(RTIS_ERR_CUDA, "rtis_beamform_bb: " + err);
+    rtis::trace_call(p, st);
     rtis_status s = ensure_table(p, st);
     if (s != RTIS_OK) return s;
-    cudaError_t e = rtis::launch_bb_beamform(p, map, d_out, st);
+    cudaError_t e = RTIS_TRACED(p, st, RTIS_KERNEL_BB_BEAMFORM, rtis::launch_bb_beamform(p, map, d_out, st));
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_beamform_bb: launch");
 }
 
@@ -620,22 +670,30 @@ rtis_status rtis_process(rtis_plan* plan, const int16_t* d_in, float* d_out, voi
     if (!rtis::aligned(d_out, 4)) return fail(RTIS_ERR_INVALID_ARG, "rtis_process: d_out must be 4-byte aligned");
     Plan& p = plan->p;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rtis::trace_call(p, st);
     rtis_status s = ensure_table(p, st);
     if (s != RTIS_OK) return s;
-    cudaError_t e = rtis::launch_mf_forward(p, d_in, st);
+    using rtis::launch_mf_inverse;
+    cudaError_t e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_FORWARD, rtis::launch_mf_forward(p, d_in, st));
     if (p.opt.path == RTIS_PATH_FD) {
-        if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, nullptr, p.d_A, st);
-        if (e == cudaSuccess) e = rtis::launch_fd_energyscape(p, p.d_A, d_out, st);
+        if (e == cudaSuccess) e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_INVERSE, launch_mf_inverse(p, nullptr, p.d_A, st));
+        if (e == cudaSuccess)
+            e = RTIS_TRACED(p, st, RTIS_KERNEL_FD_ENERGYSCAPE, rtis::launch_fd_energyscape(p, p.d_A, d_out, st));
     } else if (p.opt.path == RTIS_PATH_BB) {
-        if (e == cudaSuccess) e = rtis::launch_mf_inverse_bb(p, p.d_a, p.bb_stride, st);
-        if (e == cudaSuccess) e = rtis::launch_bb_beamform(p, p.tmap_zb, d_out, st);
+        if (e == cudaSuccess)
+            e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_INVERSE, rtis::launch_mf_inverse_bb(p, p.d_a, p.bb_stride, st));
+        if (e == cudaSuccess)
+            e = RTIS_TRACED(p, st, RTIS_KERNEL_BB_BEAMFORM, rtis::launch_bb_beamform(p, p.tmap_zb, d_out, st));
     } else {
         if (p.a_bf16) {
-            if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, nullptr, nullptr, st, p.d_a16);
-            if (e == cudaSuccess) e = rtis::launch_td_beamform(p, p.tmap_a16, true, d_out, st);
+            if (e == cudaSuccess)
+                e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_INVERSE, launch_mf_inverse(p, nullptr, nullptr, st, p.d_a16));
+            if (e == cudaSuccess)
+                e = RTIS_TRACED(p, st, RTIS_KERNEL_TD_BEAMFORM, rtis::launch_td_beamform(p, p.tmap_a16, true, d_out, st));
         } else {
-            if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, p.d_a, nullptr, st);
-            if (e == cudaSuccess) e = rtis::launch_td_beamform(p, p.tmap_a, false, d_out, st);
+            if (e == cudaSuccess) e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_INVERSE, launch_mf_inverse(p, p.d_a, nullptr, st));
+            if (e == cudaSuccess)
+                e = RTIS_TRACED(p, st, RTIS_KERNEL_TD_BEAMFORM, rtis::launch_td_beamform(p, p.tmap_a, false, d_out, st));
         }
     }
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_process: launch");
@@ -655,6 +713,7 @@ rtis_status rtis_process_many(rtis_plan* plan, const int16_t* d_in, int n, float
         return fail(RTIS_ERR_UNSUPPORTED, "rtis_process_many: the frequency-domain path needs F <= 32768");
     const size_t in_stride = static_cast<size_t>(p.M) * p.N, out_stride = static_cast<size_t>(p.D) * p.n_out;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rtis::trace_call(p, st);
     rtis_status s = ensure_table(p, st);
     if (s != RTIS_OK) return s;
     cudaError_t e = cudaSuccess;
@@ -669,10 +728,11 @@ rtis_status rtis_process_many(rtis_plan* plan, const int16_t* d_in, int n, float
         mb.z_stride = static_cast<size_t>(p.M) * 2 * p.P;
         mb.a_stride = in_stride;
         mb.A_tstride = 1;
-        e = rtis::launch_mf_forward(p, d_in, st, mb);
+        e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_FORWARD, rtis::launch_mf_forward(p, d_in, st, mb));
         if (e == cudaSuccess)
-            e = rtis::launch_mf_inverse(p, d_out_td ? p.d_ab : nullptr, d_out_fd ? p.d_X : nullptr, st, nullptr, n,
-                                        p.M * n, mb);
+            e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_INVERSE,
+                            rtis::launch_mf_inverse(p, d_out_td ? p.d_ab : nullptr, d_out_fd ? p.d_X : nullptr, st,
+                                                    nullptr, n, p.M * n, mb));
         const int per_sensor = rtis::td_tiles(p);
         for (int t0 = 0; d_out_td && t0 < n && e == cudaSuccess; t0 += rtis::kTdMaxSensors) {
             const int cnt = std::min(rtis::kTdMaxSensors, n - t0);
@@ -691,19 +751,22 @@ rtis_status rtis_process_many(rtis_plan* plan, const int16_t* d_in, int n, float
             bt.stall = (rtis::fault_mode() == rtis::kFaultStall) ? 1 : 0;
             // the plan's tuned grid: one CTA per tile, or its persistent CTA count
             const int grid = (p.td_grid <= 0 || p.td_grid >= per_sensor) ? bt.total_tiles : p.td_grid;
-            e = rtis::launch_td_batch(maps, bt, p.td_variant, grid, st);
+            e = RTIS_TRACED(p, st, RTIS_KERNEL_TD_BEAMFORM, rtis::launch_td_batch(maps, bt, p.td_variant, grid, st));
         }
     }
     // per measurement: matched filter -> analytic signal (time domain) and/or the
     // in-band spectra as frame t of X [Kb][M][n]; the time-domain energyscape
     for (int t = 0; (n > p.max_batch || (d_out_td && p.a_bf16)) && t < n && e == cudaSuccess; ++t) {
-        e = rtis::launch_mf_forward(p, d_in + t * in_stride, st);
+        e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_FORWARD, rtis::launch_mf_forward(p, d_in + t * in_stride, st));
         float2* a32 = (d_out_td && !p.a_bf16) ? p.d_a : nullptr;
         uint32_t* a16 = (d_out_td && p.a_bf16) ? p.d_a16 : nullptr;
         float2* Xt = d_out_fd ? p.d_X + t : nullptr;
-        if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, a32, Xt, st, a16, n, p.M * n);
+        if (e == cudaSuccess)
+            e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_INVERSE, rtis::launch_mf_inverse(p, a32, Xt, st, a16, n, p.M * n));
         if (e == cudaSuccess && d_out_td)
-            e = rtis::launch_td_beamform(p, p.a_bf16 ? p.tmap_a16 : p.tmap_a, p.a_bf16, d_out_td + t * out_stride, st);
+            e = RTIS_TRACED(p, st, RTIS_KERNEL_TD_BEAMFORM,
+                            rtis::launch_td_beamform(p, p.a_bf16 ? p.tmap_a16 : p.tmap_a, p.a_bf16,
+                                                     d_out_td + t * out_stride, st));
     }
     if (e == cudaSuccess && d_out_fd) {
         // the steering GEMM: "frequency" k' + k_lo (exact) times "delay" delta/F (the
@@ -730,8 +793,10 @@ rtis_status rtis_process_many(rtis_plan* plan, const int16_t* d_in, int n, float
             if (!rtis::fd_gemm_encode_ymap(g, p.d_Y, &ymap, &err)) return fail(RTIS_ERR_CUDA, "rtis_process_many: " + err);
             ym = &ymap;
         }
-        e = rtis::launch_fd_gemm(g, p.d_X, p.d_Y, ym, st);
-        if (e == cudaSuccess) e = rtis::launch_fd_energyscape_from_y(p, p.d_Y, n, d_out_fd, st);
+        e = RTIS_TRACED(p, st, RTIS_KERNEL_FD_GEMM, rtis::launch_fd_gemm(g, p.d_X, p.d_Y, ym, st));
+        if (e == cudaSuccess)
+            e = RTIS_TRACED(p, st, RTIS_KERNEL_FD_ENERGYSCAPE,
+                            rtis::launch_fd_energyscape_from_y(p, p.d_Y, n, d_out_fd, st));
     }
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_process_many: launch");
 }
@@ -745,9 +810,11 @@ rtis_status rtis_beamform_fd(rtis_plan* plan, const float* d_A, float* d_out, vo
     if (rtis::fdes_smem_bytes(p) > 227 * 1024)
         return fail(RTIS_ERR_UNSUPPORTED, "rtis_beamform_fd: needs F <= 32768 and the envelope in shared memory");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rtis::trace_call(p, st);
     rtis_status s = ensure_table(p, st);
     if (s != RTIS_OK) return s;
-    cudaError_t e = rtis::launch_fd_energyscape(p, reinterpret_cast<const float2*>(d_A), d_out, st);
+    cudaError_t e = RTIS_TRACED(p, st, RTIS_KERNEL_FD_ENERGYSCAPE,
+                                rtis::launch_fd_energyscape(p, reinterpret_cast<const float2*>(d_A), d_out, st));
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_beamform_fd: launch");
 }
 
@@ -903,11 +970,14 @@ rtis_status rtis_backward(rtis_plan* plan, const int16_t* d_in, const float* d_g
         return fail(RTIS_ERR_UNSUPPORTED, "rtis_backward: decimation too coarse for the beamformer tile");
     if (rtis::adj_smem_bytes(p) > 227 * 1024) return fail(RTIS_ERR_UNSUPPORTED, "rtis_backward: halo too large");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rtis::trace_call(p, st);
     rtis_status s = ensure_table(p, st);
     if (s != RTIS_OK) return s;
-    cudaError_t e = rtis::launch_mf_forward(p, d_in, st);  // recompute the matched filter
-    if (e == cudaSuccess) e = rtis::launch_mf_inverse(p, p.d_a, nullptr, st);
-    if (e == cudaSuccess) e = rtis::launch_td_adjoint(p, d_grad_out, d_grad_xyz, d_grad_gain, d_grad_delay, st);
+    cudaError_t e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_FORWARD, rtis::launch_mf_forward(p, d_in, st));  // recompute the MF
+    if (e == cudaSuccess) e = RTIS_TRACED(p, st, RTIS_KERNEL_MF_INVERSE, rtis::launch_mf_inverse(p, p.d_a, nullptr, st));
+    if (e == cudaSuccess)
+        e = RTIS_TRACED(p, st, RTIS_KERNEL_ADJOINT,
+                        rtis::launch_td_adjoint(p, d_grad_out, d_grad_xyz, d_grad_gain, d_grad_delay, st));
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_backward: launch");
 }
 
@@ -917,6 +987,48 @@ rtis_status rtis_loss_l2(rtis_plan* plan, const float* d_E, const float* d_E_ref
     if (!plan || !d_E || !d_E_ref || !d_loss) return fail(RTIS_ERR_INVALID_ARG, "rtis_loss_l2: NULL argument");
     cudaError_t e = rtis::launch_l2_loss(plan->p, d_E, d_E_ref, d_grad_out, d_loss, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? RTIS_OK : cuda_fail(e, "rtis_loss_l2: launch");
+}
+
+rtis_status rtis_plan_set_tracing(rtis_plan* plan, int enable) {
+    if (!plan) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_set_tracing: NULL plan");
+    Plan& p = plan->p;
+    if (!enable) {
+        cudaDeviceSynchronize();  // no recorded event is still pending when it is destroyed
+        rtis::destroy_trace_events(p);
+        return RTIS_OK;
+    }
+    if (p.trace_on) return RTIS_OK;
+    for (cudaEvent_t& ev : p.trace_ev) {
+        const cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) {
+            rtis::destroy_trace_events(p);
+            return cuda_fail(e, "rtis_plan_set_tracing: cudaEventCreate");
+        }
+    }
+    p.trace_on = true;
+    p.trace_n = 0;
+    return RTIS_OK;
+}
+
+rtis_status rtis_plan_get_trace(rtis_plan* plan, rtis_trace_entry* out, int capacity, int* n_out) {
+    if (!plan) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_get_trace: NULL plan");
+    Plan& p = plan->p;
+    if (!p.trace_on) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_get_trace: tracing is off");
+    if (capacity > 0 && !out) return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_get_trace: NULL output");
+    if (p.trace_n > 0) {
+        const cudaError_t e = cudaEventSynchronize(p.trace_ev[2 * p.trace_n - 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "rtis_plan_get_trace: cudaEventSynchronize");
+    }
+    for (int i = 0; i < p.trace_n && i < capacity; ++i) {
+        float ms = 0.f;
+        const cudaError_t e = cudaEventElapsedTime(&ms, p.trace_ev[2 * i], p.trace_ev[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "rtis_plan_get_trace: cudaEventElapsedTime");
+        out[i].kernel = p.trace_kind[i];
+        out[i].index = i;
+        out[i].ms = ms;
+    }
+    if (n_out) *n_out = p.trace_n;
+    return RTIS_OK;
 }
 
 rtis_status rtis_plan_sync(rtis_plan* plan, unsigned* bits_out) {

@@ -110,7 +110,21 @@ struct Plan {
     CUtensorMap tmap_a16;       // TMA view of d_a16 as [M][N] 4-byte elements (BF16 plans)
     bool a_bf16 = false;        // rtis_process / batches beamform from the BF16 copy of a
     bool table_dirty = true;
+
+    // kernel tracing (rtis_plan_set_tracing): an event pair around every launch of a
+    // traced call, in launch order; the list restarts with each traced call
+    bool trace_on = false;
+    bool trace_live = false;    // the current call records (tracing on, stream not capturing)
+    int trace_n = 0;
+    cudaEvent_t trace_ev[2 * RTIS_TRACE_MAX] = {};
+    int trace_kind[RTIS_TRACE_MAX] = {};
 };
+
+// tracing helpers: trace_call starts a traced call's list; trace_begin/trace_end
+// bracket one launch (slot -1: not recorded)
+void trace_call(Plan& p, cudaStream_t st);
+int trace_begin(Plan& p, cudaStream_t st, int kind);
+void trace_end(Plan& p, cudaStream_t st, int slot);
 
 // ----------------------------------------------------------------------------
 // frequency-domain beamforming GEMM (kernels_fd.cu)

@@ -174,6 +174,14 @@ class Plan:
         """Waits for the device; returns (and clears) the device status bits."""
         return nat.rtis_plan_sync(self.handle)
 
+    def set_tracing(self, enable=True):
+        """CUDA-event timing of the library's own launches in each later call (see trace())."""
+        nat.rtis_plan_set_tracing(self.handle, enable)
+
+    def trace(self):
+        """The last traced call's kernel launches as [(kernel name, ms)], in launch order."""
+        return nat.rtis_plan_get_trace(self.handle)
+
 
 def pdm_demodulate(words, n_mics, n_samples, decim=10, taps=None, shift=0, out=None, stream=None):
     """PDM front end: words (int32 or uint32 device tensor [n_words], bit m of word k =

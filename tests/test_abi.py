@@ -115,6 +115,8 @@ def test_null_arguments(nat):
     assert lib.rtis_matched_filter(None, None, None, None, None) == nat.RTIS_ERR_INVALID_ARG
     assert lib.rtis_beamform_td(None, None, None, None) == nat.RTIS_ERR_INVALID_ARG
     assert lib.rtis_plan_sync(None, None) == nat.RTIS_ERR_INVALID_ARG
+    assert lib.rtis_plan_set_tracing(None, 1) == nat.RTIS_ERR_INVALID_ARG
+    assert lib.rtis_plan_get_trace(None, None, 0, None) == nat.RTIS_ERR_INVALID_ARG
     lib.rtis_plan_destroy(None)
     assert nat.rtis_status_string(0) == "ok"
 
