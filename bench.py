@@ -919,6 +919,10 @@ def run_hemisphere_batched(args, rank, world, local):
     torch.cuda.synchronize()
     assert plan.sync() == 0
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # the library's own CUDA events around each of its launches in every timed step (rtis
+    # tracing, on this stream); a step's trace is read after its end event is recorded
+    plan.set_tracing(True)
+    traces = []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -928,10 +932,16 @@ def run_hemisphere_batched(args, rank, world, local):
             evs[k][0].record(stream)
             step()
             evs[k][1].record(stream)
+            traces.append(plan.trace())
         torch.cuda.synchronize()
+    plan.set_tracing(False)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     t_total = sum(step_ms) / 1e3
     assert plan.sync() == 0
+    launch_ms = {}
+    for tr in traces:
+        for name, ms in tr:
+            launch_ms.setdefault(name, []).append(ms)
 
     # breakdown, same calls split by path, and the beamformer kernels alone (per launch)
     nb = max(3, min(args.steps, 10))
@@ -1019,13 +1029,38 @@ def run_hemisphere_batched(args, rank, world, local):
     n_sm = props.multi_processor_count
     peak_tf = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     basis = f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {SM_MAX_MHZ_NOMINAL:.0f} MHz"
-    td_flops = float(N_DIRS) * N_SAMPLES * N_MICS * 4 * 2 * 2
-    ach = td_flops / (td_ms / 1e3) / 1e12
+    timing = "the library's CUDA events around this kernel's launches in every timed step (rtis tracing)"
+    # time-domain beamformer: launches of 16 measurements (the step's last one may hold fewer)
+    per_td = [min(16, B - 16 * i) for i in range((B + 15) // 16)]
+    td_flops = float(N_DIRS) * N_SAMPLES * N_MICS * 4 * 2 * 2  # per measurement
+    td_launch = launch_ms.get("td_beamform", [float("nan")])
+    td_meas_ms = sum(td_launch) / (args.steps * B)  # per measurement
+    ach = td_flops / (td_meas_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "td_beamform_kernel", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": ach / peak_tf, "traffic": TD_TRAFFIC_BYTES, "peak_basis": basis,
-                "algorithmic_flops_per_launch": td_flops, "launch_ms": td_ms,
-                "timing": "CUDA events around single-measurement rtis_beamform_td launches in a breakdown loop "
-                          "of this run (the step's batched launches over 16 measurements are slightly faster)"}
+                "algorithmic_flops_per_launch": td_flops * per_td[0], "launch_ms": statistics.mean(td_launch),
+                "measurements_per_launch": per_td, "timing": timing,
+                "single_measurement_launch_ms": td_ms,
+                "single_measurement_frac": td_flops / (td_ms / 1e3) / 1e12 / peak_tf}
+    # frequency-domain path: the steering GEMM (HBM-bound: X in, Y out) and the IFFTs from Y
+    P = plan.info.fft_len // 4
+    fdes_flops = float(N_DIRS) * (4 * 5.0 * P * np.log2(P) + 3 * 6.0 * plan.Kb + 3.0 * N_SAMPLES
+                                  + 2.0 * 41 * plan.n_out)  # per measurement
+    fdes_ms = statistics.mean(launch_ms.get("fd_energyscape", [float("nan")]))
+    gemm_ms = statistics.mean(launch_ms.get("fd_gemm", [float("nan")]))
+    gemm_bytes = float(plan.Kb) * N_MICS * B * 8 + float(plan.Kb) * N_DIRS * B * 8
+    hbm = load_peaks().get("hbm_gbs")
+    rooflines_other = {
+        "fd_energyscape_kernel": {"bound": "alu", "achieved": fdes_flops * B / (fdes_ms / 1e3) / 1e12, "peak": peak_tf,
+                                  "unit": "TFLOP/s", "frac": fdes_flops * B / (fdes_ms / 1e3) / 1e12 / peak_tf,
+                                  "launch_ms": fdes_ms, "measurements_per_launch": B,
+                                  "algorithmic_flops_per_launch": fdes_flops * B, "timing": timing},
+        "fd_gemm_kernel": {"bound": "hbm", "achieved": gemm_bytes / (gemm_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": gemm_bytes / (gemm_ms / 1e3) / 1e9 / hbm if hbm else None, "launch_ms": gemm_ms,
+                           "algorithmic_bytes_per_launch": gemm_bytes, "precision": "fp32 (3 x bf16)",
+                           "peak_source": "MEASURED_PEAKS.json hbm_gbs", "timing": timing},
+    }
+    share = {k: sum(v) / (args.steps) for k, v in launch_ms.items()}
     line = {
         "metric": METRIC, "value": value, "unit": "energyscapes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
@@ -1050,10 +1085,14 @@ def run_hemisphere_batched(args, rank, world, local):
                                "filters + GEMM + per-direction IFFTs; the two share one matched filter per "
                                "measurement in the timed step"},
         "roofline": roofline,
+        "rooflines_other": rooflines_other,
+        "kernel_ms_per_step": share,
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_es, t_mf, t_das, pick, o_td, o_fd = oracle_sample(cfg, args.cpu_dirs)
+        if not args.no_legs:
+            line["precision_and_batching"] = precision_and_batching_legs(dev, flush, cfg, pick, o_td)
         try:
             line["error_vs_oracle"] = oracle_error_entry(pick, {"td": (o_td, E_td[0] if E_td.dim() == 3 else E_td),
                                                                 "fd": (o_fd, E_fd[0] if E_fd.dim() == 3 else E_fd)})
@@ -1072,6 +1111,217 @@ def run_hemisphere_batched(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# precision and batching legs of the default bench line: each one short, each with its
+# own CUDA-event time, roofline fraction and error against the FP64 oracle
+# ---------------------------------------------------------------------------
+def _timed(fn, flush, stream, reps):
+    """CUDA-event milliseconds of fn() per rep, L2 flushed before each (outside the events)."""
+    import torch
+    out = []
+    for k in range(reps):
+        flush(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def _fp32_peak_tflops(dev):
+    import torch
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    return n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+
+
+def _rows_error(got_rows, ref_rows):
+    ref = np.asarray(ref_rows, dtype=np.float64)
+    got = np.asarray(got_rows, dtype=np.float64)
+    return {"max_abs_err_over_peak": float(np.max(np.abs(got - ref)) / ref.max()),
+            "peak_index_match": bool(np.argmax(got) == np.argmax(ref))}
+
+
+def leg_fd_gemm(dev, flush, precision, reps):
+    """The 1200-bin x 2048-dir x 32-mic x 64-frame steering GEMM in one precision."""
+    import torch
+
+    import oracle
+    import synth
+    from paper_2208_10839_gb300 import FdGemm
+    cfg = synth.gemm_frames()
+    K, M, T = cfg["X"].shape
+    D = cfg["dirs"].shape[0]
+    stream = torch.cuda.current_stream()
+    with FdGemm(cfg["mic_xyz"], cfg["dirs"], cfg["freqs"], T, precision=precision) as g:
+        X = torch.from_numpy(cfg["X"].astype(np.complex64)).to(dev)
+        Y = torch.empty((K, D, T), dtype=torch.complex64, device=dev)
+        g.run(X, Y)
+        ms = statistics.median(_timed(lambda: g.run(X, Y), flush, stream, reps))
+        picks = sorted({0, K // 4, K // 2, (3 * K) // 4, K - 1})
+        Ys = Y[picks].cpu().numpy().astype(np.complex128)
+    W = oracle.steering_matrix(cfg["freqs"][picks], cfg["mic_xyz"], cfg["dirs"], cfg["c"])
+    Yr = oracle.fd_gemm(W, cfg["X"][picks].astype(np.complex64).astype(np.complex128))
+    bytes_alg = K * M * T * 8 + K * D * T * 8
+    hbm = load_peaks().get("hbm_gbs")
+    gbs = bytes_alg / (ms / 1e3) / 1e9
+    return {"precision": precision, "launch_ms": ms, "frames_per_s": T / (ms / 1e3),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm if hbm else None,
+                         "algorithmic_bytes_per_launch": bytes_alg, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+            "tensor_tflops": 8.0 * K * D * M * T * (3 if precision == "fp32" else 1) / (ms / 1e3) / 1e12,
+            "error_vs_fp64_oracle": {"max_abs_over_max_abs": float(np.max(np.abs(Ys - Yr)) / np.max(np.abs(Yr))),
+                                     "bins_checked": picks}}
+
+
+def leg_td_storage(dev, flush, cfg, pick, o_td, precision, reps):
+    """The hemisphere measurement through rtis_process on the time-domain path with the
+    analytic signal stored in `precision` (FP32 arithmetic either way)."""
+    import torch
+
+    from paper_2208_10839_gb300 import Plan
+    stream = torch.cuda.current_stream()
+    x = torch.from_numpy(cfg["x"]).to(dev)
+    with Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"], precision=precision) as p:
+        E = p.process(x)
+        p.set_tracing(True)
+        chain, td = [], []
+        for k in range(reps):
+            chain += _timed(lambda: p.process(x, E), flush, stream, 1)
+            td += [ms for name, ms in p.trace() if name == "td_beamform"]
+        assert p.sync() == 0
+        got = E.cpu().numpy()[pick]
+    flops = float(N_DIRS) * N_SAMPLES * N_MICS * 16
+    peak = _fp32_peak_tflops(dev)
+    td_ms = statistics.median(td)
+    return {"storage": precision, "chain_ms": statistics.median(chain), "energyscapes_per_s": 1e3 / statistics.median(chain),
+            "td_beamform_ms": td_ms,
+            "roofline": {"bound": "alu", "achieved": flops / td_ms / 1e9, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / td_ms / 1e9 / peak},
+            "error_vs_fp64_oracle": dict(_rows_error(got, o_td), directions_sampled=int(len(pick)))}
+
+
+def leg_ring(dev, flush, precision, reps):
+    """8 sensors with ragged N and D in one autotuned, graph-replayed batch."""
+    import torch
+
+    import oracle
+    import synth
+    from paper_2208_10839_gb300 import Batch, Plan
+    ring = synth.ring_sensors()
+    sensors = ring["sensors"]
+    stream = torch.cuda.current_stream()
+    plans = [Plan(s["mic_xyz"], s["fs"], s["chirp"], s["dirs"], s["n_samples"], precision=precision) for s in sensors]
+    try:
+        xs = [torch.from_numpy(s["x"]).to(dev) for s in sensors]
+        outs = [torch.empty((p.D, p.n_out), dtype=torch.float32, device=dev) for p in plans]
+        with Batch(plans) as batch:
+            batch.run(xs, outs)  # autotunes, then graph replays
+            batch.run(xs, outs)
+            ms = statistics.median(_timed(lambda: batch.run(xs, outs), flush, stream, reps))
+            assert batch.sync() == 0
+            info = batch.info
+        i_big = int(np.argmax([s["n_samples"] * s["dirs"].shape[0] for s in sensors]))
+        s = sensors[i_big]
+        rows = np.arange(0, s["dirs"].shape[0], s["dirs"].shape[0] // 8)[:8]
+        got = outs[i_big].cpu().numpy()[rows]
+    finally:
+        for p in plans:
+            p.close()
+    a = oracle.matched_filter(s["x"], s["chirp"], s["fs"])
+    ref = oracle.envelope_decimate(oracle.das_td(a, oracle.steering_delays(s["mic_xyz"], s["dirs"][rows], s["fs"],
+                                                                           s["c"])), oracle.lpf_taps())
+    flops = float(sum(x["dirs"].shape[0] * x["n_samples"] for x in sensors)) * N_MICS * 16
+    peak = _fp32_peak_tflops(dev)
+    return {"storage": precision, "batch_ms": ms, "energyscapes_per_s": len(sensors) / (ms / 1e3),
+            "beamformer_ms_autotuned": info.tuned_ms, "tiles": info.total_tiles,
+            "roofline_beamformer": {"bound": "alu", "achieved": flops / info.tuned_ms / 1e9, "peak": peak,
+                                    "unit": "TFLOP/s", "frac": flops / info.tuned_ms / 1e9 / peak},
+            "error_vs_fp64_oracle": dict(_rows_error(got, ref), sensor=i_big, directions_sampled=len(rows),
+                                         n_samples=int(s["n_samples"]))}
+
+
+def leg_calibration(dev, flush, reps):
+    """One self-calibration gradient (energyscape, L2 loss, adjoint) of the perturbed array; the
+    gradient's error against the FP64 oracle's on a cotangent that lives on 16 directions."""
+    import torch
+
+    import oracle
+    import synth
+    from paper_2208_10839_gb300 import Plan
+    cfg = synth.calibration()
+    stream = torch.cuda.current_stream()
+    with Plan(cfg["mic_nominal"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"], c=cfg["c"]) as p:
+        x = torch.from_numpy(cfg["x"]).to(dev)
+        E_ref = p.process(torch.from_numpy(cfg["x_ref"]).to(dev)).clone()
+        E = torch.empty_like(E_ref)
+        G = torch.empty_like(E_ref)
+        loss = torch.empty(1, dtype=torch.float32, device=dev)
+
+        def step():
+            p.process(x, E)
+            from paper_2208_10839_gb300 import _native as nat
+            nat.rtis_loss_l2(p.handle, E, E_ref, G, loss, None)
+            p.backward(x, G)
+
+        step()
+        p.set_tracing(True)
+        tot, adj = [], []
+        for k in range(reps):
+            flush(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.process(x, E)
+            from paper_2208_10839_gb300 import _native as nat
+            nat.rtis_loss_l2(p.handle, E, E_ref, G, loss, None)
+            p.backward(x, G)
+            e1.record(stream)
+            adj += [ms for name, ms in p.trace() if name == "adjoint"]
+            torch.cuda.synchronize()
+            tot.append(e0.elapsed_time(e1))
+        # gradient accuracy: a cotangent on 16 sampled directions
+        rng = np.random.default_rng(1)
+        pick = np.sort(rng.choice(p.D, 16, replace=False))
+        Gs = np.zeros((p.D, p.n_out), dtype=np.float32)
+        Gs[pick] = rng.standard_normal((16, p.n_out)).astype(np.float32)
+        gx, gg, gd = p.backward(x, torch.from_numpy(Gs).to(dev))
+        got = [v.cpu().numpy().astype(np.float64) for v in (gx, gg, gd)]
+        assert p.sync() == 0
+    _, gx_r, gg_r, gd_r = oracle.energyscape_vjp(cfg["x"], cfg["chirp"], cfg["mic_nominal"], cfg["dirs"][pick],
+                                                 cfg["fs"], cfg["c"], Gs[pick].astype(np.float64))
+    err = {name: float(np.max(np.abs(g - r)) / np.max(np.abs(r)))
+           for name, g, r in (("xyz", got[0], gx_r), ("gain", got[1], gg_r), ("delay", got[2], gd_r))}
+    flops = float(N_DIRS) * N_SAMPLES * N_MICS * 32
+    peak = _fp32_peak_tflops(dev)
+    adj_ms = statistics.median(adj)
+    return {"step_ms": statistics.median(tot), "gradients_per_s": 1e3 / statistics.median(tot), "adjoint_ms": adj_ms,
+            "roofline_adjoint": {"bound": "alu", "achieved": flops / adj_ms / 1e9, "peak": peak, "unit": "TFLOP/s",
+                                 "frac": flops / adj_ms / 1e9 / peak},
+            "gradient_error_vs_fp64_oracle": dict(err, tolerance=2e-3, directions_in_cotangent=16,
+                                                  note="max |g - g64| / max |g64| per quantity")}
+
+
+def precision_and_batching_legs(dev, flush, cfg, pick, o_td, reps=5):
+    """The forms the default line compares with plain FP32: every leg fails on its own."""
+    out = {}
+    legs = [("fd_gemm_bf16", lambda: leg_fd_gemm(dev, flush, "bf16", reps)),
+            ("fd_gemm_fp16", lambda: leg_fd_gemm(dev, flush, "fp16", reps)),
+            ("fd_gemm_fp32", lambda: leg_fd_gemm(dev, flush, "fp32", reps)),
+            ("td_fp32_storage", lambda: leg_td_storage(dev, flush, cfg, pick, o_td, "fp32", reps)),
+            ("td_bf16_storage", lambda: leg_td_storage(dev, flush, cfg, pick, o_td, "bf16", reps)),
+            ("ring_fp32", lambda: leg_ring(dev, flush, "fp32", reps)),
+            ("ring_bf16", lambda: leg_ring(dev, flush, "bf16", reps)),
+            ("calibration", lambda: leg_calibration(dev, flush, reps))]
+    for name, fn in legs:
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as exc:  # noqa: BLE001 -- one leg must not cost the others or the main line
+            out[name] = {"unavailable": f"{type(exc).__name__}: {exc}"[:300]}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 2)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1079,6 +1329,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="default workload: skip the short precision and batching legs (GEMM in BF16/FP16/FP32, "
+                         "TD with BF16 storage, the 8-sensor ring in FP32/BF16, a calibration gradient)")
     ap.add_argument("--cpu-pool-dirs", type=int, default=16,
                     help="directions each all-cores oracle worker times (scaled to all directions)")
     ap.add_argument("--cpu-dirs", type=int, default=128, help="directions in the oracle's timed sample")

@@ -482,8 +482,9 @@ rtis_status rtis_matched_filter_noalloc(const int16_t* d_in, int n_mics, int n_s
  * rtis_plan_set_tracing(plan, 1) creates RTIS_TRACE_MAX pairs of CUDA events
  * (once; 0 destroys them).  While tracing is on, every call on the plan that
  * launches kernels (rtis_process, rtis_process_many, rtis_matched_filter,
- * rtis_beamform_td, rtis_beamform_fd, rtis_beamform_bb, rtis_backward, and the
- * steering-table refresh they may trigger) starts a new list and records an
+ * rtis_beamform_td, rtis_beamform_fd, rtis_beamform_bb, rtis_backward,
+ * rtis_set_calibration, and the steering-table refresh they may trigger) starts
+ * a new list and records an
  * event pair around each of its kernel launches on the caller's stream, in
  * launch order.  Calls on a stream that is being captured are not traced.
  * rtis_plan_get_trace waits for the last traced call's final event and copies

@@ -950,6 +950,7 @@ rtis_status rtis_set_calibration(rtis_plan* plan, const float* d_mic_xyz, const 
         e = cudaMemcpyAsync(p.d_delay, d_delay_s, p.M * sizeof(float), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "rtis_set_calibration: copy");
     p.table_dirty = true;
+    rtis::trace_call(p, st);
     return ensure_table(p, st);
 }
 
