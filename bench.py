@@ -884,6 +884,78 @@ def run_pdm(args, rank, world, local):
     plan.close()
 
 
+def run_fd_many(args, rank, world, local):
+    """The frequency-domain path alone over --batch hemisphere measurements per step
+    (rtis_process_many): batched matched filters, the steering GEMM with the measurements as
+    frames, and the IFFT/envelope/low-pass kernel reading its output.  Used for profiling."""
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2208_10839_gb300 import Plan
+    from paper_2208_10839_gb300 import build as _b
+    _b.build()
+    dev = torch.device("cuda", local)
+    B = args.batch
+    cfgs = [synth.hemisphere(seed_scene=1 + 1000 * rank + i) for i in range(B)]
+    cfg = cfgs[0]
+    plan = Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"], max_batch=B, path="fd")
+    x = torch.from_numpy(np.stack([c["x"] for c in cfgs])).to(dev)
+    E = torch.empty((B, N_DIRS, plan.n_out), dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        flush(1.0)
+        plan.process_many(x, paths=("fd",), out_fd=E)
+    torch.cuda.synchronize()
+    assert plan.sync() == 0
+    plan.set_tracing(True)
+    evs, traces = [], []
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush(float(k))
+            e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            e[0].record(stream)
+            plan.process_many(x, paths=("fd",), out_fd=E)
+            e[1].record(stream)
+            traces.append(plan.trace())
+            evs.append(e)
+        torch.cuda.synchronize()
+    plan.set_tracing(False)
+    assert plan.sync() == 0
+    t = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    if world > 1:
+        (t,) = max_over_ranks([t], dev)
+    launch = {}
+    for tr in traces:
+        for name, ms in tr:
+            launch.setdefault(name, []).append(ms)
+    P = plan.info.fft_len // 4
+    fdes_flops = float(N_DIRS) * (4 * 5.0 * P * np.log2(P) + 3 * 6.0 * plan.Kb + 3.0 * N_SAMPLES + 2.0 * 41 * plan.n_out)
+    fdes_ms = statistics.mean(launch["fd_energyscape"])
+    peak_tf = _fp32_peak_tflops(dev)
+    line = {
+        "metric": "frequency-domain energyscapes/s at 32ch x 16384 samples x 2048 dirs",
+        "value": replica_rate(args.steps * B, world, t), "unit": "energyscapes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("time-domain and frequency-domain DAS", "frequency-domain DAS"),
+                   "batch_per_step": B, "l2": "flushed between steps, outside the timed events"},
+        "kernel_ms_per_step": {k: sum(v) / args.steps for k, v in launch.items()},
+        "roofline": {"bound": "alu", "kernel": "fd_energyscape_kernel", "achieved": fdes_flops * B / fdes_ms / 1e9,
+                     "peak": peak_tf, "unit": "TFLOP/s", "frac": fdes_flops * B / fdes_ms / 1e9 / peak_tf,
+                     "launch_ms": fdes_ms, "algorithmic_flops_per_launch": fdes_flops * B,
+                     "timing": "the library's CUDA events around this kernel's launches (rtis tracing)"},
+        "gpu_launches": args.steps * 5,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def run_hemisphere_batched(args, rank, world, local):
     """B measurements per step through rtis_process_many: per measurement the matched
     filter and the time-domain energyscape, and for the whole batch the frequency-domain
@@ -1336,6 +1408,7 @@ def main():
                     help="directions each all-cores oracle worker times (scaled to all directions)")
     ap.add_argument("--cpu-dirs", type=int, default=128, help="directions in the oracle's timed sample")
     ap.add_argument("--workload", default="hemisphere", choices=["hemisphere", "fd_gemm", "ring", "calibration", "paper_design", "stream",
+                                                               "fd_many",
                                                                "baseband", "pdm"],
                     help="hemisphere: the energyscape chain (default); fd_gemm: the 1200-bin frequency-domain "
                          "beamforming GEMM (32 mics x 64 frames -> 2048 directions); ring: 8 sensors with "
@@ -1375,6 +1448,8 @@ def main():
         return run_pdm(args, rank, world, local)
     if args.workload == "stream":
         return run_stream(args, rank, world, local)
+    if args.workload == "fd_many":
+        return run_fd_many(args, rank, world, local)
     if args.batch > 1:
         return run_hemisphere_batched(args, rank, world, local)
 

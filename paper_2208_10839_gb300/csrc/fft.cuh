@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace rtis {
 namespace fft {
@@ -16,6 +17,29 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// complex a + b and a - b as one packed FP32x2 instruction each (sm_100 and later);
+// the same IEEE sums as two scalar adds
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+    uint64_t r;
+    asm("{\n\t.reg .b64 pa, pb;\n\tmov.b64 pa, {%1, %2};\n\tmov.b64 pb, {%3, %4};\n\t"
+        "add.rn.f32x2 %0, pa, pb;\n\t}"
+        : "=l"(r)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+    return o;
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    uint64_t r;
+    asm("{\n\t.reg .b64 pa, pb;\n\tmov.b64 pa, {%1, %2};\n\tmov.b64 pb, {%3, %4};\n\t"
+        "sub.rn.f32x2 %0, pa, pb;\n\t}"
+        : "=l"(r)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+    return o;
+}
 
 // cos and sin of 2*pi*e/32 for e = 0..15 (folded to constants once unrolled)
 __device__ __forceinline__ float cos32(int e) {
@@ -61,8 +85,10 @@ __device__ __forceinline__ constexpr int bitrev(int k) {
 }
 
 // In-register radix-R DFT (R = 1, 2, 4, 8, 16, 32): decimation-in-frequency
-// butterflies, then a static bit-reversal reorder.
-template <int R, bool INV>
+// butterflies, then a static bit-reversal reorder.  NZ < R: only the first NZ
+// inputs can be nonzero, and the first stage skips the sums with the zeros
+// (v[i + R/2] = 0 gives v[i] = a and v[i + R/2] = rot(a); both zero gives zeros).
+template <int R, bool INV, int NZ = R>
 __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
 #pragma unroll
     for (int len = R; len >= 2; len >>= 1) {
@@ -72,8 +98,17 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
 #pragma unroll
             for (int i = 0; i < half; ++i) {
                 const float2 a = v[s + i], b = v[s + i + half];
-                v[s + i] = make_float2(a.x + b.x, a.y + b.y);
-                v[s + i + half] = rot32<INV>(make_float2(a.x - b.x, a.y - b.y), i * (32 / len));
+                if (len == R && NZ < R && i + half >= NZ) {
+                    if (i >= NZ) {
+                        v[s + i] = make_float2(0.f, 0.f);
+                        v[s + i + half] = make_float2(0.f, 0.f);
+                    } else {
+                        v[s + i + half] = rot32<INV>(a, i * (32 / len));
+                    }
+                    continue;
+                }
+                v[s + i] = cadd(a, b);
+                v[s + i + half] = rot32<INV>(csub(a, b), i * (32 / len));
             }
         }
     }

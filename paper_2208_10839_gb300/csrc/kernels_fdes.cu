@@ -22,6 +22,8 @@
 // (w^j = hi[j >> 8] lo[j & 255]) instead of the F-point table; the radix-16
 // passes take w = e^{2 pi i x/P} from two more (32 + 16 entries, read without
 // bank conflicts) and its powers by squaring and products.
+#include <algorithm>
+
 #include "fft.cuh"
 #include "rtis_internal.h"
 
@@ -32,6 +34,8 @@ using namespace fft;
 
 constexpr int kFdesThreads = 256;
 constexpr int kFdesChunk = 16;  // slots of 256 bins per thread per anchor (tail: 8, 4, 2, 1)
+constexpr int kFoldOut = 8;     // register fold: output bins per thread (n_out <= 2048)
+constexpr int kFoldTaps = 11;   // register fold: taps per residue class (low-pass length <= 44)
 
 struct FdesArgs {
     const float2* A;      // [M][Kb] in-band matched-filter spectra (already / F)
@@ -60,13 +64,15 @@ struct FdesSmem {
 
 __host__ __device__ constexpr int fpad(int i) { return i + (i >> 5); }  // 1-in-32 bank skew
 
-__host__ __device__ inline FdesSmem fdes_layout(int P, int F, int Kb, int n_out, int lpf_len, int M) {
+// nb: entries of the steered-spectrum buffer B (Kb, or the pruned first pass's padded
+// NZ x 256 slots, zeros past Kb)
+__host__ __device__ inline FdesSmem fdes_layout(int P, int F, int nb, int n_out, int lpf_len, int M) {
     FdesSmem L;
     int o = 0;
     L.fbuf = o;
     o += (fpad(P - 1) + 1) * 8;
     L.B = o;
-    o += Kb * 8;
+    o += nb * 8;
     L.twhi = o;
     o += (F / 256) * 8;
     L.twlo = o;
@@ -125,9 +131,11 @@ __device__ __forceinline__ void fdes_gemv_chunk(const FdesArgs& a, const float2*
 
 // One inverse radix-16 Stockham pass over P points (padded layout fpad),
 // Ns = product of the earlier radices.  The last pass (Ns = P/16) writes
-// env[p] = |b(4p + q)| for p < p_need instead of the complex values.
+// env[p] = |b(4p + q)| for p < e_end (the samples n < N of this phase) and
+// zeros for e_end <= p < p_fill (the low-pass reads past the record's end),
+// instead of the complex values.
 template <int LOGP, int NS, bool LAST>
-__device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const float2* ct, int p_need) {
+__device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const float2* ct, int e_end, int p_fill) {
     constexpr int P = 1 << LOGP;
     constexpr int NB = P / 16;
     constexpr int BPT = (NB + kFdesThreads - 1) / kFdesThreads;
@@ -203,7 +211,8 @@ __device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const float
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     const int p = k + r * NS;
-                    if (p < p_need) env[p] = magnitude_from_norm(v[b][r].x * v[b][r].x + v[b][r].y * v[b][r].y);
+                    const float mag = magnitude_from_norm(v[b][r].x * v[b][r].x + v[b][r].y * v[b][r].y);
+                    if (p < p_fill) env[p] = p < e_end ? mag : 0.f;
                 }
             }
         }
@@ -214,11 +223,18 @@ __device__ __forceinline__ void fdes_pass16(float2* buf, float* env, const float
 // FROM_Y: the steered spectra come from the batched GEMM (Y[d][k'][t]); CTA b
 // handles direction b / T of measurement b % T (neighbouring measurements share
 // Y's sectors and run side by side).  Otherwise the CTA steers direction b itself.
-template <int LOGP, bool FROM_Y>
+// NZ: bins k' = t + 256 r can be nonzero only for r < NZ (the band's slots; the rest
+// of the first pass's inputs are the zero padding up to P).  FOLD: every output
+// bin of a thread (i = t + 256 m) has the same residue (R i - half) mod 4, so per
+// phase the thread's low-pass taps are one comb j0 + 4 s, held in registers, and
+// its outputs accumulate in registers across the four phases.
+template <int LOGP, bool FROM_Y, int NZ, bool FOLD>
 __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const FdesArgs a) {
     constexpr int P = 1 << LOGP;
     extern __shared__ __align__(16) unsigned char sm[];
-    const FdesSmem L = fdes_layout(P, a.F, a.Kb, a.n_out, a.lpf_len, a.M);
+    constexpr bool PADB = NZ < P / kFdesThreads;  // B holds NZ x 256 slots, zeros past Kb
+    const int nb = PADB ? NZ * kFdesThreads : a.Kb;
+    const FdesSmem L = fdes_layout(P, a.F, nb, a.n_out, a.lpf_len, a.M);
     float2* fbuf = reinterpret_cast<float2*>(sm + L.fbuf);
     float2* B = reinterpret_cast<float2*>(sm + L.B);
     float2* twhi = reinterpret_cast<float2*>(sm + L.twhi);
@@ -252,10 +268,11 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
     const SplitTwiddles tws{twhi, twlo};
 
     if constexpr (FROM_Y) {
-        for (int kp = tid; kp < Kb; kp += kFdesThreads)
-            B[kp] = __ldg(a.Y + (static_cast<size_t>(d) * Kb + kp) * a.T + t_meas);
+        for (int kp = tid; kp < nb; kp += kFdesThreads)
+            B[kp] = kp < Kb ? __ldg(a.Y + (static_cast<size_t>(d) * Kb + kp) * a.T + t_meas) : make_float2(0.f, 0.f);
         __syncthreads();
     } else {
+        for (int kp = Kb + tid; kp < nb; kp += kFdesThreads) B[kp] = make_float2(0.f, 0.f);
         // ---- steered spectrum B_d ------------------------------------------------
         // slots of 256 bins: full chunks of kFdesChunk slots, then the tail in chunks
         // of 8, 4, 2, 1 so that no thread advances the recurrence past the band
@@ -284,59 +301,108 @@ __global__ void __launch_bounds__(kFdesThreads, 2) fd_energyscape_kernel(const F
     // ---- four phase IFFTs, each folded into the low-pass outputs ------------
     constexpr int R0 = P / kFdesThreads;  // first-pass radix, 1 .. 32
     static_assert(R0 >= 1 && R0 <= 32, "P = 256 .. 8192");
+    static_assert(NZ >= 1 && NZ <= R0, "nonzero first-pass slots");
     float* env = reinterpret_cast<float*>(fbuf);  // |b(4p + q)|, written by the last pass
     const int half = (a.lpf_len - 1) >> 1;
-    const int p_need = (a.N + 3) >> 2;  // samples n = 4p + q < N
-    const unsigned fmask = static_cast<unsigned>(a.F - 1);
+    // the register fold: outputs i = tid + 256 m, m < kFoldOut; taps j0 + 4 s, s < kFoldTaps
+    float facc[kFoldOut];
+#pragma unroll
+    for (int m = 0; m < kFoldOut; ++m) facc[m] = 0.f;
+    const int res = ((a.R * tid - half) % 4 + 4) & 3;  // (R i - half) mod 4 for all of this thread's i
     for (int q = 0; q < 4; ++q) {
-        {  // first pass (radix R0, Ns = 1): bins k' = t + 256 r, pre-twiddled by w_F^{-k' q}
+        {  // first pass (radix R0, Ns = 1): bins k' = t + 256 r, pre-twiddled by e^{+2 pi i k' q / F}
+            // = e^{+2 pi i t q / F} e^{+2 pi i 256 q r / F}: a start value and a constant step per phase
             float2 v[R0];
+            float2 w = q == 0 ? make_float2(1.f, 0.f) : conjf2(tws(static_cast<int>((static_cast<unsigned>(tid) * q) & (a.F - 1))));
+            const float2 wstep = q == 0 ? make_float2(1.f, 0.f) : conjf2(tws(256 * q));
 #pragma unroll
             for (int r = 0; r < R0; ++r) {
-                const int kp = tid + r * kFdesThreads;
                 float2 g = make_float2(0.f, 0.f);
-                if (kp < Kb) {
-                    const float2 x = B[kp];
-                    g = (q == 0) ? x : cmul(x, conjf2(tws(static_cast<int>((static_cast<unsigned>(kp) * q) & fmask))));
+                if (r < NZ) {
+                    const int kp = tid + r * kFdesThreads;
+                    if (PADB || kp < Kb) g = (q == 0) ? B[kp] : cmul(B[kp], w);
+                    if (q != 0 && r + 1 < NZ) w = cmul(w, wstep);
                 }
                 v[r] = g;
             }
-            dft_reg<R0, true>(v);
+            dft_reg<R0, true, NZ>(v);
             // R0 divides 32, so t R0 + r stays in one 32-point block: fpad is linear in r
             float2* dst = fbuf + fpad(tid * R0);
 #pragma unroll
             for (int r = 0; r < R0; ++r) dst[r] = v[r];
         }
         __syncthreads();
-        fdes_pass16<LOGP, R0, false>(fbuf, env, ct, p_need);
-        fdes_pass16<LOGP, 16 * R0, true>(fbuf, env, ct, p_need);
         const int e_end = (a.N - q + 3) >> 2;  // env entries of this phase with n = 4p + q < N
-        for (int i = tid; i < a.n_out; i += kFdesThreads) {
-            const int n0 = a.R * i - half;          // n = n0 + j
-            const int j0 = ((q - n0) % 4 + 4) & 3;  // first tap with n = q (mod 4)
-            // taps j = j0 + 4 s read env[e0 + s] (n0 + j0 - q is a multiple of 4); only
-            // 0 <= n < N count, i.e. 0 <= e0 + s < e_end
-            const int e0 = (n0 + j0 - q) >> 2;
-            const int s_lo = max(0, -e0);
-            const int s_hi = min((a.lpf_len - j0 + 3) >> 2, e_end - e0);
-            float acc = 0.f;
-            for (int sk = s_lo; sk < s_hi; ++sk) acc = fmaf(hs[j0 + 4 * sk], env[e0 + sk], acc);
-            Eacc[i] += acc;
+        fdes_pass16<LOGP, R0, false>(fbuf, env, ct, e_end, 0);
+        fdes_pass16<LOGP, 16 * R0, true>(fbuf, env, ct, e_end, e_end + 4 * kFoldTaps + 4);
+        if constexpr (FOLD) {
+            // taps j = j0 + 4 s read env[(R i - half + j0 - q) / 4 + s]; entries past the record's
+            // end were written as zeros, entries before its start are skipped below
+            const int j0 = (q - res + 4) & 3;
+            float hreg[kFoldTaps];
+#pragma unroll
+            for (int s4 = 0; s4 < kFoldTaps; ++s4) {
+                const int j = j0 + 4 * s4;
+                hreg[s4] = j < a.lpf_len ? hs[j] : 0.f;
+            }
+#pragma unroll
+            for (int m = 0; m < kFoldOut; ++m) {
+                const int i = tid + m * kFdesThreads;
+                if (i < a.n_out) {
+                    const int e0 = (a.R * i - half + j0 - q) >> 2;
+                    float acc = 0.f;
+                    if (m > 0 || e0 >= 0) {  // i >= 256 starts well inside the record
+#pragma unroll
+                        for (int s4 = 0; s4 < kFoldTaps; ++s4) acc = fmaf(hreg[s4], env[e0 + s4], acc);
+                    } else {
+#pragma unroll
+                        for (int s4 = 0; s4 < kFoldTaps; ++s4)
+                            if (e0 + s4 >= 0) acc = fmaf(hreg[s4], env[e0 + s4], acc);
+                    }
+                    facc[m] += acc;
+                }
+            }
+        } else {
+            for (int i = tid; i < a.n_out; i += kFdesThreads) {
+                const int n0 = a.R * i - half;          // n = n0 + j
+                const int j0 = ((q - n0) % 4 + 4) & 3;  // first tap with n = q (mod 4)
+                // taps j = j0 + 4 s read env[e0 + s] (n0 + j0 - q is a multiple of 4); only
+                // 0 <= n < N count, i.e. 0 <= e0 + s < e_end
+                const int e0 = (n0 + j0 - q) >> 2;
+                const int s_lo = max(0, -e0);
+                const int s_hi = min((a.lpf_len - j0 + 3) >> 2, e_end - e0);
+                float acc = 0.f;
+                for (int sk = s_lo; sk < s_hi; ++sk) acc = fmaf(hs[j0 + 4 * sk], env[e0 + sk], acc);
+                Eacc[i] += acc;
+            }
         }
         __syncthreads();
     }
     float* Erow = a.E + (static_cast<size_t>(t_meas) * a.D + d) * a.n_out;
-    for (int i = tid; i < a.n_out; i += kFdesThreads) {
-        const float e = Eacc[i];
-        if (!isfinite(e)) atomicOr(a.status, RTIS_DEV_NONFINITE);
-        Erow[i] = e;
+    if constexpr (FOLD) {
+#pragma unroll
+        for (int m = 0; m < kFoldOut; ++m) {
+            const int i = tid + m * kFdesThreads;
+            if (i < a.n_out) {
+                if (!isfinite(facc[m])) atomicOr(a.status, RTIS_DEV_NONFINITE);
+                Erow[i] = facc[m];
+            }
+        }
+    } else {
+        for (int i = tid; i < a.n_out; i += kFdesThreads) {
+            const float e = Eacc[i];
+            if (!isfinite(e)) atomicOr(a.status, RTIS_DEV_NONFINITE);
+            Erow[i] = e;
+        }
     }
 }
 
-template <int LOGP, bool FROM_Y>
+template <int LOGP, bool FROM_Y, int NZ, bool FOLD>
 cudaError_t fdes_launch_t(const Plan& p, const float2* d_A, const float2* d_Y, int T, float* d_out, cudaStream_t st) {
-    const size_t sm = static_cast<size_t>(fdes_layout(1 << LOGP, p.F, p.Kb, p.n_out, p.lpf_len, p.M).bytes);
-    cudaError_t e = cudaFuncSetAttribute(fd_energyscape_kernel<LOGP, FROM_Y>,
+    constexpr int R0 = (1 << LOGP) / kFdesThreads;
+    const int nb = NZ < R0 ? NZ * kFdesThreads : p.Kb;
+    const size_t sm = static_cast<size_t>(fdes_layout(1 << LOGP, p.F, nb, p.n_out, p.lpf_len, p.M).bytes);
+    cudaError_t e = cudaFuncSetAttribute(fd_energyscape_kernel<LOGP, FROM_Y, NZ, FOLD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
     if (e != cudaSuccess) return e;
     FdesArgs a;
@@ -358,19 +424,33 @@ cudaError_t fdes_launch_t(const Plan& p, const float2* d_A, const float2* d_Y, i
     a.lpf_len = p.lpf_len;
     a.n_out = p.n_out;
     a.status = p.d_status;
-    fd_energyscape_kernel<LOGP, FROM_Y><<<p.D * (FROM_Y ? T : 1), kFdesThreads, sm, st>>>(a);
+    fd_energyscape_kernel<LOGP, FROM_Y, NZ, FOLD><<<p.D * (FROM_Y ? T : 1), kFdesThreads, sm, st>>>(a);
     return cudaGetLastError();
+}
+
+// The common case (the band fills at most R0/2 + 2 of the first pass's 256-bin slots,
+// at most 2048 output bins, a low-pass of at most 44 taps) runs the pruned first pass
+// and the register fold; anything else the general kernel.
+template <int LOGP, bool FROM_Y>
+cudaError_t fdes_launch_pick(const Plan& p, const float2* d_A, const float2* d_Y, int T, float* d_out,
+                             cudaStream_t st) {
+    constexpr int R0 = (1 << LOGP) / kFdesThreads;
+    constexpr int NZH = R0 / 2 + 2 < R0 ? R0 / 2 + 2 : R0;
+    const int nz = (p.Kb + kFdesThreads - 1) / kFdesThreads;
+    const bool fold = p.n_out <= kFoldOut * kFdesThreads && (p.lpf_len + 3) / 4 <= kFoldTaps;
+    if (nz <= NZH && fold) return fdes_launch_t<LOGP, FROM_Y, NZH, true>(p, d_A, d_Y, T, d_out, st);
+    return fdes_launch_t<LOGP, FROM_Y, R0, false>(p, d_A, d_Y, T, d_out, st);
 }
 
 template <bool FROM_Y>
 cudaError_t fdes_dispatch(const Plan& p, const float2* d_A, const float2* d_Y, int T, float* d_out, cudaStream_t st) {
     switch (p.logP) {
-        case 8: return fdes_launch_t<8, FROM_Y>(p, d_A, d_Y, T, d_out, st);
-        case 9: return fdes_launch_t<9, FROM_Y>(p, d_A, d_Y, T, d_out, st);
-        case 10: return fdes_launch_t<10, FROM_Y>(p, d_A, d_Y, T, d_out, st);
-        case 11: return fdes_launch_t<11, FROM_Y>(p, d_A, d_Y, T, d_out, st);
-        case 12: return fdes_launch_t<12, FROM_Y>(p, d_A, d_Y, T, d_out, st);
-        case 13: return fdes_launch_t<13, FROM_Y>(p, d_A, d_Y, T, d_out, st);
+        case 8: return fdes_launch_pick<8, FROM_Y>(p, d_A, d_Y, T, d_out, st);
+        case 9: return fdes_launch_pick<9, FROM_Y>(p, d_A, d_Y, T, d_out, st);
+        case 10: return fdes_launch_pick<10, FROM_Y>(p, d_A, d_Y, T, d_out, st);
+        case 11: return fdes_launch_pick<11, FROM_Y>(p, d_A, d_Y, T, d_out, st);
+        case 12: return fdes_launch_pick<12, FROM_Y>(p, d_A, d_Y, T, d_out, st);
+        case 13: return fdes_launch_pick<13, FROM_Y>(p, d_A, d_Y, T, d_out, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -379,7 +459,10 @@ cudaError_t fdes_dispatch(const Plan& p, const float2* d_A, const float2* d_Y, i
 
 size_t fdes_smem_bytes(const Plan& p) {
     if (p.logP < 8 || p.logP > 13) return ~static_cast<size_t>(0);
-    return static_cast<size_t>(fdes_layout(p.P, p.F, p.Kb, p.n_out, p.lpf_len, p.M).bytes);
+    // the larger of the two kernels' buffers (the padded one holds at most R0/2 + 2 slots)
+    const int R0 = p.P / kFdesThreads;
+    const int nb = std::max(p.Kb, std::min(R0, R0 / 2 + 2) * kFdesThreads);
+    return static_cast<size_t>(fdes_layout(p.P, p.F, nb, p.n_out, p.lpf_len, p.M).bytes);
 }
 
 cudaError_t launch_fd_energyscape(const Plan& p, const float2* d_A, float* d_out, cudaStream_t st) {
