@@ -18,6 +18,9 @@
 // table computed on the host in FP64.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <cstring>
+
 #include "fft.cuh"
 #include "rtis_internal.h"
 
@@ -28,18 +31,13 @@ using namespace fft;
 
 constexpr int kMfThreads = 512;
 
-// grid (M, 2, n): channel m, polyphase pair h (h = 0: x[4p], x[4p+1]; h = 1:
-// x[4p+2], x[4p+3]), measurement blockIdx.z (input and spectra advance by their strides)
+// One polyphase pair of one channel: h = 0 packs x[4p], x[4p+1], h = 1 packs
+// x[4p+2], x[4p+3] as a complex sequence; its P-point FFT goes to Z[(2m + h) P ...].
 template <int LOGP>
-__global__ void __launch_bounds__(kMfThreads) mf_forward_kernel(const int16_t* __restrict__ x, int N,
-                                                                float2* __restrict__ Z,
-                                                                const float2* __restrict__ tw, int F,
-                                                                size_t x_stride, size_t z_stride) {
-    extern __shared__ float2 sbuf[];
+__device__ __forceinline__ void mf_forward_body(float2* sbuf, const int16_t* __restrict__ x, int N,
+                                                float2* __restrict__ Z, const float2* __restrict__ tw, int F, int m,
+                                                int h) {
     constexpr int P = 1 << LOGP;
-    const int m = blockIdx.x, h = blockIdx.y;
-    x += blockIdx.z * x_stride;
-    Z += blockIdx.z * z_stride;
     const short4* xr = reinterpret_cast<const short4*>(x + static_cast<size_t>(m) * N);
     const int nq = N >> 2;
     const float sc = 1.0f / 32768.0f;
@@ -57,27 +55,28 @@ __global__ void __launch_bounds__(kMfThreads) mf_forward_kernel(const int16_t* _
     for (int k = threadIdx.x; k < P; k += kMfThreads) out[k] = sbuf[spad(k)];
 }
 
-// grid (M, nq): channel m, output phase q.  Rebuilds the in-band spectrum
-// A_m[k] from the two half-size spectra, optionally stores it (q == 0), then
-// inverse-transforms phase q.
+// grid (M, 2, n): channel m, polyphase pair h, measurement blockIdx.z (input and
+// spectra advance by their strides)
 template <int LOGP>
-__global__ void __launch_bounds__(kMfThreads) mf_inverse_kernel(const float2* __restrict__ Z,
-                                                                const float2* __restrict__ C,
+__global__ void __launch_bounds__(kMfThreads) mf_forward_kernel(const int16_t* __restrict__ x, int N,
+                                                                float2* __restrict__ Z,
                                                                 const float2* __restrict__ tw, int F,
-                                                                int k_lo, int Kb, int N,
-                                                                float2* __restrict__ a,
-                                                                float2* __restrict__ A_out,
-                                                                uint32_t* __restrict__ a16, int a_ms, int a_ks,
-                                                                size_t z_stride, size_t a_stride, size_t A_tstride,
-                                                                float2* __restrict__ zb, int Nb, int zb_stride,
-                                                                int k_c) {
+                                                                size_t x_stride, size_t z_stride) {
     extern __shared__ float2 sbuf[];
+    mf_forward_body<LOGP>(sbuf, x + blockIdx.z * x_stride, N, Z + blockIdx.z * z_stride, tw, F,
+                          static_cast<int>(blockIdx.x), static_cast<int>(blockIdx.y));
+}
+
+// Channel m, output phase q: rebuilds the in-band spectrum A_m[k] from the two
+// half-size spectra, optionally stores it (q == 0), then inverse-transforms phase q.
+template <int LOGP>
+__device__ __forceinline__ void mf_inverse_body(float2* sbuf, const float2* __restrict__ Z,
+                                                const float2* __restrict__ C, const float2* __restrict__ tw, int F,
+                                                int k_lo, int Kb, int N, float2* __restrict__ a,
+                                                float2* __restrict__ A_out, uint32_t* __restrict__ a16, int a_ms,
+                                                int a_ks, float2* __restrict__ zb, int Nb, int zb_stride, int k_c,
+                                                int m, int q) {
     constexpr int P = 1 << LOGP;
-    const int m = blockIdx.x, q = blockIdx.y;
-    Z += blockIdx.z * z_stride;  // measurement blockIdx.z
-    if (a) a += blockIdx.z * a_stride;
-    if (a16) a16 += blockIdx.z * a_stride;
-    if (A_out) A_out += blockIdx.z * A_tstride;
     const float2* Za = Z + static_cast<size_t>(m) * 2 * P;
     const float2* Zb = Za + P;
     for (int kp = threadIdx.x; kp < P; kp += kMfThreads) {
@@ -127,6 +126,59 @@ __global__ void __launch_bounds__(kMfThreads) mf_inverse_kernel(const float2* __
                 const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
                 a16[static_cast<size_t>(m) * N + n] = *reinterpret_cast<const uint32_t*>(&h);
             }
+        }
+    }
+}
+
+// grid (M, nq, n): channel m, output phase q, measurement blockIdx.z
+template <int LOGP>
+__global__ void __launch_bounds__(kMfThreads) mf_inverse_kernel(const float2* __restrict__ Z,
+                                                                const float2* __restrict__ C,
+                                                                const float2* __restrict__ tw, int F,
+                                                                int k_lo, int Kb, int N,
+                                                                float2* __restrict__ a,
+                                                                float2* __restrict__ A_out,
+                                                                uint32_t* __restrict__ a16, int a_ms, int a_ks,
+                                                                size_t z_stride, size_t a_stride, size_t A_tstride,
+                                                                float2* __restrict__ zb, int Nb, int zb_stride,
+                                                                int k_c) {
+    extern __shared__ float2 sbuf[];
+    mf_inverse_body<LOGP>(sbuf, Z + blockIdx.z * z_stride, C, tw, F, k_lo, Kb, N, a ? a + blockIdx.z * a_stride : a,
+                          A_out ? A_out + blockIdx.z * A_tstride : A_out, a16 ? a16 + blockIdx.z * a_stride : a16,
+                          a_ms, a_ks, zb, Nb, zb_stride, k_c, static_cast<int>(blockIdx.x),
+                          static_cast<int>(blockIdx.y));
+}
+
+// Several sensors with their own record lengths in one launch: block b runs work
+// item b of the flat list (sensor s: items item0[s] ..), each with its sensor's FFT
+// size.  The bodies are the single-sensor kernels' own, so the results are the same
+// bit for bit.  FWD: items (m, h) = (j / 2, j % 2); otherwise (m, q) = (j / 4, j % 4).
+template <bool FWD>
+__global__ void __launch_bounds__(kMfThreads) mf_ragged_kernel(const __grid_constant__ MfRagged r) {
+    extern __shared__ float2 sbuf[];
+    const int b = static_cast<int>(blockIdx.x);
+    int s = 0;
+    while (s + 1 < r.n && b >= r.s[s + 1].item0) ++s;
+    const MfRaggedSensor& S = r.s[s];
+    const int j = b - S.item0;
+    if constexpr (FWD) {
+        const int m = j >> 1, h = j & 1;
+        switch (S.logP) {
+#define RTIS_MF_FWD(L) case L: mf_forward_body<L>(sbuf, S.x, S.N, S.Z, S.tw, S.F, m, h); break;
+            RTIS_MF_FWD(6) RTIS_MF_FWD(7) RTIS_MF_FWD(8) RTIS_MF_FWD(9) RTIS_MF_FWD(10) RTIS_MF_FWD(11)
+            RTIS_MF_FWD(12) RTIS_MF_FWD(13) RTIS_MF_FWD(14)
+#undef RTIS_MF_FWD
+            default: break;
+        }
+    } else {
+        const int m = j >> 2, q = j & 3;
+        switch (S.logP) {
+#define RTIS_MF_INV(L) \
+    case L: mf_inverse_body<L>(sbuf, S.Z, S.C, S.tw, S.F, S.k_lo, S.Kb, S.N, S.a, nullptr, S.a16, S.Kb, 1, nullptr, 0, 0, 0, m, q); break;
+            RTIS_MF_INV(6) RTIS_MF_INV(7) RTIS_MF_INV(8) RTIS_MF_INV(9) RTIS_MF_INV(10) RTIS_MF_INV(11)
+            RTIS_MF_INV(12) RTIS_MF_INV(13) RTIS_MF_INV(14)
+#undef RTIS_MF_INV
+            default: break;
         }
     }
 }
@@ -188,6 +240,50 @@ cudaError_t launch_mf_inverse_bb(const Plan& p, float2* d_z, int stride, cudaStr
         case 14: return mf_inverse_bb_t<14>(p, d_z, stride, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_mf_ragged(const Plan* const* plans, int n, const int16_t* const* d_in, cudaStream_t st) {
+    if (n < 1 || n > kMfMaxSensors) return cudaErrorInvalidValue;
+    MfRagged fw, iv;
+    std::memset(&fw, 0, sizeof(fw));
+    fw.n = n;
+    int items_f = 0, items_i = 0, logp_max = 0;
+    for (int i = 0; i < n; ++i) {
+        const Plan& p = *plans[i];
+        if (p.logP < 6 || p.logP > 14) return cudaErrorInvalidValue;
+        MfRaggedSensor& S = fw.s[i];
+        S.x = d_in[i];
+        S.N = p.N;
+        S.Z = p.d_Z;
+        S.tw = p.d_tw;
+        S.F = p.F;
+        S.logP = p.logP;
+        S.C = p.d_C;
+        S.k_lo = p.k_lo;
+        S.Kb = p.Kb;
+        S.a = p.a_bf16 ? nullptr : p.d_a;
+        S.a16 = p.a_bf16 ? p.d_a16 : nullptr;
+        S.item0 = items_f;
+        items_f += 2 * p.M;
+        logp_max = std::max(logp_max, p.logP);
+    }
+    iv = fw;
+    for (int i = 0; i < n; ++i) {
+        iv.s[i].item0 = items_i;
+        items_i += 4 * plans[i]->M;
+    }
+    const size_t sm = static_cast<size_t>(spad((1 << logp_max) - 1) + 1) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(mf_ragged_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sm));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mf_ragged_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(sm));
+    if (e != cudaSuccess) return e;
+    mf_ragged_kernel<true><<<items_f, kMfThreads, sm, st>>>(fw);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mf_ragged_kernel<false><<<items_i, kMfThreads, sm, st>>>(iv);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mf_forward(const Plan& p, const int16_t* d_in, cudaStream_t st, const MfBatch& mb) {

@@ -42,18 +42,18 @@ rtis_status validate_io(const rtis_batch* b, const int16_t* const* d_in, float* 
     return RTIS_OK;
 }
 
-// matched filters of every sensor, then the one batched beamformer launch
+// every sensor's matched filter in two launches (forward FFTs, then phase IFFTs, over
+// all sensors' channels at their own sizes), then the one batched beamformer launch
 cudaError_t enqueue(rtis_batch* b, const int16_t* const* d_in, float* const* d_out, int variant, int grid,
                     cudaStream_t st) {
-    for (size_t i = 0; i < b->plans.size(); ++i) {
-        rtis::Plan& p = b->plans[i]->p;
-        cudaError_t e = rtis::launch_mf_forward(p, d_in[i], st);
-        if (e == cudaSuccess)
-            e = p.a_bf16 ? rtis::launch_mf_inverse(p, nullptr, nullptr, st, p.d_a16)
-                         : rtis::launch_mf_inverse(p, p.d_a, nullptr, st);
-        if (e != cudaSuccess) return e;
+    const rtis::Plan* ps[rtis::kMfMaxSensors];
+    const int n = static_cast<int>(b->plans.size());
+    for (int i = 0; i < n; ++i) {
+        ps[i] = &b->plans[i]->p;
         b->bt.s[i].E = d_out[i];
     }
+    cudaError_t e = rtis::launch_mf_ragged(ps, n, d_in, st);
+    if (e != cudaSuccess) return e;
     return rtis::launch_td_batch(b->maps, b->bt, variant, grid, st);
 }
 

@@ -173,6 +173,24 @@ cudaError_t launch_mf_forward(const Plan& p, const int16_t* d_in, cudaStream_t s
 cudaError_t launch_mf_inverse(const Plan& p, float2* d_a, float2* d_A, cudaStream_t st, uint32_t* d_a16 = nullptr,
                               int a_ms = -1, int a_ks = 1, const MfBatch& mb = MfBatch());
 cudaError_t launch_steering_table(Plan& p, cudaStream_t st);
+// the matched filters of several sensors (their own N, F, band) in two launches:
+// every sensor's forward FFTs, then every sensor's four phase IFFTs, into each
+// plan's own workspaces (a, or a16 for BF16 plans)
+constexpr int kMfMaxSensors = 16;
+struct MfRaggedSensor {
+    const int16_t* x;
+    float2* Z;
+    const float2* tw;
+    const float2* C;
+    float2* a;
+    uint32_t* a16;
+    int N, F, logP, k_lo, Kb, item0;
+};
+struct MfRagged {
+    MfRaggedSensor s[kMfMaxSensors];
+    int n;
+};
+cudaError_t launch_mf_ragged(const Plan* const* plans, int n, const int16_t* const* d_in, cudaStream_t st);
 // z_m[j] = a_m[4j] exp(-2 pi i k_c 4j / F), j < Nb, into d_z rows `stride` elements apart
 // (phase-0 inverse only; the half spectra come from launch_mf_forward)
 cudaError_t launch_mf_inverse_bb(const Plan& p, float2* d_z, int stride, cudaStream_t st);
