@@ -43,8 +43,8 @@ FP32_LANES_PER_SM = 128     # FP32 FMA lanes per SM (4 SMSPs x 32)
 SM_MAX_MHZ_NOMINAL = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each beamformer (ncu capture of this
 # workload, see profiles/); set to None whenever that kernel changes until it is re-captured
-TD_TRAFFIC_BYTES = None  # re-captured after the warp-specialised rewrite (see profiles/)
-FD_TRAFFIC_BYTES = 1774336
+TD_TRAFFIC_BYTES = 5552896
+FD_TRAFFIC_BYTES = None  # the per-direction FD kernel changed since its capture
 # td_adjoint_kernel on the calibration workload (32 x 16384 x 2048)
 ADJ_TRAFFIC_BYTES = 20086784
 # fd_gemm_kernel<BF16> captured at 400 bins (DRAM read + write), per bin; X and Y both grow with the bins
@@ -1369,7 +1369,7 @@ def leg_calibration(dev, flush, reps):
     return {"step_ms": statistics.median(tot), "gradients_per_s": 1e3 / statistics.median(tot), "adjoint_ms": adj_ms,
             "roofline_adjoint": {"bound": "alu", "achieved": flops / adj_ms / 1e9, "peak": peak, "unit": "TFLOP/s",
                                  "frac": flops / adj_ms / 1e9 / peak},
-            "gradient_error_vs_fp64_oracle": dict(err, tolerance=2e-3, directions_in_cotangent=16,
+            "gradient_error_vs_fp64_oracle": dict(err, tolerance=1e-6, directions_in_cotangent=16,
                                                   note="max |g - g64| / max |g64| per quantity")}
 
 
