@@ -10,7 +10,7 @@
 //   dL/d delta_dm = g_m sum_n Re(conj(G_b) I'),   dL/d g_m = sum_{d,n} Re(conj(G_b) I)
 //   dL/d Delta_m = fs sum_d dL/d delta_dm,        dL/d p_m = -(fs/c) sum_d dL/d delta_dm u_d
 //
-// Nothing per direction is stored between passes: each tile (8 directions x
+// Nothing per direction is stored between passes: each tile (16 directions x
 // 960 samples, the forward tiling) recomputes its beams from the staged
 // channel rows, turns them into G_b in registers, then streams the rows a
 // second time and forms, per mic, the four tap correlations
@@ -28,9 +28,10 @@
 namespace rtis {
 namespace {
 
-constexpr uint32_t kAdjPolls = 1u << 22;
-constexpr int kAdjMS = 2, kAdjNS = 4;  // mics per stage, ring depth (the forward's default layout)
-static_assert(kAdjMS == 2, "the pass-B reduction pairs the two mics of a stage");
+// ring waits sleep up to kAdjHintNs per poll; kAdjPolls x kAdjHintNs ~ 1.3 s bounds a wait
+constexpr uint32_t kAdjHintNs = 20000;
+constexpr uint32_t kAdjPolls = 1u << 16;
+constexpr int kAdjMS = 4, kAdjNS = 4;  // mics per stage, ring depth
 
 struct AdjArgs {
     const int* shift;
@@ -99,102 +100,181 @@ __device__ __forceinline__ float4 adj_corr_mic(const uint64_t (&gb)[kTdOutPerThr
     return make_float4(r[0], r[1], r[2], r[3]);
 }
 
-__global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
+// Pass-B reduction of one pair of mics (m0, m0 + 1): the (value, slope) sums of both,
+// reduce-scattered over the warp (after the xor-16 and xor-8 exchanges lane bits (4, 3)
+// select (mic, value/slope); then a plain sum); lanes m0 and m0 + 1 receive their mic's
+// totals.
+__device__ __forceinline__ void adj_pair_reduce(const float (&red)[2][2], int lane, int m0, float& sum_g,
+                                                float& sum_d) {
+    const bool b16 = lane & 16, b8 = lane & 8;
+    float k0 = b16 ? red[1][0] : red[0][0], k1 = b16 ? red[1][1] : red[0][1];
+    const float s0 = b16 ? red[0][0] : red[1][0], s1 = b16 ? red[0][1] : red[1][1];
+    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+    float k = b8 ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, b8 ? k0 : k1, 8);
+    k += __shfl_xor_sync(0xffffffffu, k, 4);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    const int src = (lane == m0 + 1) ? 16 : 0;
+    const float tg = __shfl_sync(0xffffffffu, k, src), td = __shfl_sync(0xffffffffu, k, src + 8);
+    if (lane == m0 || lane == m0 + 1) {
+        sum_g = tg;
+        sum_d = td;
+    }
+}
+
+// The forward beamformer's shape: one persistent CTA per SM, 16 direction warps and a
+// producer warpgroup (warp 16 issues the TMA boxes, warps 17..19 hand their registers
+// back through setmaxnreg), full/empty mbarrier ring running across tiles.  A tile is
+// 16 directions x one range tile; its stages are the mic groups twice over (pass A
+// recomputes the beams, pass B correlates G_b with the same rows).  Every direction
+// warp runs every loop (a direction past the set's end has zero weights and cotangent)
+// and writes its partials only for a real direction.
+template <int MS, int NS>
+__global__ void __launch_bounds__(kTdThreads, 1)
     td_adjoint_kernel(const __grid_constant__ CUtensorMap tmap, const AdjArgs args) {
-    constexpr int NT = 32 * kTdDirsPerCta;
+    constexpr int NW = kTdWarps;
     constexpr int T = kTdOutPerThread;
-    constexpr int MS = kAdjMS, NS = kAdjNS;
+    static_assert(MS % 2 == 0, "pass B reduces the mics of a stage in pairs");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int row = args.row;
     float2* stage = reinterpret_cast<float2*>(smem_raw);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + static_cast<size_t>(NS) * MS * row * 8);
-    int* done = reinterpret_cast<int*>(bar + NS);
-    int* issued = done + NS;
-    float* hs = reinterpret_cast<float*>(issued + NS);
-    float* gseg = hs + ((args.lpf_len + 3) & ~3);  // [8 warps][seg]
+    const size_t ring_bytes = static_cast<size_t>(NS) * MS * row * 8;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + ring_bytes);
+    uint64_t* empty = full + NS;
+    int* abort_flag = reinterpret_cast<int*>(empty + NS);
+    int* issued = abort_flag + 1;  // [NS], producer only
+    float* hs = reinterpret_cast<float*>(smem_raw + ring_bytes + kTdBarrierBytes);
+    float* gseg = hs + ((args.lpf_len + 3) & ~3);  // [16 warps][seg]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int d = blockIdx.x * kTdDirsPerCta + warp;
-    const int nt = blockIdx.y;
-    const int i0 = nt * args.bins_per_tile;
-    const int half = (args.lpf_len - 1) >> 1;
-    const int n_start = args.R * i0 - half;
-    const int x0 = (n_start - args.H) & ~1;
-    const int M = args.M;
-    const int ngroups = (M + MS - 1) / MS;
-    const int nstages = 2 * ngroups;  // pass A then pass B over the same rows
-    const uint32_t stage_bytes = static_cast<uint32_t>(MS * args.nbox * kTdBox * 8);
-    // samples this tile owns: those of its output bins (the last tile: up to N)
-    const int own_lo = args.R * i0;
-    const bool last_tile = (i0 + args.bins_per_tile >= args.n_out);
-    const int own_hi = last_tile ? args.N : args.R * (i0 + args.bins_per_tile);
-
-    auto issue = [&](int st) {
-        const int b = st % NS;
-        const int grp = st % ngroups;
-        issued[b] += 1;
-        ptx::mbar_arrive_expect_tx(&bar[b], stage_bytes);
-        for (int mi = 0; mi < MS; ++mi) {
-            float2* dst = stage + static_cast<size_t>(b * MS + mi) * row;
-            for (int bx = 0; bx < args.nbox; ++bx)
-                ptx::tma_load_2d(dst + bx * kTdBox, &tmap, x0 + bx * kTdBox, grp * MS + mi, &bar[b]);
-        }
-    };
-
     if (threadIdx.x == 0) {
-        ptx::prefetch_tmap(&tmap);
         for (int b = 0; b < NS; ++b) {
-            ptx::mbar_init(&bar[b], 1);
-            done[b] = 0;
+            ptx::mbar_init(&full[b], 1);
+            ptx::mbar_init(&empty[b], NW);
             issued[b] = 0;
         }
+        *abort_flag = 0;
         ptx::fence_mbar_init();
         ptx::fence_proxy_async();
     }
-    for (int j = threadIdx.x; j < args.lpf_len; j += NT) hs[j] = args.h[j];
+    for (int j = threadIdx.x; j < args.lpf_len; j += kTdThreads) hs[j] = args.h[j];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < NS && st < nstages; ++st) issue(st);
-    }
+    volatile int* vabort = abort_flag;
+    const int half = (args.lpf_len - 1) >> 1;
+    const int M = args.M;
+    const int ngroups = (M + MS - 1) / MS;
+    const int nstages = 2 * ngroups;  // pass A then pass B over the same rows
+    const int n_dgroups = (args.D + NW - 1) / NW;
+    const int total = n_dgroups * ((args.n_out + args.bins_per_tile - 1) / args.bins_per_tile);
 
-    const bool dir_ok = d < args.D;
-    int my_shift = 0;
-    float4 my_w = make_float4(0.f, 0.f, 0.f, 0.f), my_wd = my_w;
-    float my_g = 0.f;
-    if (dir_ok && lane < M) {
-        const size_t e = static_cast<size_t>(d) * M + lane;
-        my_shift = __ldg(args.shift + e);
-        my_w = __ldg(args.wraw + e);
-        my_wd = __ldg(args.wder + e);
-        my_g = __ldg(args.gain + lane);
-    }
-    // cotangent segment of this warp's direction, bins [iseg0, iseg0 + seg)
-    const int reach = (half + args.R - 1) / args.R + 1;
-    const int iseg0 = i0 - reach;
-    float* gs = gseg + warp * args.seg;
-    for (int k = lane; k < args.seg; k += 32) {
-        const int i = iseg0 + k;
-        gs[k] = (dir_ok && i >= 0 && i < args.n_out) ? __ldg(args.G + static_cast<size_t>(d) * args.n_out + i) : 0.f;
-    }
-
-    uint64_t acc[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) acc[t] = 0ull;
-    const int lane_base = n_start - x0 + lane * T - 1;
-    float sum_d = 0.f, sum_g = 0.f;  // lane m keeps mic m's totals
-    bool timed_out = false;
-
-    for (int st = 0; st < nstages; ++st) {
-        const int b = st % NS;
-        if (!timed_out) {
-            if (!ptx::mbar_wait_bounded(&bar[b], static_cast<uint32_t>((st / NS) & 1), kAdjPolls)) {
-                timed_out = true;
-                atomicOr(args.status, RTIS_DEV_TIMEOUT);
+    if (warp >= NW) {
+        // ---------------- producer ----------------
+        ptx::setmaxnreg_dec<kTdProducerRegs>();
+        if (warp != NW) return;
+        const uint32_t stage_bytes = static_cast<uint32_t>(MS * args.nbox * kTdBox * 8);
+        if (lane == 0) ptx::prefetch_tmap(&tmap);
+        int g = 0;
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < total && !stop; tile += gridDim.x) {
+            const int i0 = (tile / n_dgroups) * args.bins_per_tile;
+            const int x0 = (args.R * i0 - half - args.H) & ~1;
+            for (int st = 0; st < nstages; ++st, ++g) {
+                const int b = g % NS;
+                const int use = g / NS;
+                int ok = 1;
+                if (lane == 0) {
+                    if (*vabort) {
+                        ok = 0;
+                    } else if (use > 0 && !ptx::mbar_wait_hinted(&empty[b], static_cast<uint32_t>((use - 1) & 1),
+                                                                 kAdjPolls, kAdjHintNs)) {
+                        ok = 0;
+                        atomicOr(args.status, RTIS_DEV_TIMEOUT);
+                        *vabort = 1;
+                    }
+                    if (ok) {
+                        ptx::fence_proxy_async();
+                        ptx::mbar_arrive_expect_tx(&full[b], stage_bytes);
+                        issued[b] = use + 1;
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    stop = true;
+                    break;
+                }
+                const int grp = st % ngroups;
+                for (int j = lane; j < MS * args.nbox; j += 32) {
+                    const int mi = j / args.nbox;
+                    const int bx = j - mi * args.nbox;
+                    ptx::tma_load_2d(stage + static_cast<size_t>(b * MS + mi) * row + bx * kTdBox, &tmap,
+                                     x0 + bx * kTdBox, grp * MS + mi, &full[b]);
+                }
             }
         }
-        const bool pass_b = st >= ngroups;
-        const int grp = st % ngroups;
-        if (dir_ok && !__any_sync(0xffffffffu, timed_out)) {
+        if (lane == 0) {
+            for (int b = 0; b < NS; ++b)
+                if (issued[b] > 0)
+                    ptx::mbar_wait_hinted(&full[b], static_cast<uint32_t>((issued[b] - 1) & 1), kAdjPolls, kAdjHintNs);
+        }
+        return;
+    }
+
+    // ---------------- direction warps ----------------
+    ptx::setmaxnreg_inc<kTdConsumerRegs>();
+    const int reach = (half + args.R - 1) / args.R + 1;
+    float* gs = gseg + warp * args.seg;
+    int g = 0;
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int dg = tile % n_dgroups;
+        const int nt = tile / n_dgroups;
+        const int d = dg * NW + warp;
+        const int i0 = nt * args.bins_per_tile;
+        const int n_start = args.R * i0 - half;
+        const int x0 = (n_start - args.H) & ~1;
+        // samples this tile owns: those of its output bins (the last tile: up to N)
+        const int own_lo = args.R * i0;
+        const bool last_tile = (i0 + args.bins_per_tile >= args.n_out);
+        const int own_hi = last_tile ? args.N : args.R * (i0 + args.bins_per_tile);
+
+        const bool dir_ok = d < args.D;
+        int my_shift = 0;
+        float4 my_w = make_float4(0.f, 0.f, 0.f, 0.f), my_wd = my_w;
+        float my_g = 0.f;
+        if (dir_ok && lane < M) {
+            const size_t e = static_cast<size_t>(d) * M + lane;
+            my_shift = __ldg(args.shift + e);
+            my_w = __ldg(args.wraw + e);
+            my_wd = __ldg(args.wder + e);
+            my_g = __ldg(args.gain + lane);
+        }
+        // cotangent segment of this warp's direction, bins [iseg0, iseg0 + seg)
+        const int iseg0 = i0 - reach;
+        __syncwarp();  // the previous tile's reads of the segment are done
+        for (int k = lane; k < args.seg; k += 32) {
+            const int i = iseg0 + k;
+            gs[k] = (dir_ok && i >= 0 && i < args.n_out) ? __ldg(args.G + static_cast<size_t>(d) * args.n_out + i)
+                                                         : 0.f;
+        }
+
+        uint64_t acc[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) acc[t] = 0ull;
+        const int lane_base = n_start - x0 + lane * T - 1;
+        float sum_d = 0.f, sum_g = 0.f;  // lane m keeps mic m's totals
+        bool failed = false;
+
+        for (int st = 0; st < nstages; ++st, ++g) {
+            const int b = g % NS;
+            const uint32_t par = static_cast<uint32_t>((g / NS) & 1);
+            const bool ok = !*vabort && ptx::mbar_wait_hinted(&full[b], par, kAdjPolls, kAdjHintNs);
+            if (!__all_sync(0xffffffffu, ok)) {
+                failed = true;
+                break;
+            }
+            const bool pass_b = st >= ngroups;
+            const int grp = st % ngroups;
             if (!pass_b) {
 #pragma unroll
                 for (int mi = 0; mi < MS; ++mi) {
@@ -204,119 +284,90 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
                     const int s0 = lane_base + J;
                     const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
                         stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
-                    const float g = __shfl_sync(0xffffffffu, my_g, m);
-                    const float f0 = g * __shfl_sync(0xffffffffu, my_w.x, m);
-                    const float f1 = g * __shfl_sync(0xffffffffu, my_w.y, m);
-                    const float f2 = g * __shfl_sync(0xffffffffu, my_w.z, m);
-                    const float f3 = g * __shfl_sync(0xffffffffu, my_w.w, m);
+                    const float gm = __shfl_sync(0xffffffffu, my_g, m);
+                    const float f0 = gm * __shfl_sync(0xffffffffu, my_w.x, m);
+                    const float f1 = gm * __shfl_sync(0xffffffffu, my_w.y, m);
+                    const float f2 = gm * __shfl_sync(0xffffffffu, my_w.z, m);
+                    const float f3 = gm * __shfl_sync(0xffffffffu, my_w.w, m);
                     if (s0 & 1)
                         adj_fwd_mic<true>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
                     else
                         adj_fwd_mic<false>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
                 }
             } else {
-                // both mics of the stage, then one joint reduction of their (value, slope) sums
-                float red[MS][2];
 #pragma unroll
-                for (int mi = 0; mi < MS; ++mi) {
-                    red[mi][0] = red[mi][1] = 0.f;
-                    const int m = grp * MS + mi;
-                    if (m < M) {
-                        const int J = __shfl_sync(0xffffffffu, my_shift, m);
-                        const int s0 = lane_base + J;
-                        const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
-                            stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
-                        const float4 C = (s0 & 1) ? adj_corr_mic<true>(acc, p) : adj_corr_mic<false>(acc, p);
-                        const float w0 = __shfl_sync(0xffffffffu, my_w.x, m), w1 = __shfl_sync(0xffffffffu, my_w.y, m);
-                        const float w2 = __shfl_sync(0xffffffffu, my_w.z, m), w3 = __shfl_sync(0xffffffffu, my_w.w, m);
-                        const float d0 = __shfl_sync(0xffffffffu, my_wd.x, m), d1 = __shfl_sync(0xffffffffu, my_wd.y, m);
-                        const float d2 = __shfl_sync(0xffffffffu, my_wd.z, m), d3 = __shfl_sync(0xffffffffu, my_wd.w, m);
-                        red[mi][0] = fmaf(w0, C.x, fmaf(w1, C.y, fmaf(w2, C.z, w3 * C.w)));
-                        red[mi][1] = fmaf(d0, C.x, fmaf(d1, C.y, fmaf(d2, C.z, d3 * C.w)));
+                for (int pr = 0; pr < MS / 2; ++pr) {
+                    // both mics of the pair, then one joint reduction of their (value, slope) sums
+                    float red[2][2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int mi = 2 * pr + h;
+                        red[h][0] = red[h][1] = 0.f;
+                        const int m = grp * MS + mi;
+                        if (m < M) {
+                            const int J = __shfl_sync(0xffffffffu, my_shift, m);
+                            const int s0 = lane_base + J;
+                            const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
+                                stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
+                            const float4 C = (s0 & 1) ? adj_corr_mic<true>(acc, p) : adj_corr_mic<false>(acc, p);
+                            const float w0 = __shfl_sync(0xffffffffu, my_w.x, m), w1 = __shfl_sync(0xffffffffu, my_w.y, m);
+                            const float w2 = __shfl_sync(0xffffffffu, my_w.z, m), w3 = __shfl_sync(0xffffffffu, my_w.w, m);
+                            const float d0 = __shfl_sync(0xffffffffu, my_wd.x, m), d1 = __shfl_sync(0xffffffffu, my_wd.y, m);
+                            const float d2 = __shfl_sync(0xffffffffu, my_wd.z, m), d3 = __shfl_sync(0xffffffffu, my_wd.w, m);
+                            red[h][0] = fmaf(w0, C.x, fmaf(w1, C.y, fmaf(w2, C.z, w3 * C.w)));
+                            red[h][1] = fmaf(d0, C.x, fmaf(d1, C.y, fmaf(d2, C.z, d3 * C.w)));
+                        }
+                    }
+                    adj_pair_reduce(red, lane, grp * MS + 2 * pr, sum_g, sum_d);
+                }
+            }
+            if (st == ngroups - 1) {
+                // beams of this tile are complete: turn them into G_b = G_env b / |b| on owned
+                // samples.  G_env[n] sums the bins i in [ceil((n - half)/R), floor((n + half)/R)]
+                // (tap j = n - R i + half); both ends advance incrementally with n.
+                __syncwarp();
+                const int R = args.R;
+                const int n_first = n_start + lane * T;
+                const int xo = n_first - half + R * reach * 4;  // > 0
+                int i_lo = (xo + R - 1) / R - reach * 4;           // ceil((n - half)/R)
+                int r_lo = (i_lo + reach * 4) * R - xo;            // R i_lo - (n - half), in [0, R)
+                const int yo = n_first + half + R * reach * 4;
+                int i_hi = yo / R - reach * 4;                     // floor((n + half)/R)
+                int r_hi = yo - (i_hi + reach * 4) * R;            // (n + half) - R i_hi, in [0, R)
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const int n = n_first + t;
+                    float ge = 0.f;
+                    if (n >= own_lo && n < own_hi && n >= 0 && n < args.N) {
+                        int j = 2 * half - r_lo;  // tap of bin i_lo
+                        for (int i = i_lo; i <= i_hi; ++i, j -= R) ge = fmaf(gs[i - iseg0], hs[j], ge);
+                    }
+                    const float2 v = unpack2(acc[t]);
+                    const float m2 = v.x * v.x + v.y * v.y;
+                    const float sc = m2 > 0.f ? ge * rsqrtf(m2) : 0.f;
+                    acc[t] = pack2(sc * v.x, sc * v.y);
+                    // n -> n + 1
+                    if (--r_lo < 0) {
+                        r_lo += R;
+                        ++i_lo;
+                    }
+                    if (++r_hi == R) {
+                        r_hi = 0;
+                        ++i_hi;
                     }
                 }
-                // reduce-scatter of the 4 sums over the warp: after the xor-16 and xor-8
-                // exchanges lane bits (4, 3) select (mic, value/slope); then a plain sum
-                const bool b16 = lane & 16, b8 = lane & 8;
-                float k0 = b16 ? red[1][0] : red[0][0], k1 = b16 ? red[1][1] : red[0][1];
-                const float s0 = b16 ? red[0][0] : red[1][0], s1 = b16 ? red[0][1] : red[1][1];
-                k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
-                k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
-                float k = b8 ? k1 : k0;
-                k += __shfl_xor_sync(0xffffffffu, b8 ? k0 : k1, 8);
-                k += __shfl_xor_sync(0xffffffffu, k, 4);
-                k += __shfl_xor_sync(0xffffffffu, k, 2);
-                k += __shfl_xor_sync(0xffffffffu, k, 1);
-                const int m0 = grp * MS;
-                const int src = (lane == m0 + 1) ? 16 : 0;
-                const float tg = __shfl_sync(0xffffffffu, k, src), td = __shfl_sync(0xffffffffu, k, src + 8);
-                if (lane == m0 || lane == m0 + 1) {
-                    sum_g = tg;
-                    sum_d = td;
-                }
             }
-        }
-        if (st == ngroups - 1 && dir_ok && !__any_sync(0xffffffffu, timed_out)) {
-            // beams of this tile are complete: turn them into G_b = G_env b / |b| on owned
-            // samples.  G_env[n] sums the bins i in [ceil((n - half)/R), floor((n + half)/R)]
-            // (tap j = n - R i + half); both ends advance incrementally with n.
             __syncwarp();
-            const int R = args.R;
-            const int n_first = n_start + lane * T;
-            const int xo = n_first - half + R * reach * 4;  // > 0
-            int i_lo = (xo + R - 1) / R - reach * 4;           // ceil((n - half)/R)
-            int r_lo = (i_lo + reach * 4) * R - xo;            // R i_lo - (n - half), in [0, R)
-            const int yo = n_first + half + R * reach * 4;
-            int i_hi = yo / R - reach * 4;                     // floor((n + half)/R)
-            int r_hi = yo - (i_hi + reach * 4) * R;            // (n + half) - R i_hi, in [0, R)
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                const int n = n_first + t;
-                float ge = 0.f;
-                if (n >= own_lo && n < own_hi && n >= 0 && n < args.N) {
-                    int j = 2 * half - r_lo;  // tap of bin i_lo
-                    for (int i = i_lo; i <= i_hi; ++i, j -= R) ge = fmaf(gs[i - iseg0], hs[j], ge);
-                }
-                const float2 v = unpack2(acc[t]);
-                const float m2 = v.x * v.x + v.y * v.y;
-                const float sc = m2 > 0.f ? ge * rsqrtf(m2) : 0.f;
-                acc[t] = pack2(sc * v.x, sc * v.y);
-                // n -> n + 1
-                if (--r_lo < 0) {
-                    r_lo += R;
-                    ++i_lo;
-                }
-                if (++r_hi == R) {
-                    r_hi = 0;
-                    ++i_hi;
-                }
+            if (lane == 0) ptx::mbar_arrive(&empty[b]);  // the producer may refill buffer b
+        }
+        if (failed) {
+            if (lane == 0) {
+                if (!*vabort) atomicOr(args.status, RTIS_DEV_TIMEOUT);
+                *vabort = 1;
             }
+            break;
         }
-        // release buffer b; the CTA's last warp to get here refills it
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence_block();
-            const int prev = atomicAdd(&done[b], 1);
-            if (prev == kTdDirsPerCta - 1) {
-                done[b] = 0;
-                __threadfence_block();
-                if (st + NS < nstages) {
-                    ptx::fence_proxy_async();
-                    issue(st + NS);
-                }
-            }
-        }
-    }
-    if (dir_ok && lane < M && !timed_out)
-        args.part[(static_cast<size_t>(nt) * args.D + d) * M + lane] = make_float2(my_g * sum_d, sum_g);
-
-    if (__syncthreads_or(timed_out)) {
-        if (threadIdx.x == 0) {
-            for (int b = 0; b < NS; ++b)
-                if (issued[b] > 0)
-                    ptx::mbar_wait_bounded(&bar[b], static_cast<uint32_t>((issued[b] - 1) & 1), kAdjPolls);
-        }
-        __syncthreads();
+        if (dir_ok && lane < M) args.part[(static_cast<size_t>(nt) * args.D + d) * M + lane] = make_float2(my_g * sum_d, sum_g);
     }
 }
 
@@ -422,8 +473,8 @@ int adj_seg(const Plan& p) {
 }  // namespace
 
 size_t adj_smem_bytes(const Plan& p) {
-    return static_cast<size_t>(kAdjNS) * kAdjMS * p.td_row * 8 + kAdjNS * (8 + 4 + 4) +
-           static_cast<size_t>((p.lpf_len + 3) & ~3) * 4 + static_cast<size_t>(kTdDirsPerCta) * adj_seg(p) * 4;
+    return static_cast<size_t>(kAdjNS) * kAdjMS * p.td_row * 8 + kTdBarrierBytes +
+           static_cast<size_t>((p.lpf_len + 3) & ~3) * 4 + static_cast<size_t>(kTdWarps) * adj_seg(p) * 4;
 }
 
 cudaError_t launch_td_adjoint(const Plan& p, const float* d_grad_out, float* d_gxyz, float* d_ggain, float* d_gdelay,
@@ -449,12 +500,15 @@ cudaError_t launch_td_adjoint(const Plan& p, const float* d_grad_out, float* d_g
     a.bins_per_tile = p.td_bins_per_tile;
     a.seg = adj_seg(p);
     const size_t smem = adj_smem_bytes(p);
-    cudaError_t e = cudaFuncSetAttribute(td_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(td_adjoint_kernel<kAdjMS, kAdjNS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
+    int n_sm = 1, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 1;
     const int n_tiles = (p.n_out + p.td_bins_per_tile - 1) / p.td_bins_per_tile;
-    const dim3 grid((p.D + kTdDirsPerCta - 1) / kTdDirsPerCta, n_tiles);
-    td_adjoint_kernel<<<grid, 32 * kTdDirsPerCta, smem, st>>>(p.tmap_a, a);
+    const int total = ((p.D + kTdWarps - 1) / kTdWarps) * n_tiles;
+    td_adjoint_kernel<kAdjMS, kAdjNS><<<std::min(total, n_sm), kTdThreads, smem, st>>>(p.tmap_a, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     adj_reduce1_kernel<<<dim3(p.M, kAdjRedBlocks), kAdjRedThreads, 0, st>>>(p.d_adj, p.d_dirs, p.M, p.D, n_tiles,
