@@ -164,7 +164,9 @@ rtis_status rtis_plan_get_info(const rtis_plan* plan, rtis_plan_info* info);
  * rtis_process -- whole chain for one recording (Fig. 3): matched filter,
  * delay-and-sum on the plan's path, envelope, low-pass, subsample.
  *   RTIS_PATH_TD  Catmull-Rom fractional delays on the full-rate analytic signal.
- *   RTIS_PATH_FD  exact phase ramps on the in-band spectrum; needs F <= 32768.
+ *   RTIS_PATH_FD  exact phase ramps on the in-band spectrum; needs F <= 65536 with
+ *                 its spectrum, FFT buffer and outputs in shared memory (N up to
+ *                 about 46000 at R = 10; larger N: RTIS_ERR_UNSUPPORTED).
  *   RTIS_PATH_BB  complex baseband: the paper subsamples before its filters
  *                 (Sec. 4.3); this path subsamples after the matched filter.
  *                 The analytic signal, demodulated by the mid-band bin
@@ -189,7 +191,7 @@ rtis_status rtis_process(rtis_plan* plan, const int16_t* d_in, float* d_out, voi
  * feeding either or both delay-and-sum forms:
  *   d_out_td  [n][n_dirs][n_out]: time-domain energyscapes (or NULL);
  *   d_out_fd  [n][n_dirs][n_out]: frequency-domain energyscapes (or NULL;
- *             needs n <= opt.max_batch and F <= 32768).
+ *             needs n <= opt.max_batch and F <= 65536).
  * The frequency-domain delay-and-sum of all n runs as ONE batched complex
  * GEMM on the tensor cores (the phase-ramp form of Fig. 3 / Sec. 4.1 with the
  * measurements as frames: Y[d][k][t] = sum_m g_m e^{+2 pi i k delta_dm/F} A_m^t[k],
@@ -224,7 +226,7 @@ rtis_status rtis_beamform_td(rtis_plan* plan, const float* d_a, float* d_out, vo
 /*
  * rtis_beamform_fd -- frequency-domain delay-and-sum with the envelope,
  * low-pass and subsampling, from the in-band matched-filter spectra
- * (rtis_matched_filter's d_A).  Needs F <= 32768.
+ * (rtis_matched_filter's d_A).  Needs F <= 65536 (as RTIS_PATH_FD).
  *   d_A    device complex float [n_mics][k_hi-k_lo+1], 8-byte aligned
  *   d_out  device float [n_dirs][n_out]
  */

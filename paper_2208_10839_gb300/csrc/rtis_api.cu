@@ -318,7 +318,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     if (opt.path == RTIS_PATH_FD && rtis::fdes_smem_bytes(p) > 227 * 1024) {
         delete plan;
         return fail(RTIS_ERR_UNSUPPORTED,
-                    "rtis_plan_create: frequency-domain path needs F <= 32768 and the envelope in shared memory");
+                    "rtis_plan_create: the frequency-domain path needs F <= 65536 and its buffers in shared memory (N <= ~46000 at R = 10)");
     }
     if (opt.path == RTIS_PATH_BB) {
         // coarse grid: every 4th sample; |floor(delta/4)| <= bb_Jlim whenever |floor(delta)| <= Jlim
@@ -710,7 +710,7 @@ rtis_status rtis_process_many(rtis_plan* plan, const int16_t* d_in, int n, float
     if (d_out_fd && n > p.max_batch)
         return fail(RTIS_ERR_INVALID_ARG, "rtis_process_many: n exceeds the plan's max_batch (rtis_options)");
     if (d_out_fd && rtis::fdes_smem_bytes(p) > 227 * 1024)
-        return fail(RTIS_ERR_UNSUPPORTED, "rtis_process_many: the frequency-domain path needs F <= 32768");
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_process_many: the frequency-domain path needs F <= 65536 and its buffers in shared memory");
     const size_t in_stride = static_cast<size_t>(p.M) * p.N, out_stride = static_cast<size_t>(p.D) * p.n_out;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rtis::trace_call(p, st);
@@ -808,7 +808,7 @@ rtis_status rtis_beamform_fd(rtis_plan* plan, const float* d_A, float* d_out, vo
         return fail(RTIS_ERR_INVALID_ARG, "rtis_beamform_fd: d_A must be 8-byte aligned");
     Plan& p = plan->p;
     if (rtis::fdes_smem_bytes(p) > 227 * 1024)
-        return fail(RTIS_ERR_UNSUPPORTED, "rtis_beamform_fd: needs F <= 32768 and the envelope in shared memory");
+        return fail(RTIS_ERR_UNSUPPORTED, "rtis_beamform_fd: needs F <= 65536 and its buffers in shared memory");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rtis::trace_call(p, st);
     rtis_status s = ensure_table(p, st);

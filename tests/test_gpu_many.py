@@ -124,3 +124,26 @@ def test_both_paths_from_one_matched_filter(torch_cuda):
             got = E_fd[t].cpu().numpy().astype(np.float64)
             assert np.max(np.abs(got - ref)) <= E_TOL * ref.max()
         assert p.sync() == 0 and pf.sync() == 0
+
+
+def test_fd_batched_gemm_longest_records(torch_cuda):
+    """F = 65536 (32768-sample records, the ring's longest sensors): the batched GEMM over
+    8738 in-band bins and the 512-thread IFFT kernel reading its output, against the
+    per-measurement path and the oracle."""
+    torch = torch_cuda
+    from paper_2208_10839_gb300 import Plan
+    cfgs = [synth.hemisphere(seed_scene=40 + i, n_samples=32768, n_dirs=16) for i in range(2)]
+    cfg = cfgs[0]
+    xs = np.stack([c["x"] for c in cfgs])
+    x = torch.from_numpy(xs).cuda()
+    with Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], 32768, path="fd", max_batch=2) as p:
+        assert p.info.fft_len == 65536
+        E = p.process_many(x)
+        ref = torch.stack([p.process(x[t]) for t in range(2)])
+        assert p.sync() == 0
+    E, ref = E.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)
+    for t in range(2):
+        E_ref = orc.energyscape(xs[t], cfg["chirp"], cfg["mic_xyz"], cfg["dirs"], cfg["fs"], cfg["c"], path="fd")
+        for got in (E[t], ref[t]):
+            assert np.max(np.abs(got - E_ref)) <= E_TOL * E_ref.max()
+            assert np.argmax(got) == np.argmax(E_ref)

@@ -273,6 +273,27 @@ def test_process_fd_edge_shapes(torch_cuda, M, N, D, decim, taps):
         assert_energyscape(E.cpu().numpy(), E_ref)
 
 
+@pytest.mark.parametrize("N,D,decim,taps", [
+    (32768, 24, 10, None),   # F = 65536: 512-thread kernel, pruned first pass, register fold
+    (33000, 9, 9, 13),       # custom short low-pass, ragged N
+    (32768, 7, 15, 61),      # a low-pass longer than the register fold takes: the general kernel
+])
+def test_process_fd_longest_records(torch_cuda, N, D, decim, taps):
+    """The frequency-domain path at F = 65536 (records of 32768 samples and more)."""
+    torch = torch_cuda
+    cfg = synth.hemisphere(seed_scene=11, n_samples=N, n_dirs=D)
+    rng = np.random.default_rng(N + D)
+    h = None if taps is None else rng.uniform(0.0, 1.0, size=taps).astype(np.float32)
+    E_ref = orc.energyscape(cfg["x"], cfg["chirp"], cfg["mic_xyz"], cfg["dirs"], cfg["fs"], cfg["c"], path="fd",
+                            R=decim, h=None if h is None else h.astype(np.float64))
+    with make_plan(cfg, decim=decim, lpf_taps=h, path="fd") as p:
+        assert p.info.fft_len == 65536
+        E = p.process(to_dev(torch, cfg["x"]))
+        assert p.sync() == 0
+        rel = assert_energyscape(E.cpu().numpy(), E_ref)
+    print(f"FD at F = 65536, N = {N}: {rel:.1e} of the peak")
+
+
 @pytest.mark.slow
 def test_process_fd_hemisphere_full_size_sampled(torch_cuda):
     torch = torch_cuda
