@@ -44,9 +44,9 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each beamformer (ncu capture of this
 # workload, see profiles/); set to None whenever that kernel changes until it is re-captured
 TD_TRAFFIC_BYTES = 5552896
-FD_TRAFFIC_BYTES = None  # the per-direction FD kernel changed since its capture
+FD_TRAFFIC_BYTES = 1790000  # ncu prints 1.79 MB read, 0 written
 # td_adjoint_kernel on the calibration workload (32 x 16384 x 2048)
-ADJ_TRAFFIC_BYTES = None  # the adjoint changed since its capture
+ADJ_TRAFFIC_BYTES = 20133376
 # fd_gemm_kernel<BF16> captured at 400 bins (DRAM read + write), per bin; X and Y both grow with the bins
 FD_GEMM_TRAFFIC_PER_BIN = (13952256 + 358419200) / 400
 N_REF_DIRS = 16   # directions per step of the reference arm (the FP64 oracle)
