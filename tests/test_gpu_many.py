@@ -147,3 +147,26 @@ def test_fd_batched_gemm_longest_records(torch_cuda):
         for got in (E[t], ref[t]):
             assert np.max(np.abs(got - E_ref)) <= E_TOL * E_ref.max()
             assert np.argmax(got) == np.argmax(E_ref)
+
+
+@pytest.mark.parametrize("N", [16384, 20000, 31000])
+def test_fd_batched_f32768_record_lengths(torch_cuda, N):
+    """F = 32768 on the batched path for records from 16384 samples (the hemisphere) to
+    31000 (each phase then needs more than half of its P-point IFFT's outputs)."""
+    torch = torch_cuda
+    from paper_2208_10839_gb300 import Plan
+    cfgs = [synth.hemisphere(seed_scene=60 + i, n_samples=N, n_dirs=40) for i in range(3)]
+    cfg = cfgs[0]
+    xs = np.stack([c["x"] for c in cfgs])
+    x = torch.from_numpy(xs).cuda()
+    with Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], N, path="fd", max_batch=4) as p:
+        assert p.info.fft_len == 32768
+        E = p.process_many(x)
+        assert p.sync() == 0
+    E = E.cpu().numpy().astype(np.float64)
+    for t in range(3):
+        E_ref = orc.energyscape(xs[t], cfg["chirp"], cfg["mic_xyz"], cfg["dirs"], cfg["fs"], cfg["c"], path="fd")
+        err = np.max(np.abs(E[t] - E_ref)) / E_ref.max()
+        print(f"batched FD, N = {N}, measurement {t}: {err:.1e} of the peak")
+        assert err <= E_TOL
+        assert np.argmax(E[t]) == np.argmax(E_ref)
