@@ -45,6 +45,8 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # workload, see profiles/); set to None whenever that kernel changes until it is re-captured
 TD_TRAFFIC_BYTES = 5552896
 FD_TRAFFIC_BYTES = 1790000  # ncu prints 1.79 MB read, 0 written
+# bb_beamform_kernel on the hemisphere workload (the <4, 5> layout; z and the tables, E stays in L2)
+BB_TRAFFIC_BYTES = 2921472
 # td_adjoint_kernel on the calibration workload (32 x 16384 x 2048)
 ADJ_TRAFFIC_BYTES = 20133376
 # fd_gemm_kernel<BF16> captured at 400 bins (DRAM read + write), per bin; X and Y both grow with the bins
@@ -784,12 +786,12 @@ def run_baseband(args, rank, world, local):
                           "speedup": tdk_s / bbk_s},
         "max_abs_diff_over_peak_vs_exact_delay_fd": {"bb": err_fd, "td": err_td_fd},
         "roofline": {"bound": "alu", "kernel": "bb_beamform_kernel", "achieved": ach, "peak": peak_tf,
-                     "unit": "TFLOP/s", "frac": ach / peak_tf, "traffic": None,
+                     "unit": "TFLOP/s", "frac": ach / peak_tf, "traffic": BB_TRAFFIC_BYTES,
                      "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x "
                                    f"{SM_MAX_MHZ_NOMINAL:.0f} MHz",
                      "algorithmic_flops_per_launch": bb_flops, "launch_ms": bbk_s * 1e3,
                      "tuned_variant_grid": [p_bb.info.bb_variant, p_bb.info.bb_grid],
-                     "td_equivalent": {"flops": td_flops, "frac": td_flops / tdk_s / 1e12 / peak_tf}},
+                     "td_beamform_kernel": {"flops": td_flops, "frac": td_flops / tdk_s / 1e12 / peak_tf}},
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }

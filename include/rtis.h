@@ -322,9 +322,9 @@ rtis_status rtis_plan_sync(rtis_plan* plan, unsigned* bits);
  *   Device-side checks report into plans[0]'s status word.
  *
  * rtis_batch_create / rtis_batch_run / rtis_batch_destroy -- a reusable
- * batch.  The first run autotunes the beamformer (three stage layouts x three
- * grids: 1 or 2 persistent CTAs per SM, or one CTA per tile, each timed on
- * the real inputs; the outputs are
+ * batch.  The first run autotunes the beamformer (every stage layout of
+ * rtis_plan_info.td_layout_ms that fits x two grids: one persistent CTA per
+ * SM, or one CTA per tile, each timed on the real inputs; the outputs are
  * written several times); every run replays the batch as a CUDA graph on an
  * internal stream, ordered after and before `stream` with events.  A new set
  * of input/output pointers re-captures the graph.  The plans must outlive
@@ -334,7 +334,7 @@ typedef struct rtis_batch rtis_batch;
 typedef struct rtis_batch_info {
     int n_sensors, total_tiles;
     int tuned;        /* 1 once the first run has autotuned */
-    int variant;      /* beamformer stage layout: 0 = 2 mics x 4 stages, 1 = 4 x 2, 2 = 1 x 8 */
+    int variant;      /* beamformer stage layout v, timed at rtis_plan_info.td_layout_ms[2v] */
     int grid;         /* beamformer CTAs */
     float tuned_ms;   /* beamformer time of the chosen candidate */
 } rtis_batch_info;

@@ -10,15 +10,17 @@
 //   E[d][i] = sum_j h_i(4j - R i) |b_d[j]|: the plan's low-pass taps read at
 //             the coarse offsets from R i, renormalised to unit DC gain
 //
-// The layout follows the time-domain beamformer: one CTA is 8 warps = 8
-// directions x one range tile of 32 lanes x 14 coarse samples; channel rows
-// arrive by TMA through an mbarrier ring of NS stages x MS mics; the envelope,
-// low-pass and subsampling run in the epilogue out of shared memory.  Per mic
-// and coarse sample a lane forms s = sum_q w_q z (one packed multiply and three
-// packed FMAs on (re, im)) and accumulates cr * s and ci * s (two packed FMAs),
-// r = cr + i ci; the beam is (acc_c.re - acc_s.im, acc_c.im + acc_s.re).
-// That is 6 packed FMAs per (mic, coarse sample) against 4 per (mic, sample) on
-// the full-rate grid: 2.7x fewer.  Waits are bounded as in the other kernels.
+// The layout follows the time-domain beamformer: one persistent CTA per SM of
+// 16 direction warps and a producer warpgroup; a CTA tile is 16 directions x
+// one range tile of 32 lanes x 14 coarse samples.  Channel rows arrive by TMA
+// through a full/empty mbarrier ring of NS stages x MS mics that runs across
+// tile boundaries; the envelope, low-pass and subsampling run in the epilogue
+// out of a shared-memory row per warp.  Per mic and coarse sample a lane forms
+// s = sum_q w_q z (one packed multiply and three packed FMAs on (re, im)) and
+// accumulates cr * s and ci * s (two packed FMAs), r = cr + i ci; the beam is
+// (acc_c.re - acc_s.im, acc_c.im + acc_s.re).  That is 6 packed FMAs per
+// (mic, coarse sample) against 4 per (mic, sample) on the full-rate grid:
+// 2.7x fewer.  Every wait is bounded as in the other kernels.
 #include <algorithm>
 #include <cstring>
 
@@ -33,7 +35,9 @@ using ptx::mul2;
 using ptx::pack2;
 using ptx::unpack2;
 
-constexpr uint32_t kBbWaitPolls = 1u << 22;  // bounded mbarrier wait (~ seconds)
+// ring waits sleep up to kBbHintNs per poll; kBbPolls x kBbHintNs ~ 1.3 s bounds a wait
+constexpr uint32_t kBbHintNs = 20000;
+constexpr uint32_t kBbPolls = 1u << 16;
 
 struct BbArgs {
     const int* shift;    // [D][M]
@@ -43,7 +47,7 @@ struct BbArgs {
     float* E;            // [D][n_out]
     unsigned* status;
     int M, Nb, D, R, half, n_out, bins_per_tile, n_dgroups, total_tiles, H, row, nbox, ntap;
-    uint32_t stage_area;  // bytes of the stage ring; the envelope rows follow it
+    uint32_t stage_area;  // bytes of the stage ring; barriers, envelope rows and taps follow it
 };
 
 // one mic's contribution to a lane's T coarse samples; p points at the 16-byte
@@ -82,78 +86,120 @@ __device__ __forceinline__ void bb_mic(uint64_t (&ac)[kBbOutPerThread], uint64_t
     }
 }
 
+// Five warpgroups, one CTA per SM, as in the time-domain beamformer: warps
+// 0..15 beamform one direction each, warp 16 is the producer and warps 17..19
+// only hand their registers back (512 x 112 + 128 x 24 <= 640 x 96).
+// The producer walks the CTA's tiles and stages, waits until all 16 consumers
+// released a buffer's previous contents (its "empty" mbarrier), re-arms its
+// "full" mbarrier and issues the TMA boxes, one lane per box.  The ring runs
+// across tile boundaries, so the next tile's first rows land while the
+// consumers are still in this tile's epilogue.  A timeout sets the status word
+// and the CTA's abort flag; the producer then stops issuing and lets every
+// copy it issued land before it exits.
 template <int MS, int NS>
-__global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
+__global__ void __launch_bounds__(kBbThreads, 1)
     bb_beamform_kernel(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ BbArgs A) {
-    constexpr int NT = 32 * kTdDirsPerCta;
+    constexpr int NW = kBbWarps;
     constexpr int T = kBbOutPerThread;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* stage = smem_raw;
-    float* env_all = reinterpret_cast<float*>(smem_raw + A.stage_area);  // [8][kBbWarpSamples]
-    uint64_t* bar = reinterpret_cast<uint64_t*>(env_all + kTdDirsPerCta * kBbWarpSamples);
-    int* done = reinterpret_cast<int*>(bar + NS);
-    int* issued = done + NS;
-    int* next_issued = issued + NS;  // stages of this CTA's next tile already in flight
-    float* hs = reinterpret_cast<float*>(next_issued + 1);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + A.stage_area);
+    uint64_t* empty = full + NS;
+    int* abort_flag = reinterpret_cast<int*>(empty + NS);
+    int* issued = abort_flag + 1;  // [NS]: uses of each buffer issued so far (producer only)
+    float* env_all = reinterpret_cast<float*>(smem_raw + A.stage_area + kTdBarrierBytes);  // [NW][kBbWarpSamples]
+    float* hs = env_all + NW * kBbWarpSamples;                                              // [4][ntap]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int b = 0; b < NS; ++b) {
-            ptx::mbar_init(&bar[b], 1);
-            done[b] = 0;
+            ptx::mbar_init(&full[b], 1);
+            ptx::mbar_init(&empty[b], NW);
             issued[b] = 0;
         }
-        *next_issued = 0;
+        *abort_flag = 0;
         ptx::fence_mbar_init();
         ptx::fence_proxy_async();
     }
-    for (int j = threadIdx.x; j < 4 * A.ntap; j += NT) hs[j] = A.hb[j];
+    for (int j = threadIdx.x; j < 4 * A.ntap; j += kBbThreads) hs[j] = A.hb[j];
+    __syncthreads();
+    volatile int* vabort = abort_flag;
 
     const int M = A.M, row = A.row;
     const int nstages = (M + MS - 1) / MS;
-    const uint32_t stage_bytes = static_cast<uint32_t>(MS * A.nbox * kBbBox * 8);
     // TMA x of a tile's rows: an even element (16 bytes) at or before its first
     // coarse sample jS = ceil((R i0 - half) / 4) minus the halo
     auto tile_x0 = [&](int t) {
         const int i0t = (t / A.n_dgroups) * A.bins_per_tile;
         return (-((A.half - A.R * i0t) >> 2) - A.H) & ~1;
     };
-    // stage st of a tile whose rows start at x, into ring slot g (global stage count):
-    // a whole warp issues it, lane 0 arming the barrier and every lane one box
-    auto issue_warp = [&](int g, int x, int st) {
-        const int b = g % NS;
+
+    if (warp >= NW) {
+        // ---------------- producer warpgroup: warp NW issues, the other three leave ----------------
+        ptx::setmaxnreg_dec<kTdProducerRegs>();
+        if (warp != NW) return;
+        const uint32_t stage_bytes = static_cast<uint32_t>(MS * A.nbox * kBbBox * 8);
+        if (lane == 0) ptx::prefetch_tmap(&zmap);
+        int g = 0;  // stages issued by this CTA so far
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < A.total_tiles && !stop; tile += gridDim.x) {
+            const int x0 = tile_x0(tile);
+            for (int st = 0; st < nstages; ++st, ++g) {
+                const int b = g % NS;
+                const int use = g / NS;
+                int ok = 1;
+                if (lane == 0) {
+                    if (*vabort) {
+                        ok = 0;
+                    } else if (use > 0 && !ptx::mbar_wait_hinted(&empty[b], static_cast<uint32_t>((use - 1) & 1),
+                                                                 kBbPolls, kBbHintNs)) {
+                        ok = 0;
+                        atomicOr(A.status, RTIS_DEV_TIMEOUT);
+                        *vabort = 1;
+                    }
+                    if (ok) {
+                        ptx::fence_proxy_async();
+                        ptx::mbar_arrive_expect_tx(&full[b], stage_bytes);
+                        issued[b] = use + 1;
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    stop = true;
+                    break;
+                }
+                // rows st * MS + mi >= M lie outside the tensor and arrive as zeros
+                for (int k = lane; k < MS * A.nbox; k += 32) {
+                    const int mi = k / A.nbox, bx = k - mi * A.nbox;
+                    unsigned char* dst =
+                        stage + (static_cast<size_t>(b * MS + mi) * row + static_cast<size_t>(bx) * kBbBox) * 8;
+                    ptx::tma_load_2d(dst, &zmap, x0 + bx * kBbBox, st * MS + mi, &full[b]);
+                }
+            }
+        }
+        // every copy this CTA issued lands before the CTA can exit
         if (lane == 0) {
-            issued[b] += 1;
-            ptx::mbar_arrive_expect_tx(&bar[b], stage_bytes);
+            for (int b = 0; b < NS; ++b)
+                if (issued[b] > 0)
+                    ptx::mbar_wait_hinted(&full[b], static_cast<uint32_t>((issued[b] - 1) & 1), kBbPolls, kBbHintNs);
         }
-        __syncwarp();
-        for (int k = lane; k < MS * A.nbox; k += 32) {
-            const int mi = k / A.nbox, bx = k - mi * A.nbox;
-            unsigned char* dst = stage + (static_cast<size_t>(b * MS + mi) * row + static_cast<size_t>(bx) * kBbBox) * 8;
-            ptx::tma_load_2d(dst, &zmap, x + bx * kBbBox, st * MS + mi, &bar[b]);
-        }
-    };
-    int g0 = 0;
-    bool timed_out = false;
+        return;
+    }
+
+    // ---------------- consumers: warp = direction within the tile ----------------
+    ptx::setmaxnreg_inc<kTdConsumerRegs>();
+    float* env = env_all + warp * kBbWarpSamples;
+    int g = 0;
     for (int tile = blockIdx.x; tile < A.total_tiles; tile += gridDim.x) {
         const int dg = tile % A.n_dgroups;
-        const int d = dg * kTdDirsPerCta + warp;
+        const int d = dg * NW + warp;
         const int i0 = (tile / A.n_dgroups) * A.bins_per_tile;
         const int jS = -((A.half - A.R * i0) >> 2);  // ceil((R i0 - half) / 4): first coarse sample
         const int x0 = tile_x0(tile);
-        const int next_tile = tile + gridDim.x;
 
-        __syncthreads();  // the previous tile's refills are all issued
-        if (warp == 0) {
-            if (lane == 0 && tile == static_cast<int>(blockIdx.x)) ptx::prefetch_tmap(&zmap);
-            // the first stages not already prefetched while the previous tile finished
-            const int pre = *next_issued;
-            for (int st = pre; st < NS && st < nstages; ++st) issue_warp(g0 + st, x0, st);
-            __syncwarp();
-            if (lane == 0) *next_issued = 0;
-        }
-
-        // lane m holds the steering entry of mic m for this warp's direction
+        // lane m holds the steering entry of mic m for this warp's direction; a
+        // direction past the set's end keeps zero weights and shift, so it reads
+        // inside the staged rows and sums zeros (no branch around the mic loop)
         const bool dir_ok = d < A.D;
         int my_shift = 0;
         float4 my_w = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -173,72 +219,49 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
         }
         const int lane_base = jS - x0 + lane * T - 1;  // smem index of z[jS + lane T - 1]
 
-        for (int st = 0; st < nstages; ++st) {
-            const int b = (g0 + st) % NS;
-            if (!timed_out) {
-                const uint32_t par = static_cast<uint32_t>(((g0 + st) / NS) & 1);
-                if (!ptx::mbar_wait_bounded(&bar[b], par, kBbWaitPolls)) {
-                    timed_out = true;
-                    atomicOr(A.status, RTIS_DEV_TIMEOUT);
-                }
+        bool failed = false;
+        for (int st = 0; st < nstages; ++st, ++g) {
+            const int b = g % NS;
+            const uint32_t par = static_cast<uint32_t>((g / NS) & 1);
+            const bool ok = !*vabort && ptx::mbar_wait_hinted(&full[b], par, kBbPolls, kBbHintNs);
+            if (!__all_sync(0xffffffffu, ok)) {
+                failed = true;
+                break;
             }
-            const bool warp_timed_out = __any_sync(0xffffffffu, timed_out);
-            if (dir_ok && !warp_timed_out) {
 #pragma unroll
-                for (int mi = 0; mi < MS; ++mi) {
-                    const int m = st * MS + mi;
-                    if (m >= M) break;
-                    const int J = __shfl_sync(0xffffffffu, my_shift, m);
-                    const float f0 = __shfl_sync(0xffffffffu, my_w.x, m);
-                    const float f1 = __shfl_sync(0xffffffffu, my_w.y, m);
-                    const float f2 = __shfl_sync(0xffffffffu, my_w.z, m);
-                    const float f3 = __shfl_sync(0xffffffffu, my_w.w, m);
-                    const float rc = __shfl_sync(0xffffffffu, my_r.x, m);
-                    const float rs = __shfl_sync(0xffffffffu, my_r.y, m);
-                    const int s0 = lane_base + J;  // parity is warp-uniform (T even)
-                    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
-                        stage + (static_cast<size_t>(b * MS + mi) * row + (s0 & ~1)) * 8);
-                    if (s0 & 1)
-                        bb_mic<true>(ac, as, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3),
-                                     pack2(rc, rc), pack2(rs, rs));
-                    else
-                        bb_mic<false>(ac, as, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3),
-                                      pack2(rc, rc), pack2(rs, rs));
-                }
+            for (int mi = 0; mi < MS; ++mi) {
+                const int m = st * MS + mi;
+                if (m >= M) break;
+                const int J = __shfl_sync(0xffffffffu, my_shift, m);
+                const float f0 = __shfl_sync(0xffffffffu, my_w.x, m);
+                const float f1 = __shfl_sync(0xffffffffu, my_w.y, m);
+                const float f2 = __shfl_sync(0xffffffffu, my_w.z, m);
+                const float f3 = __shfl_sync(0xffffffffu, my_w.w, m);
+                const float rc = __shfl_sync(0xffffffffu, my_r.x, m);
+                const float rs = __shfl_sync(0xffffffffu, my_r.y, m);
+                const int s0 = lane_base + J;  // parity is warp-uniform (T even)
+                const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
+                    stage + (static_cast<size_t>(b * MS + mi) * row + (s0 & ~1)) * 8);
+                if (s0 & 1)
+                    bb_mic<true>(ac, as, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3), pack2(rc, rc),
+                                 pack2(rs, rs));
+                else
+                    bb_mic<false>(ac, as, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3),
+                                  pack2(rc, rc), pack2(rs, rs));
             }
-            // release buffer b; the CTA's last warp to get here refills it with the
-            // stage NS later: of this tile, or else of the CTA's next tile
             __syncwarp();
-            int last = 0;
-            if (lane == 0) {
-                __threadfence_block();
-                const int prev = atomicAdd(&done[b], 1);
-                if (prev == kTdDirsPerCta - 1) {
-                    done[b] = 0;
-                    __threadfence_block();
-                    last = 1;
-                }
-            }
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (last && !warp_timed_out) {  // no refills once a wait has given up
-                const int nst = st + NS;
-                if (nst < nstages) {
-                    ptx::fence_proxy_async();
-                    issue_warp(g0 + nst, x0, nst);
-                } else if (next_tile < A.total_tiles && nst - nstages < nstages) {
-                    ptx::fence_proxy_async();
-                    issue_warp(g0 + nst, tile_x0(next_tile), nst - nstages);
-                    if (lane == 0) atomicAdd(next_issued, 1);
-                }
-            }
+            if (lane == 0) ptx::mbar_arrive(&empty[b]);  // the producer may refill buffer b
         }
-        g0 += nstages;
+        if (failed) {
+            if (lane == 0) {
+                if (!*vabort) atomicOr(A.status, RTIS_DEV_TIMEOUT);
+                *vabort = 1;
+            }
+            break;
+        }
 
-        if (__syncthreads_or(timed_out)) break;  // uniform: leave the tile loop, drain below
-
-        // epilogue (its own shared memory: the ring may already hold the next tile's rows):
-        // |b| over the warp's coarse samples, then the coarse low-pass
-        float* env = env_all + warp * kBbWarpSamples;
+        // epilogue: |b| over the warp's coarse samples into its own row, then the
+        // coarse low-pass
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const int j = jS + lane * T + t;
@@ -262,22 +285,13 @@ __global__ void __launch_bounds__(32 * kTdDirsPerCta, 2)
                 Erow[i] = acc_e;
             }
         }
-    }
-
-    if (__syncthreads_or(timed_out)) {
-        // give copies still in flight a bounded chance to land, then leave
-        if (threadIdx.x == 0) {
-            for (int b = 0; b < NS; ++b)
-                if (issued[b] > 0)
-                    ptx::mbar_wait_bounded(&bar[b], static_cast<uint32_t>((issued[b] - 1) & 1), kBbWaitPolls);
-        }
-        __syncthreads();
+        __syncwarp();  // the row is rewritten by the warp's next tile
     }
 }
 
 // stage layouts the autotuner picks from: (mics per stage, stages in the ring)
-constexpr int kBbVariantMS[kBbVariants] = {2, 2, 4, 1, 4, 2};
-constexpr int kBbVariantNS[kBbVariants] = {4, 8, 4, 8, 5, 10};
+constexpr int kBbVariantMS[kBbVariants] = {2, 4, 4, 2, 4, 8};
+constexpr int kBbVariantNS[kBbVariants] = {8, 4, 5, 10, 8, 4};
 
 uint32_t bb_stage_area(const Plan& p, int variant) {
     const size_t ring = static_cast<size_t>(kBbVariantMS[variant]) * kBbVariantNS[variant] * p.bb_row * 8;
@@ -285,17 +299,18 @@ uint32_t bb_stage_area(const Plan& p, int variant) {
 }
 
 size_t bb_smem_variant(const Plan& p, int variant) {
-    // ring, envelope rows, barriers + counters (<= 10 stages), next-tile count, taps
-    return bb_stage_area(p, variant) + static_cast<size_t>(kTdDirsPerCta) * kBbWarpSamples * 4 + 10 * (8 + 4 + 4) +
-           16 + static_cast<size_t>(4) * p.bb_ntap * 4;
+    // ring, barriers + abort flag + issue counters, one envelope row per consumer warp, taps
+    return bb_stage_area(p, variant) + kTdBarrierBytes + static_cast<size_t>(kBbWarps) * kBbWarpSamples * 4 +
+           static_cast<size_t>(4) * p.bb_ntap * 4;
 }
 
 template <int MS, int NS>
 cudaError_t bb_launch_t(const CUtensorMap& zmap, const BbArgs& A, int grid, size_t smem, cudaStream_t st) {
+    static_assert(16 * NS + 4 * (NS + 1) <= kTdBarrierBytes, "barrier area");
     cudaError_t e = cudaFuncSetAttribute(bb_beamform_kernel<MS, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    bb_beamform_kernel<MS, NS><<<grid, 32 * kTdDirsPerCta, smem, st>>>(zmap, A);
+    bb_beamform_kernel<MS, NS><<<grid, kBbThreads, smem, st>>>(zmap, A);
     return cudaGetLastError();
 }
 
@@ -315,7 +330,7 @@ cudaError_t bb_launch(const Plan& p, const CUtensorMap& zmap, float* d_out, int 
     A.half = (p.lpf_len - 1) / 2;
     A.n_out = p.n_out;
     A.bins_per_tile = p.bb_bins_per_tile;
-    A.n_dgroups = (p.D + kTdDirsPerCta - 1) / kTdDirsPerCta;
+    A.n_dgroups = (p.D + kBbWarps - 1) / kBbWarps;
     A.total_tiles = bb_tiles(p);
     A.H = p.bb_H;
     A.row = p.bb_row;
@@ -324,12 +339,12 @@ cudaError_t bb_launch(const Plan& p, const CUtensorMap& zmap, float* d_out, int 
     A.stage_area = bb_stage_area(p, variant);
     const size_t smem = bb_smem_variant(p, variant);
     switch (variant) {
-        case 0: return bb_launch_t<2, 4>(zmap, A, grid, smem, st);
-        case 1: return bb_launch_t<2, 8>(zmap, A, grid, smem, st);
-        case 2: return bb_launch_t<4, 4>(zmap, A, grid, smem, st);
-        case 3: return bb_launch_t<1, 8>(zmap, A, grid, smem, st);
-        case 4: return bb_launch_t<4, 5>(zmap, A, grid, smem, st);
-        case 5: return bb_launch_t<2, 10>(zmap, A, grid, smem, st);
+        case 0: return bb_launch_t<2, 8>(zmap, A, grid, smem, st);
+        case 1: return bb_launch_t<4, 4>(zmap, A, grid, smem, st);
+        case 2: return bb_launch_t<4, 5>(zmap, A, grid, smem, st);
+        case 3: return bb_launch_t<2, 10>(zmap, A, grid, smem, st);
+        case 4: return bb_launch_t<4, 8>(zmap, A, grid, smem, st);
+        case 5: return bb_launch_t<8, 4>(zmap, A, grid, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -342,17 +357,17 @@ bool bb_variant_fits(const Plan& p, int variant) {
 }
 
 int bb_tiles(const Plan& p) {
-    return ((p.D + kTdDirsPerCta - 1) / kTdDirsPerCta) * ((p.n_out + p.bb_bins_per_tile - 1) / p.bb_bins_per_tile);
+    return ((p.D + kBbWarps - 1) / kBbWarps) * ((p.n_out + p.bb_bins_per_tile - 1) / p.bb_bins_per_tile);
 }
 
-// Times every stage layout with one CTA per tile and with two persistent CTAs
+// Times every stage layout with one CTA per tile and with one persistent CTA
 // per SM on the plan's own (zeroed) workspace and keeps the fastest.
 cudaError_t bb_autotune(Plan& p, float* d_scratch_out) {
     int n_sm = 1, dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 1;
     const int tiles = bb_tiles(p);
-    const int grids[2] = {tiles, std::min(tiles, 2 * n_sm)};
+    const int grids[2] = {tiles, std::min(tiles, n_sm)};
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -392,7 +407,7 @@ cudaError_t launch_bb_beamform(const Plan& p, const CUtensorMap& zmap, float* d_
         int n_sm = 1, dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 1;
-        grid = std::min(bb_tiles(p), 2 * n_sm);
+        grid = std::min(bb_tiles(p), n_sm);
     }
     return bb_launch(p, zmap, d_out, p.bb_variant, grid, st);
 }

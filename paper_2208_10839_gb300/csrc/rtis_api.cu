@@ -516,7 +516,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
                 return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: the forced bb_layout does not fit shared memory");
             }
             p.bb_variant = opt.bb_layout - 1;
-            p.bb_grid = opt.grid_mode == 2 ? std::min(rtis::bb_tiles(p), 2 * n_sm) : rtis::bb_tiles(p);
+            p.bb_grid = opt.grid_mode == 2 ? std::min(rtis::bb_tiles(p), n_sm) : rtis::bb_tiles(p);
         } else if (e == cudaSuccess && opt.path == RTIS_PATH_BB) {
             e = rtis::bb_autotune(p, scratch);
         }

@@ -18,7 +18,6 @@ namespace rtis {
 // ----------------------------------------------------------------------------
 constexpr int kTdOutPerThread = 30;                   // even: 16-byte pair loads, conflict-free
 constexpr int kTdWarpSamples = 32 * kTdOutPerThread;  // samples one warp beamforms
-constexpr int kTdDirsPerCta = 8;                      // baseband and adjoint kernels: one warp per direction
 constexpr int kTdWarps = 16;                          // time-domain beamformer: directions (consumer warps) per CTA
 constexpr int kTdBox = 256;                           // TMA box width (8-byte elements)
 constexpr int kTdBarrierBytes = 256;                  // full/empty mbarriers, abort flag, issue counters
@@ -29,11 +28,13 @@ constexpr int kMaxMics = 32;                          // lanes hold per-mic stee
 
 // complex-baseband beamformer (kernels_bb.cu): the same CTA shape on a grid of
 // every 4th sample
+constexpr int kBbWarps = 16;                          // directions (consumer warps) per CTA
+constexpr int kBbThreads = 32 * (kBbWarps + 4);       // + a producer warpgroup; registers as kTd*Regs
 constexpr int kBbQ = 4;                               // full-rate samples per coarse sample
 constexpr int kBbOutPerThread = 14;                   // coarse samples per lane: T/2 odd, conflict-free 16-byte loads
 constexpr int kBbWarpSamples = 32 * kBbOutPerThread;
 constexpr int kBbBox = 96;                            // TMA box width (8-byte elements)
-constexpr int kBbVariants = 6;  // stage layouts: (2, 4), (2, 8), (4, 4), (1, 8), (4, 5), (2, 10)
+constexpr int kBbVariants = 6;  // stage layouts: (2, 8), (4, 4), (4, 5), (2, 10), (4, 8), (8, 4)
 
 // |z| from |z|^2 = x^2 + y^2 as n2 rsqrt(n2) (a few ulp, no slow path); 0 for 0, and a
 // NaN stays NaN (n2 * 0) so non-finite inputs still show in the output
