@@ -48,7 +48,7 @@ FD_TRAFFIC_BYTES = 1790000  # ncu prints 1.79 MB read, 0 written
 # bb_beamform_kernel on the hemisphere workload (the <4, 5> layout; z and the tables, E stays in L2)
 BB_TRAFFIC_BYTES = 2921472
 # td_adjoint_kernel on the calibration workload (32 x 16384 x 2048)
-ADJ_TRAFFIC_BYTES = 20133376
+ADJ_TRAFFIC_BYTES = 20115456
 # fd_gemm_kernel<BF16> captured at 400 bins (DRAM read + write), per bin; X and Y both grow with the bins
 FD_GEMM_TRAFFIC_PER_BIN = (13952256 + 358419200) / 400
 N_REF_DIRS = 16   # directions per step of the reference arm (the FP64 oracle)

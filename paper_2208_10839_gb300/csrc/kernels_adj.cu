@@ -265,7 +265,8 @@ __global__ void __launch_bounds__(kTdThreads, 1)
         float sum_d = 0.f, sum_g = 0.f;  // lane m keeps mic m's totals
         bool failed = false;
 
-        for (int st = 0; st < nstages; ++st, ++g) {
+        // pass A: the tile's beams
+        for (int st = 0; st < ngroups; ++st, ++g) {
             const int b = g % NS;
             const uint32_t par = static_cast<uint32_t>((g / NS) & 1);
             const bool ok = !*vabort && ptx::mbar_wait_hinted(&full[b], par, kAdjPolls, kAdjHintNs);
@@ -273,89 +274,98 @@ __global__ void __launch_bounds__(kTdThreads, 1)
                 failed = true;
                 break;
             }
-            const bool pass_b = st >= ngroups;
-            const int grp = st % ngroups;
-            if (!pass_b) {
+            // the stage's mics in a rolled loop (as in pass B): each mic's body is already
+            // 120 packed FMAs, and unrolled the two passes overflow the instruction cache
+#pragma unroll 1
+            for (int mi = 0; mi < MS; ++mi) {
+                const int m = st * MS + mi;
+                if (m >= M) break;
+                const int J = __shfl_sync(0xffffffffu, my_shift, m);
+                const int s0 = lane_base + J;
+                const ulonglong2* p =
+                    reinterpret_cast<const ulonglong2*>(stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
+                const float gm = __shfl_sync(0xffffffffu, my_g, m);
+                const float f0 = gm * __shfl_sync(0xffffffffu, my_w.x, m);
+                const float f1 = gm * __shfl_sync(0xffffffffu, my_w.y, m);
+                const float f2 = gm * __shfl_sync(0xffffffffu, my_w.z, m);
+                const float f3 = gm * __shfl_sync(0xffffffffu, my_w.w, m);
+                if (s0 & 1)
+                    adj_fwd_mic<true>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+                else
+                    adj_fwd_mic<false>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+            }
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&empty[b]);  // the producer may refill buffer b
+        }
+        if (!failed) {
+            // the beams are complete: turn them into G_b = G_env b / |b| on owned samples.
+            // G_env[n] sums the bins i in [ceil((n - half)/R), floor((n + half)/R)] (tap
+            // j = n - R i + half); both ends advance incrementally with n.
+            __syncwarp();
+            const int R = args.R;
+            const int n_first = n_start + lane * T;
+            const int xo = n_first - half + R * reach * 4;  // > 0
+            int i_lo = (xo + R - 1) / R - reach * 4;           // ceil((n - half)/R)
+            int r_lo = (i_lo + reach * 4) * R - xo;            // R i_lo - (n - half), in [0, R)
+            const int yo = n_first + half + R * reach * 4;
+            int i_hi = yo / R - reach * 4;                     // floor((n + half)/R)
+            int r_hi = yo - (i_hi + reach * 4) * R;            // (n + half) - R i_hi, in [0, R)
 #pragma unroll
-                for (int mi = 0; mi < MS; ++mi) {
-                    const int m = grp * MS + mi;
-                    if (m >= M) break;
-                    const int J = __shfl_sync(0xffffffffu, my_shift, m);
-                    const int s0 = lane_base + J;
-                    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
-                        stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
-                    const float gm = __shfl_sync(0xffffffffu, my_g, m);
-                    const float f0 = gm * __shfl_sync(0xffffffffu, my_w.x, m);
-                    const float f1 = gm * __shfl_sync(0xffffffffu, my_w.y, m);
-                    const float f2 = gm * __shfl_sync(0xffffffffu, my_w.z, m);
-                    const float f3 = gm * __shfl_sync(0xffffffffu, my_w.w, m);
-                    if (s0 & 1)
-                        adj_fwd_mic<true>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
-                    else
-                        adj_fwd_mic<false>(acc, p, pack2(f0, f0), pack2(f1, f1), pack2(f2, f2), pack2(f3, f3));
+            for (int t = 0; t < T; ++t) {
+                const int n = n_first + t;
+                float ge = 0.f;
+                if (n >= own_lo && n < own_hi && n >= 0 && n < args.N) {
+                    int j = 2 * half - r_lo;  // tap of bin i_lo
+                    for (int i = i_lo; i <= i_hi; ++i, j -= R) ge = fmaf(gs[i - iseg0], hs[j], ge);
                 }
-            } else {
-#pragma unroll
-                for (int pr = 0; pr < MS / 2; ++pr) {
-                    // both mics of the pair, then one joint reduction of their (value, slope) sums
-                    float red[2][2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int mi = 2 * pr + h;
-                        red[h][0] = red[h][1] = 0.f;
-                        const int m = grp * MS + mi;
-                        if (m < M) {
-                            const int J = __shfl_sync(0xffffffffu, my_shift, m);
-                            const int s0 = lane_base + J;
-                            const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
-                                stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
-                            const float4 C = (s0 & 1) ? adj_corr_mic<true>(acc, p) : adj_corr_mic<false>(acc, p);
-                            const float w0 = __shfl_sync(0xffffffffu, my_w.x, m), w1 = __shfl_sync(0xffffffffu, my_w.y, m);
-                            const float w2 = __shfl_sync(0xffffffffu, my_w.z, m), w3 = __shfl_sync(0xffffffffu, my_w.w, m);
-                            const float d0 = __shfl_sync(0xffffffffu, my_wd.x, m), d1 = __shfl_sync(0xffffffffu, my_wd.y, m);
-                            const float d2 = __shfl_sync(0xffffffffu, my_wd.z, m), d3 = __shfl_sync(0xffffffffu, my_wd.w, m);
-                            red[h][0] = fmaf(w0, C.x, fmaf(w1, C.y, fmaf(w2, C.z, w3 * C.w)));
-                            red[h][1] = fmaf(d0, C.x, fmaf(d1, C.y, fmaf(d2, C.z, d3 * C.w)));
-                        }
-                    }
-                    adj_pair_reduce(red, lane, grp * MS + 2 * pr, sum_g, sum_d);
+                const float2 v = unpack2(acc[t]);
+                const float m2 = v.x * v.x + v.y * v.y;
+                const float sc = m2 > 0.f ? ge * rsqrtf(m2) : 0.f;
+                acc[t] = pack2(sc * v.x, sc * v.y);
+                // n -> n + 1
+                if (--r_lo < 0) {
+                    r_lo += R;
+                    ++i_lo;
+                }
+                if (++r_hi == R) {
+                    r_hi = 0;
+                    ++i_hi;
                 }
             }
-            if (st == ngroups - 1) {
-                // beams of this tile are complete: turn them into G_b = G_env b / |b| on owned
-                // samples.  G_env[n] sums the bins i in [ceil((n - half)/R), floor((n + half)/R)]
-                // (tap j = n - R i + half); both ends advance incrementally with n.
-                __syncwarp();
-                const int R = args.R;
-                const int n_first = n_start + lane * T;
-                const int xo = n_first - half + R * reach * 4;  // > 0
-                int i_lo = (xo + R - 1) / R - reach * 4;           // ceil((n - half)/R)
-                int r_lo = (i_lo + reach * 4) * R - xo;            // R i_lo - (n - half), in [0, R)
-                const int yo = n_first + half + R * reach * 4;
-                int i_hi = yo / R - reach * 4;                     // floor((n + half)/R)
-                int r_hi = yo - (i_hi + reach * 4) * R;            // (n + half) - R i_hi, in [0, R)
+        }
+        // pass B: correlate G_b with the same rows, streamed again
+        for (int st = 0; st < ngroups && !failed; ++st, ++g) {
+            const int b = g % NS;
+            const uint32_t par = static_cast<uint32_t>((g / NS) & 1);
+            const bool ok = !*vabort && ptx::mbar_wait_hinted(&full[b], par, kAdjPolls, kAdjHintNs);
+            if (!__all_sync(0xffffffffu, ok)) {
+                failed = true;
+                break;
+            }
+#pragma unroll 1
+            for (int pr = 0; pr < MS / 2; ++pr) {
+                // both mics of the pair, then one joint reduction of their (value, slope) sums
+                float red[2][2];
 #pragma unroll
-                for (int t = 0; t < T; ++t) {
-                    const int n = n_first + t;
-                    float ge = 0.f;
-                    if (n >= own_lo && n < own_hi && n >= 0 && n < args.N) {
-                        int j = 2 * half - r_lo;  // tap of bin i_lo
-                        for (int i = i_lo; i <= i_hi; ++i, j -= R) ge = fmaf(gs[i - iseg0], hs[j], ge);
-                    }
-                    const float2 v = unpack2(acc[t]);
-                    const float m2 = v.x * v.x + v.y * v.y;
-                    const float sc = m2 > 0.f ? ge * rsqrtf(m2) : 0.f;
-                    acc[t] = pack2(sc * v.x, sc * v.y);
-                    // n -> n + 1
-                    if (--r_lo < 0) {
-                        r_lo += R;
-                        ++i_lo;
-                    }
-                    if (++r_hi == R) {
-                        r_hi = 0;
-                        ++i_hi;
+                for (int h = 0; h < 2; ++h) {
+                    const int mi = 2 * pr + h;
+                    red[h][0] = red[h][1] = 0.f;
+                    const int m = st * MS + mi;
+                    if (m < M) {
+                        const int J = __shfl_sync(0xffffffffu, my_shift, m);
+                        const int s0 = lane_base + J;
+                        const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
+                            stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
+                        const float4 C = (s0 & 1) ? adj_corr_mic<true>(acc, p) : adj_corr_mic<false>(acc, p);
+                        const float w0 = __shfl_sync(0xffffffffu, my_w.x, m), w1 = __shfl_sync(0xffffffffu, my_w.y, m);
+                        const float w2 = __shfl_sync(0xffffffffu, my_w.z, m), w3 = __shfl_sync(0xffffffffu, my_w.w, m);
+                        const float d0 = __shfl_sync(0xffffffffu, my_wd.x, m), d1 = __shfl_sync(0xffffffffu, my_wd.y, m);
+                        const float d2 = __shfl_sync(0xffffffffu, my_wd.z, m), d3 = __shfl_sync(0xffffffffu, my_wd.w, m);
+                        red[h][0] = fmaf(w0, C.x, fmaf(w1, C.y, fmaf(w2, C.z, w3 * C.w)));
+                        red[h][1] = fmaf(d0, C.x, fmaf(d1, C.y, fmaf(d2, C.z, d3 * C.w)));
                     }
                 }
+                adj_pair_reduce(red, lane, st * MS + 2 * pr, sum_g, sum_d);
             }
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&empty[b]);  // the producer may refill buffer b
