@@ -901,7 +901,8 @@ def run_fd_many(args, rank, world, local):
     B = args.batch
     cfgs = [synth.hemisphere(seed_scene=1 + 1000 * rank + i) for i in range(B)]
     cfg = cfgs[0]
-    plan = Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"], max_batch=B, path="fd")
+    plan = Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"], max_batch=B, path="fd",
+                fd_ifft=args.fd_ifft)
     x = torch.from_numpy(np.stack([c["x"] for c in cfgs])).to(dev)
     E = torch.empty((B, N_DIRS, plan.n_out), dtype=torch.float32, device=dev)
     flush = L2Flush(dev)
@@ -973,7 +974,8 @@ def run_hemisphere_batched(args, rank, world, local):
     B = args.batch
     cfgs = [synth.hemisphere(seed_scene=1 + 1000 * rank + i) for i in range(B)]
     cfg = cfgs[0]
-    plan = Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"], max_batch=B)
+    plan = Plan(cfg["mic_xyz"], cfg["fs"], cfg["chirp"], cfg["dirs"], cfg["n_samples"], max_batch=B,
+                fd_ifft=args.fd_ifft)
     h = plan.handle
     xs_host = np.stack([c["x"] for c in cfgs])
     x = torch.from_numpy(xs_host).to(dev)
@@ -1419,6 +1421,9 @@ def main():
                          "time-domain chain built the paper's way (cuFFT + per-sample DAS) vs the fused kernels; "
                          "stream: host-to-host streaming through a ring of pinned slots (throughput, latency)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--fd-ifft", default="auto", choices=["auto", "fft", "tc"],
+                    help="batched frequency-domain path: inverse transform as dense DFT stages on the tensor "
+                         "cores (tc), as FFTs on the FP32 pipe (fft), or the plan's choice (auto)")
     ap.add_argument("--bins", type=int, default=1200, help="fd_gemm: frequency bins (1200 = the full workload)")
     ap.add_argument("--batch", type=int, default=64,
                     help="hemisphere: measurements per step (1: per-measurement calls; >1: rtis_process_many, "

@@ -107,7 +107,18 @@ typedef struct rtis_options {
     int grid_mode;               /* with a forced layout: 0 or 1 = one CTA per tile, 2 = the CTAs
                                     resident at once looping over the tiles.  Every layout and grid
                                     gives the same results bit for bit (only the staging differs) */
+    int fd_ifft;                 /* inverse transform of rtis_process_many's frequency-domain path:
+                                    RTIS_FD_IFFT_AUTO (default: the faster form as measured on
+                                    GB300, today the FFT), RTIS_FD_IFFT_FFT (radix-16/32 FFTs
+                                    on the FP32 pipe), RTIS_FD_IFFT_TC (two dense DFT stages on the
+                                    tcgen05 tensor cores in FP32 as three BF16 products; needs
+                                    F = 32768, at most 4608 in-band bins and a low-pass of at most
+                                    127 taps, else rtis_plan_create returns RTIS_ERR_UNSUPPORTED) */
 } rtis_options;
+
+#define RTIS_FD_IFFT_AUTO 0
+#define RTIS_FD_IFFT_FFT 1
+#define RTIS_FD_IFFT_TC 2
 
 /* Fills *opt with the defaults listed above. */
 void rtis_options_default(rtis_options* opt);
@@ -132,6 +143,8 @@ typedef struct rtis_plan_info {
                                     one CTA per tile at [2v], with the resident persistent grid at
                                     [2v + 1]; 0 where not tried */
     float bb_layout_ms[16];      /* the same for the baseband beamformer (RTIS_PATH_BB) */
+    int fd_ifft;                 /* the inverse transform rtis_process_many's frequency-domain path
+                                    runs: RTIS_FD_IFFT_FFT or RTIS_FD_IFFT_TC (0 without max_batch) */
 } rtis_plan_info;
 
 /*

@@ -47,6 +47,7 @@ class rtis_options(C.Structure):
         ("td_layout", C.c_int),
         ("bb_layout", C.c_int),
         ("grid_mode", C.c_int),
+        ("fd_ifft", C.c_int),
     ]
 
 
@@ -59,6 +60,7 @@ class rtis_plan_info(C.Structure):
         ("td_variant", C.c_int), ("td_grid", C.c_int), ("td_tuned_ms", C.c_float),
         ("n_coarse", C.c_int), ("k_c", C.c_int), ("bb_variant", C.c_int), ("bb_grid", C.c_int),
         ("bb_tuned_ms", C.c_float), ("td_layout_ms", C.c_float * 16), ("bb_layout_ms", C.c_float * 16),
+        ("fd_ifft", C.c_int),
     ]
 
 

@@ -42,7 +42,7 @@ cudaError_t dev_alloc(T** ptr, size_t count, size_t* total) {
 void free_plan_buffers(Plan& p) {
     void* bufs[] = {p.d_mic, p.d_dirs, p.d_gain, p.d_delay, p.d_tw, p.d_C, p.d_h,
                     p.d_shift, p.d_wt, p.d_dphase, p.d_wraw, p.d_wder, p.d_adj, p.d_adj_red, p.d_Z, p.d_a, p.d_A, p.d_a16,
-                    p.d_X, p.d_Y, p.d_kbin, p.d_xmax, p.d_Zb, p.d_ab, p.d_status,
+                    p.d_X, p.d_Y, p.d_kbin, p.d_xmax, p.d_Zb, p.d_ab, p.d_fdtc, p.d_status,
                     p.d_bshift, p.d_bwt, p.d_brot, p.d_hb};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -248,6 +248,8 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: max_batch must be in [0, 64]");
     if (opt.precision == RTIS_PREC_BF16 && opt.path != RTIS_PATH_TD)
         return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: BF16 storage applies to the time-domain path only");
+    if (opt.fd_ifft < RTIS_FD_IFFT_AUTO || opt.fd_ifft > RTIS_FD_IFFT_TC)
+        return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: fd_ifft must be RTIS_FD_IFFT_AUTO, _FFT or _TC");
     if (opt.td_layout < 0 || opt.td_layout > rtis::kTdVariants || opt.bb_layout < 0 ||
         opt.bb_layout > rtis::kBbVariants || opt.grid_mode < 0 || opt.grid_mode > 2)
         return fail(RTIS_ERR_INVALID_ARG, "rtis_plan_create: td_layout, bb_layout or grid_mode out of range");
@@ -314,6 +316,17 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     if (rtis::td_smem_bytes(p) > 227 * 1024) {
         delete plan;
         return fail(RTIS_ERR_UNSUPPORTED, "rtis_plan_create: steering delays too large for the staged halo");
+    }
+    if (p.max_batch > 0) {
+        // the batched frequency-domain path's inverse transform: the FFT kernel unless the
+        // caller asks for the dense DFT stages on the tensor cores (which need F = 32768)
+        const bool tc_ok = rtis::fdtc_supported(p);
+        if (opt.fd_ifft == RTIS_FD_IFFT_TC && !tc_ok) {
+            delete plan;
+            return fail(RTIS_ERR_UNSUPPORTED,
+                        "rtis_plan_create: the tensor-core IFFT needs F = 32768, at most 4608 in-band bins and at most 127 low-pass taps");
+        }
+        p.fd_ifft = (opt.fd_ifft == RTIS_FD_IFFT_TC) ? RTIS_FD_IFFT_TC : RTIS_FD_IFFT_FFT;
     }
     if (opt.path == RTIS_PATH_FD && rtis::fdes_smem_bytes(p) > 227 * 1024) {
         delete plan;
@@ -431,6 +444,7 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         RTIS_ALLOC(p.d_xmax, static_cast<size_t>(n_mics))
         RTIS_ALLOC(p.d_Zb, static_cast<size_t>(p.max_batch) * n_mics * 2 * p.P)
         RTIS_ALLOC(p.d_ab, static_cast<size_t>(p.max_batch) * n_mics * n_samples)
+        if (p.fd_ifft == RTIS_FD_IFFT_TC) RTIS_ALLOC(p.d_fdtc, rtis::fdtc_const_bytes())
     }
     if (opt.path == RTIS_PATH_BB) {
         RTIS_ALLOC(p.d_bshift, static_cast<size_t>(n_dirs) * n_mics)
@@ -465,6 +479,11 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
     RTIS_UP(p.d_C, C.data(), p.Kb * sizeof(float2))
     RTIS_UP(p.d_h, h.data(), lpf_len * sizeof(float))
     if (!hb.empty()) RTIS_UP(p.d_hb, hb.data(), hb.size() * sizeof(float))
+    if (p.d_fdtc) {
+        std::vector<unsigned char> img;
+        rtis::fdtc_build_constants(p, img);
+        RTIS_UP(p.d_fdtc, img.data(), img.size())
+    }
 #undef RTIS_UP
     if (e == cudaSuccess) e = cudaMemset(p.d_status, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = rtis::launch_steering_table(p, 0);
@@ -579,6 +598,7 @@ rtis_status rtis_plan_get_info(const rtis_plan* plan, rtis_plan_info* info) {
         info->td_layout_ms[i] = p.td_variant_ms[i];
         info->bb_layout_ms[i] = p.bb_variant_ms[i];
     }
+    info->fd_ifft = p.max_batch > 0 ? p.fd_ifft : 0;
     return RTIS_OK;
 }
 
@@ -794,7 +814,10 @@ rtis_status rtis_process_many(rtis_plan* plan, const int16_t* d_in, int n, float
             ym = &ymap;
         }
         e = RTIS_TRACED(p, st, RTIS_KERNEL_FD_GEMM, rtis::launch_fd_gemm(g, p.d_X, p.d_Y, ym, st));
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && p.d_fdtc)
+            e = RTIS_TRACED(p, st, RTIS_KERNEL_FD_ENERGYSCAPE,
+                            rtis::launch_fd_energyscape_tc(p, p.d_fdtc, p.d_Y, n, d_out_fd, g.n_sm, st));
+        else if (e == cudaSuccess)
             e = RTIS_TRACED(p, st, RTIS_KERNEL_FD_ENERGYSCAPE,
                             rtis::launch_fd_energyscape_from_y(p, p.d_Y, n, d_out_fd, st));
     }

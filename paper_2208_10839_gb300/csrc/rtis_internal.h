@@ -89,6 +89,9 @@ struct Plan {
     float* d_xmax = nullptr;    // [M] per-channel max |X| bits for the GEMM scales
     float2* d_Zb = nullptr;     // [max_batch][M][2][P] half spectra, one set per measurement
     float2* d_ab = nullptr;     // [max_batch][M][N] analytic signals, one per measurement
+    unsigned char* d_fdtc = nullptr;  // the tensor-core IFFT's two DFT matrices (hi/lo BF16), or null
+    int fd_ifft = 0;            // RTIS_FD_IFFT_FFT or RTIS_FD_IFFT_TC (batched frequency-domain path)
+    int n_sm = 0;               // multiprocessors of the plan's device
     std::vector<CUtensorMap> tmap_ab;  // TMA views of the d_ab rows (time-domain beamformer)
     unsigned* d_status = nullptr;
     size_t bytes = 0;
@@ -216,6 +219,13 @@ cudaError_t launch_fd_energyscape(const Plan& p, const float2* d_A, float* d_out
 // energyscapes of T measurements from their steered spectra Y [D][Kb][T]; out [T][D][n_out]
 cudaError_t launch_fd_energyscape_from_y(const Plan& p, const float2* d_Y, int T, float* d_out, cudaStream_t st);
 size_t fdes_smem_bytes(const Plan& p);
+// the same from Y with the inverse transform as two dense DFT stages on the tensor
+// cores (kernels_fdtc.cu); d_W holds fdtc_build_constants' image, d_out is zeroed first
+bool fdtc_supported(const Plan& p);
+size_t fdtc_const_bytes();
+void fdtc_build_constants(const Plan& p, std::vector<unsigned char>& img);
+cudaError_t launch_fd_energyscape_tc(const Plan& p, const unsigned char* d_W, const float2* d_Y, int T, float* d_out,
+                                     int n_sm, cudaStream_t st);
 
 // persistent multi-sensor time-domain beamformer
 constexpr int kTdMaxSensors = 16;

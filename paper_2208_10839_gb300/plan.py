@@ -19,7 +19,7 @@ class Plan:
 
     def __init__(self, mic_xyz, fs, chirp, directions, n_samples, *, c=343.0, decim=10, lpf_taps=None,
                  band=(20e3, 80e3), path="td", precision="fp32", max_delay_s=10e-6, position_slack_m=0.01,
-                 max_batch=0, td_layout=None, bb_layout=None, grid="tile"):
+                 max_batch=0, td_layout=None, bb_layout=None, grid="tile", fd_ifft="auto"):
         import torch  # device memory and streams only
         self._torch = torch
         o = nat.default_options()
@@ -41,6 +41,9 @@ class Plan:
         o.td_layout = 0 if td_layout is None else int(td_layout) + 1
         o.bb_layout = 0 if bb_layout is None else int(bb_layout) + 1
         o.grid_mode = {"tile": 1, "persistent": 2}[grid]
+        # process_many's frequency-domain inverse transform: "auto" (the faster form, today the FFT),
+        # "fft" (FFT kernel on the FP32 pipe) or "tc" (dense DFT stages on the tensor cores, or fail)
+        o.fd_ifft = {"auto": 0, "fft": 1, "tc": 2}[fd_ifft]
         self.handle = nat.rtis_plan_create(mic_xyz, fs, chirp, directions, n_samples, o)
         self.info_path = path
         self.info = nat.rtis_plan_get_info(self.handle)
