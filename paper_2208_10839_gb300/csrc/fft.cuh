@@ -88,7 +88,7 @@ __device__ __forceinline__ constexpr int bitrev(int k) {
 // butterflies, then a static bit-reversal reorder.  NZ < R: only the first NZ
 // inputs can be nonzero, and the first stage skips the sums with the zeros
 // (v[i + R/2] = 0 gives v[i] = a and v[i + R/2] = rot(a); both zero gives zeros).
-template <int R, bool INV, int NZ = R>
+template <int R, bool INV, int NZ = R, bool LOW = false>
 __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
 #pragma unroll
     for (int len = R; len >= 2; len >>= 1) {
@@ -108,7 +108,9 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
                     continue;
                 }
                 v[s + i] = cadd(a, b);
-                v[s + i + half] = rot32<INV>(csub(a, b), i * (32 / len));
+                // LOW: only the outputs k < R/2 are wanted; they sit at the even positions
+                // before the bit reversal, so the last stage's differences are not formed
+                if (!(LOW && len == 2)) v[s + i + half] = rot32<INV>(csub(a, b), i * (32 / len));
             }
         }
     }

@@ -47,6 +47,7 @@ struct FdesArgs {
     int T;
     unsigned* status;
     int M, D, N, F, k_lo, Kb, R, lpf_len, n_out;
+    int pf_ahead;         // from Y: blocks resident at once (the block pf_ahead later starts next)
 };
 
 // fractional part of k * (hi + lo) in cycles, compensated FP32 (k an exact integer)
@@ -136,14 +137,17 @@ __device__ __forceinline__ void fdes_gemv_chunk(const FdesArgs& a, const float2*
 // Ns = product of the earlier radices, NT threads.  The last pass (Ns = P/R) writes
 // env[p] = |b(4p + q)| for p < e_end (the samples n < N of this phase) and
 // zeros for e_end <= p < p_fill (the low-pass reads past the record's end),
-// instead of the complex values.
-template <int LOGP, int R, int NS, bool LAST, int NT>
+// instead of the complex values.  HALF (last pass, e_end <= P/2): the outputs
+// r >= R/2 lie past the record, so they are neither formed nor measured, only
+// the zeros below p_fill are written.
+template <int LOGP, int R, int NS, bool LAST, int NT, bool HALF = false>
 __device__ __forceinline__ void fdes_pass(float2* buf, float* env, const float2* ct, int e_end, int p_fill) {
     constexpr int P = 1 << LOGP;
     constexpr int NB = P / R;
     constexpr int BPT = (NB + NT - 1) / NT;
     static_assert(R == 16 || R == 32, "radix 16 or 32");
     static_assert(!LAST || NS == NB, "the last pass has Ns = P/R");
+    static_assert(!HALF || LAST, "output pruning applies to the last pass");
     float2 v[BPT][R];
     // with NB a multiple of 32, fpad(j + r NB) = fpad(j) + r (NB + NB/32) for j < NB
     constexpr int NBP = NB + NB / 32;
@@ -214,7 +218,7 @@ __device__ __forceinline__ void fdes_pass(float2* buf, float* env, const float2*
                     }
                 }
             }
-            dft_reg<R, true>(v[b]);
+            dft_reg<R, true, R, HALF>(v[b]);
             if constexpr (!LAST) {
                 const int base = (j - k) * R + k;
                 if constexpr (NS % 32 == 0) {  // fpad(base + r NS) = fpad(base) + r (NS + NS/32)
@@ -229,8 +233,12 @@ __device__ __forceinline__ void fdes_pass(float2* buf, float* env, const float2*
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int p = k + r * NS;
-                    const float mag = magnitude_from_norm(v[b][r].x * v[b][r].x + v[b][r].y * v[b][r].y);
-                    if (p < p_fill) env[p] = p < e_end ? mag : 0.f;
+                    if (HALF && r >= R / 2) {
+                        if (p < p_fill) env[p] = 0.f;
+                    } else {
+                        const float mag = magnitude_from_norm(v[b][r].x * v[b][r].x + v[b][r].y * v[b][r].y);
+                        if (p < p_fill) env[p] = p < e_end ? mag : 0.f;
+                    }
                 }
             }
         }
@@ -246,7 +254,7 @@ __device__ __forceinline__ void fdes_pass(float2* buf, float* env, const float2*
 // bin of a thread (i = t + NT m) has the same residue (R i - half) mod 4, so per
 // phase the thread's low-pass taps are one comb j0 + 4 s, held in registers, and
 // its outputs accumulate in registers across the four phases.
-template <int LOGP, bool FROM_Y, int NZ, bool FOLD, int NT>
+template <int LOGP, bool FROM_Y, int NZ, bool FOLD, int NT, bool HALF>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fd_energyscape_kernel(const FdesArgs a) {
     constexpr int P = 1 << LOGP;
     extern __shared__ __align__(16) unsigned char sm[];
@@ -286,6 +294,16 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fd_energyscape_kernel(c
     const SplitTwiddles tws{twhi, twlo};
 
     if constexpr (FROM_Y) {
+        {  // bring the spectrum of the block that starts about one block lifetime later into L2
+           // (one block of each four neighbouring measurements, which share the 32-byte sectors)
+            const int nbk = static_cast<int>(blockIdx.x) + a.pf_ahead;
+            if (a.pf_ahead > 0 && nbk < static_cast<int>(gridDim.x)) {
+                const int d2 = nbk / a.T, t2 = nbk - d2 * a.T;
+                if ((t2 & 3) == 0)
+                    for (int kp = tid; kp < Kb; kp += NT)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Y + (static_cast<size_t>(d2) * Kb + kp) * a.T + t2));
+            }
+        }
         for (int kp = tid; kp < nb; kp += NT)
             B[kp] = kp < Kb ? __ldg(a.Y + (static_cast<size_t>(d) * Kb + kp) * a.T + t_meas) : make_float2(0.f, 0.f);
         __syncthreads();
@@ -353,7 +371,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fd_energyscape_kernel(c
         const int e_end = (a.N - q + 3) >> 2;  // env entries of this phase with n = 4p + q < N
         // the rest of P: NT = 16 x (NT/16) points per first-pass output column
         fdes_pass<LOGP, NT / 16, R0, false, NT>(fbuf, env, ct, e_end, 0);
-        fdes_pass<LOGP, 16, (NT / 16) * R0, true, NT>(fbuf, env, ct, e_end, e_end + 4 * kFoldTaps + 4);
+        fdes_pass<LOGP, 16, (NT / 16) * R0, true, NT, HALF>(fbuf, env, ct, e_end, e_end + 4 * kFoldTaps + 4);
         if constexpr (FOLD) {
             // taps j = j0 + 4 s read env[(R i - half + j0 - q) / 4 + s]; entries past the record's
             // end were written as zeros, entries before its start are skipped below
@@ -416,13 +434,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fd_energyscape_kernel(c
     }
 }
 
-template <int LOGP, bool FROM_Y, int NZ, bool FOLD>
+template <int LOGP, bool FROM_Y, int NZ, bool FOLD, bool HALF = false>
 cudaError_t fdes_launch_t(const Plan& p, const float2* d_A, const float2* d_Y, int T, float* d_out, cudaStream_t st) {
     constexpr int NT = fdes_threads(LOGP);
     constexpr int R0 = (1 << LOGP) / NT;
     const int nb = NZ < R0 ? NZ * NT : p.Kb;
     const size_t sm = static_cast<size_t>(fdes_layout(1 << LOGP, p.F, nb, p.n_out, p.lpf_len, p.M).bytes);
-    cudaError_t e = cudaFuncSetAttribute(fd_energyscape_kernel<LOGP, FROM_Y, NZ, FOLD, NT>,
+    cudaError_t e = cudaFuncSetAttribute(fd_energyscape_kernel<LOGP, FROM_Y, NZ, FOLD, NT, HALF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
     if (e != cudaSuccess) return e;
     FdesArgs a;
@@ -444,13 +462,15 @@ cudaError_t fdes_launch_t(const Plan& p, const float2* d_A, const float2* d_Y, i
     a.lpf_len = p.lpf_len;
     a.n_out = p.n_out;
     a.status = p.d_status;
-    fd_energyscape_kernel<LOGP, FROM_Y, NZ, FOLD, NT><<<p.D * (FROM_Y ? T : 1), NT, sm, st>>>(a);
+    a.pf_ahead = FROM_Y ? std::max(1, p.n_sm) * (NT == 256 ? 2 : 1) : 0;
+    fd_energyscape_kernel<LOGP, FROM_Y, NZ, FOLD, NT, HALF><<<p.D * (FROM_Y ? T : 1), NT, sm, st>>>(a);
     return cudaGetLastError();
 }
 
 // The common case (the band fills at most R0/2 + 2 of the first pass's NT-bin slots,
 // at most 8 NT output bins, a low-pass of at most 44 taps) runs the pruned first pass
-// and the register fold; anything else the general kernel.
+// and the register fold, and when N <= F/2 the last pass pruned to its low half;
+// anything else the general kernel.
 template <int LOGP, bool FROM_Y>
 cudaError_t fdes_launch_pick(const Plan& p, const float2* d_A, const float2* d_Y, int T, float* d_out,
                              cudaStream_t st) {
@@ -459,6 +479,9 @@ cudaError_t fdes_launch_pick(const Plan& p, const float2* d_A, const float2* d_Y
     constexpr int NZH = R0 / 2 + 2 < R0 ? R0 / 2 + 2 : R0;
     const int nz = (p.Kb + NT - 1) / NT;
     const bool fold = p.n_out <= kFoldOut * NT && (p.lpf_len + 3) / 4 <= kFoldTaps;
+    // every sample n < N of a phase has p < P/2: the last pass forms only the low half
+    const bool half = ((p.N + 3) >> 2) <= (1 << LOGP) / 2;
+    if (nz <= NZH && fold && half) return fdes_launch_t<LOGP, FROM_Y, NZH, true, true>(p, d_A, d_Y, T, d_out, st);
     if (nz <= NZH && fold) return fdes_launch_t<LOGP, FROM_Y, NZH, true>(p, d_A, d_Y, T, d_out, st);
     return fdes_launch_t<LOGP, FROM_Y, R0, false>(p, d_A, d_Y, T, d_out, st);
 }

@@ -504,6 +504,11 @@ rtis_status rtis_plan_create(rtis_plan** out, const float* mic_xyz, int n_mics, 
         delete plan;
         return fail(RTIS_ERR_CUDA, "rtis_plan_create: " + err);
     }
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&p.n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) p.n_sm = 1;
+    }
     unsigned bits = 0;
     cudaMemcpy(&bits, p.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (!(bits & RTIS_DEV_DELAY_RANGE)) {
