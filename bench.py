@@ -1094,6 +1094,7 @@ def run_hemisphere_batched(args, rank, world, local):
     t_e2e = ee0.elapsed_time(ee1) / 1e3
     assert torch.equal(Eh_td[0], Eh_td[1]) and torch.equal(Eh_fd[0], Eh_fd[1])
     assert plan.sync() == 0
+    link = pinned_link_gbs(cs, xh, xd[1], Ed_td[0], Eh_td[0])
 
     if world > 1:
         t_total, t_e2e = max_over_ranks([t_total, t_e2e], dev)
@@ -1151,7 +1152,8 @@ def run_hemisphere_batched(args, rank, world, local):
                    "parallelism": f"{world} independent replica(s), {B} measurements per rank per step"},
         "e2e": {"value": e2e_value, "unit": "energyscapes/s", "h2d_bytes_per_step": int(x.numel() * 2),
                 "d2h_bytes_per_step": int(E_td.numel() * 4 + E_fd.numel() * 4), "calls": "rtis_process_many",
-                "pipelining": "H2D and D2H on their own streams, two buffer sets; copies overlap the next step"},
+                "pipelining": "H2D and D2H on their own streams, two buffer sets; copies overlap the next step",
+                "pinned_link": link},
         "gpu_launches": args.steps * (2 + (B + 15) // 16 + 3),
         "kernels_ms": {"td_path_per_measurement": bk["td_path"] / B,
                        "fd_path_per_measurement": bk["fd_path"] / B,
@@ -1191,6 +1193,26 @@ def run_hemisphere_batched(args, rank, world, local):
 # precision and batching legs of the default bench line: each one short, each with its
 # own CUDA-event time, roofline fraction and error against the FP64 oracle
 # ---------------------------------------------------------------------------
+def pinned_link_gbs(stream, h_in, d_in, d_out, h_out, reps=3):
+    """Bandwidth of this box's pinned host copies, measured alone on one stream with CUDA
+    events (the host side of the end-to-end figure): H2D of the input batch, D2H of one
+    energyscape batch."""
+    import torch
+    out = {}
+    for name, dst, src in (("h2d_gbs", d_in, h_in), ("d2h_gbs", h_out, d_out)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            dst.copy_(src, non_blocking=True)
+            e0.record(stream)
+            for _ in range(reps):
+                dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+        e1.synchronize()
+        out[name] = reps * src.numel() * src.element_size() / (e0.elapsed_time(e1) / 1e3) / 1e9
+    out["how"] = "pinned host buffers, one stream, CUDA events, best effort (other copies idle)"
+    return out
+
+
 def _timed(fn, flush, stream, reps):
     """CUDA-event milliseconds of fn() per rep, L2 flushed before each (outside the events)."""
     import torch
