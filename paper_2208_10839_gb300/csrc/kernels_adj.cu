@@ -100,27 +100,33 @@ __device__ __forceinline__ float4 adj_corr_mic(const uint64_t (&gb)[kTdOutPerThr
     return make_float4(r[0], r[1], r[2], r[3]);
 }
 
-// Pass-B reduction of one pair of mics (m0, m0 + 1): the (value, slope) sums of both,
-// reduce-scattered over the warp (after the xor-16 and xor-8 exchanges lane bits (4, 3)
-// select (mic, value/slope); then a plain sum); lanes m0 and m0 + 1 receive their mic's
-// totals.
-__device__ __forceinline__ void adj_pair_reduce(const float (&red)[2][2], int lane, int m0, float& sum_g,
-                                                float& sum_d) {
-    const bool b16 = lane & 16, b8 = lane & 8;
-    float k0 = b16 ? red[1][0] : red[0][0], k1 = b16 ? red[1][1] : red[0][1];
-    const float s0 = b16 ? red[0][0] : red[1][0], s1 = b16 ? red[0][1] : red[1][1];
-    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
-    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
-    float k = b8 ? k1 : k0;
-    k += __shfl_xor_sync(0xffffffffu, b8 ? k0 : k1, 8);
-    k += __shfl_xor_sync(0xffffffffu, k, 4);
-    k += __shfl_xor_sync(0xffffffffu, k, 2);
-    k += __shfl_xor_sync(0xffffffffu, k, 1);
-    const int src = (lane == m0 + 1) ? 16 : 0;
-    const float tg = __shfl_sync(0xffffffffu, k, src), td = __shfl_sync(0xffffffffu, k, src + 8);
+// Pass-B reduction of one pair of mics (m0, m0 + 1) from the raw tap correlations: the
+// eight sums C_q of the two mics are reduce-scattered over the warp (after the xor-16, 8
+// and 4 exchanges lane bits (4, 3, 2) select (mic, q); then a plain sum), lane m0 + h
+// gathers its mic's four totals and applies its own value and slope weights.
+__device__ __forceinline__ void adj_pair_reduce_c(const float4& c0, const float4& c1, int lane, int m0,
+                                                  const float4& w, const float4& wd, float& sum_g, float& sum_d) {
+    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+    float k[4];
+    {
+        const float4 keep = b16 ? c1 : c0, send = b16 ? c0 : c1;
+        k[0] = keep.x + __shfl_xor_sync(0xffffffffu, send.x, 16);
+        k[1] = keep.y + __shfl_xor_sync(0xffffffffu, send.y, 16);
+        k[2] = keep.z + __shfl_xor_sync(0xffffffffu, send.z, 16);
+        k[3] = keep.w + __shfl_xor_sync(0xffffffffu, send.w, 16);
+    }
+    const float k0 = (b8 ? k[2] : k[0]) + __shfl_xor_sync(0xffffffffu, b8 ? k[0] : k[2], 8);
+    const float k1 = (b8 ? k[3] : k[1]) + __shfl_xor_sync(0xffffffffu, b8 ? k[1] : k[3], 8);
+    float t = (b4 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, b4 ? k0 : k1, 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    // lane 16 h + 4 q holds C_q of mic m0 + h
+    const int base = (lane == m0 + 1) ? 16 : 0;
+    const float C0 = __shfl_sync(0xffffffffu, t, base), C1 = __shfl_sync(0xffffffffu, t, base + 4);
+    const float C2 = __shfl_sync(0xffffffffu, t, base + 8), C3 = __shfl_sync(0xffffffffu, t, base + 12);
     if (lane == m0 || lane == m0 + 1) {
-        sum_g = tg;
-        sum_d = td;
+        sum_g = fmaf(w.x, C0, fmaf(w.y, C1, fmaf(w.z, C2, w.w * C3)));
+        sum_d = fmaf(wd.x, C0, fmaf(wd.y, C1, fmaf(wd.z, C2, wd.w * C3)));
     }
 }
 
@@ -344,28 +350,23 @@ __global__ void __launch_bounds__(kTdThreads, 1)
             }
 #pragma unroll 1
             for (int pr = 0; pr < MS / 2; ++pr) {
-                // both mics of the pair, then one joint reduction of their (value, slope) sums
-                float red[2][2];
+                // both mics' tap correlations, then one joint reduction; each owner lane weights
+                // its own mic's totals
+                float4 cc[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int mi = 2 * pr + h;
-                    red[h][0] = red[h][1] = 0.f;
+                    cc[h] = make_float4(0.f, 0.f, 0.f, 0.f);
                     const int m = st * MS + mi;
                     if (m < M) {
                         const int J = __shfl_sync(0xffffffffu, my_shift, m);
                         const int s0 = lane_base + J;
                         const ulonglong2* p = reinterpret_cast<const ulonglong2*>(
                             stage + static_cast<size_t>(b * MS + mi) * row + (s0 & ~1));
-                        const float4 C = (s0 & 1) ? adj_corr_mic<true>(acc, p) : adj_corr_mic<false>(acc, p);
-                        const float w0 = __shfl_sync(0xffffffffu, my_w.x, m), w1 = __shfl_sync(0xffffffffu, my_w.y, m);
-                        const float w2 = __shfl_sync(0xffffffffu, my_w.z, m), w3 = __shfl_sync(0xffffffffu, my_w.w, m);
-                        const float d0 = __shfl_sync(0xffffffffu, my_wd.x, m), d1 = __shfl_sync(0xffffffffu, my_wd.y, m);
-                        const float d2 = __shfl_sync(0xffffffffu, my_wd.z, m), d3 = __shfl_sync(0xffffffffu, my_wd.w, m);
-                        red[h][0] = fmaf(w0, C.x, fmaf(w1, C.y, fmaf(w2, C.z, w3 * C.w)));
-                        red[h][1] = fmaf(d0, C.x, fmaf(d1, C.y, fmaf(d2, C.z, d3 * C.w)));
+                        cc[h] = (s0 & 1) ? adj_corr_mic<true>(acc, p) : adj_corr_mic<false>(acc, p);
                     }
                 }
-                adj_pair_reduce(red, lane, st * MS + 2 * pr, sum_g, sum_d);
+                adj_pair_reduce_c(cc[0], cc[1], lane, st * MS + 2 * pr, my_w, my_wd, sum_g, sum_d);
             }
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&empty[b]);  // the producer may refill buffer b
