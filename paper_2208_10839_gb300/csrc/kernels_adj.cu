@@ -137,7 +137,13 @@ __device__ __forceinline__ void adj_pair_reduce_c(const float4& c0, const float4
 // recomputes the beams, pass B correlates G_b with the same rows).  Every direction
 // warp runs every loop (a direction past the set's end has zero weights and cotangent)
 // and writes its partials only for a real direction.
-template <int MS, int NS>
+// FASTG: R = 10 and the 41-tap low-pass (30 samples per lane = 3 bins), so the transposed
+// low-pass of a lane's samples reads 5 cotangent bins per run of 10 samples with taps fixed
+// at compile time.
+constexpr int kAdjFastR = 10, kAdjFastTaps = 41;
+static_assert(kTdOutPerThread == 3 * kAdjFastR, "the fast G_b transform assumes 30 samples per lane");
+
+template <int MS, int NS, bool FASTG>
 __global__ void __launch_bounds__(kTdThreads, 1)
     td_adjoint_kernel(const __grid_constant__ CUtensorMap tmap, const AdjArgs args) {
     constexpr int NW = kTdWarps;
@@ -310,32 +316,70 @@ __global__ void __launch_bounds__(kTdThreads, 1)
             __syncwarp();
             const int R = args.R;
             const int n_first = n_start + lane * T;
-            const int xo = n_first - half + R * reach * 4;  // > 0
-            int i_lo = (xo + R - 1) / R - reach * 4;           // ceil((n - half)/R)
-            int r_lo = (i_lo + reach * 4) * R - xo;            // R i_lo - (n - half), in [0, R)
-            const int yo = n_first + half + R * reach * 4;
-            int i_hi = yo / R - reach * 4;                     // floor((n + half)/R)
-            int r_hi = yo - (i_hi + reach * 4) * R;            // (n + half) - R i_hi, in [0, R)
+            if constexpr (FASTG) {
+                // n = n_first + t = R (i0 + 3 lane) - half + t: in the run r of samples t = 10 r + u,
+                // bin i0 + 3 lane + r + e - 4 reaches sample t with tap u + 40 - 10 e (e = 0 only
+                // for u = 0), so five bins are live at a time; the bins are summed in increasing
+                // order, as the general loop below does
+                const float* gl = gs + 3 * lane - 4 + reach;  // lane 0's gl[0] is never used
+                float g0 = lane > 0 ? gl[0] : 0.f, g1 = gl[1], g2 = gl[2], g3 = gl[3], g4 = gl[4];
 #pragma unroll
-            for (int t = 0; t < T; ++t) {
-                const int n = n_first + t;
-                float ge = 0.f;
-                if (n >= own_lo && n < own_hi && n >= 0 && n < args.N) {
-                    int j = 2 * half - r_lo;  // tap of bin i_lo
-                    for (int i = i_lo; i <= i_hi; ++i, j -= R) ge = fmaf(gs[i - iseg0], hs[j], ge);
+                for (int r = 0; r < 3; ++r) {
+                    if (r > 0) {
+                        g0 = g1;
+                        g1 = g2;
+                        g2 = g3;
+                        g3 = g4;
+                        g4 = gl[r + 4];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 10; ++u) {
+                        // keep each sample's tap loads next to their use (hoisted, the taps would
+                        // crowd out the beams' registers)
+                        asm volatile("" ::: "memory");
+                        const int t = 10 * r + u;
+                        const int n = n_first + t;
+                        float ge = 0.f;
+                        if (u == 0) ge = fmaf(g0, hs[40], ge);
+                        ge = fmaf(g1, hs[u + 30], ge);
+                        ge = fmaf(g2, hs[u + 20], ge);
+                        ge = fmaf(g3, hs[u + 10], ge);
+                        ge = fmaf(g4, hs[u], ge);
+                        if (!(n >= own_lo && n < own_hi && n < args.N)) ge = 0.f;
+                        const float2 v = unpack2(acc[t]);
+                        const float m2 = v.x * v.x + v.y * v.y;
+                        const float sc = m2 > 0.f ? ge * rsqrtf(m2) : 0.f;
+                        acc[t] = pack2(sc * v.x, sc * v.y);
+                    }
                 }
-                const float2 v = unpack2(acc[t]);
-                const float m2 = v.x * v.x + v.y * v.y;
-                const float sc = m2 > 0.f ? ge * rsqrtf(m2) : 0.f;
-                acc[t] = pack2(sc * v.x, sc * v.y);
-                // n -> n + 1
-                if (--r_lo < 0) {
-                    r_lo += R;
-                    ++i_lo;
-                }
-                if (++r_hi == R) {
-                    r_hi = 0;
-                    ++i_hi;
+            } else {
+                const int xo = n_first - half + R * reach * 4;  // > 0
+                int i_lo = (xo + R - 1) / R - reach * 4;           // ceil((n - half)/R)
+                int r_lo = (i_lo + reach * 4) * R - xo;            // R i_lo - (n - half), in [0, R)
+                const int yo = n_first + half + R * reach * 4;
+                int i_hi = yo / R - reach * 4;                     // floor((n + half)/R)
+                int r_hi = yo - (i_hi + reach * 4) * R;            // (n + half) - R i_hi, in [0, R)
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const int n = n_first + t;
+                    float ge = 0.f;
+                    if (n >= own_lo && n < own_hi && n >= 0 && n < args.N) {
+                        int j = 2 * half - r_lo;  // tap of bin i_lo
+                        for (int i = i_lo; i <= i_hi; ++i, j -= R) ge = fmaf(gs[i - iseg0], hs[j], ge);
+                    }
+                    const float2 v = unpack2(acc[t]);
+                    const float m2 = v.x * v.x + v.y * v.y;
+                    const float sc = m2 > 0.f ? ge * rsqrtf(m2) : 0.f;
+                    acc[t] = pack2(sc * v.x, sc * v.y);
+                    // n -> n + 1
+                    if (--r_lo < 0) {
+                        r_lo += R;
+                        ++i_lo;
+                    }
+                    if (++r_hi == R) {
+                        r_hi = 0;
+                        ++i_hi;
+                    }
                 }
             }
         }
@@ -511,15 +555,16 @@ cudaError_t launch_td_adjoint(const Plan& p, const float* d_grad_out, float* d_g
     a.bins_per_tile = p.td_bins_per_tile;
     a.seg = adj_seg(p);
     const size_t smem = adj_smem_bytes(p);
-    cudaError_t e = cudaFuncSetAttribute(td_adjoint_kernel<kAdjMS, kAdjNS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    const bool fastg = p.R == kAdjFastR && p.lpf_len == kAdjFastTaps;
+    auto kern = fastg ? td_adjoint_kernel<kAdjMS, kAdjNS, true> : td_adjoint_kernel<kAdjMS, kAdjNS, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int n_sm = 1, dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 1;
     const int n_tiles = (p.n_out + p.td_bins_per_tile - 1) / p.td_bins_per_tile;
     const int total = ((p.D + kTdWarps - 1) / kTdWarps) * n_tiles;
-    td_adjoint_kernel<kAdjMS, kAdjNS><<<std::min(total, n_sm), kTdThreads, smem, st>>>(p.tmap_a, a);
+    kern<<<std::min(total, n_sm), kTdThreads, smem, st>>>(p.tmap_a, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     adj_reduce1_kernel<<<dim3(p.M, kAdjRedBlocks), kAdjRedThreads, 0, st>>>(p.d_adj, p.d_dirs, p.M, p.D, n_tiles,
