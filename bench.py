@@ -1057,11 +1057,18 @@ def run_hemisphere_batched(args, rank, world, local):
     for e_ in ev_done + ev_out + ev_out2:
         e_.record(ks)
 
-    def e2e_step(i):
+    copy_ev = []  # per timed e2e step: event pairs around its H2D and its two D2H copies
+
+    def e2e_step(i, timed=False):
         b = i & 1
+        ce = [torch.cuda.Event(enable_timing=True) for _ in range(6)] if timed else None
         hs.wait_event(ev_done[b])
         with torch.cuda.stream(hs):
+            if ce:
+                ce[0].record(hs)
             xd[b].copy_(xh, non_blocking=True)
+            if ce:
+                ce[1].record(hs)
         ev_in[b].record(hs)
         ks.wait_event(ev_in[b])
         ks.wait_event(ev_out[b])
@@ -1071,11 +1078,21 @@ def run_hemisphere_batched(args, rank, world, local):
         cs.wait_event(ev_done[b])
         cs2.wait_event(ev_done[b])
         with torch.cuda.stream(cs):
+            if ce:
+                ce[2].record(cs)
             Eh_td[b].copy_(Ed_td[b], non_blocking=True)
+            if ce:
+                ce[3].record(cs)
         with torch.cuda.stream(cs2):
+            if ce:
+                ce[4].record(cs2)
             Eh_fd[b].copy_(Ed_fd[b], non_blocking=True)
+            if ce:
+                ce[5].record(cs2)
         ev_out[b].record(cs)
         ev_out2[b].record(cs2)
+        if ce:
+            copy_ev.append(ce)
 
     for i in range(2):
         e2e_step(i)
@@ -1086,7 +1103,7 @@ def run_hemisphere_batched(args, rank, world, local):
     for c in (hs, cs, cs2):
         c.wait_event(ee0)
     for i in range(e2e_steps):
-        e2e_step(i)
+        e2e_step(i, timed=True)
     for e_ in ev_out + ev_out2:
         ks.wait_event(e_)
     ee1.record(ks)
@@ -1095,6 +1112,11 @@ def run_hemisphere_batched(args, rank, world, local):
     assert torch.equal(Eh_td[0], Eh_td[1]) and torch.equal(Eh_fd[0], Eh_fd[1])
     assert plan.sync() == 0
     link = pinned_link_gbs(cs, xh, xd[1], Ed_td[0], Eh_td[0])
+    # the same copies' durations inside the loop, where they overlap compute and each other
+    link["in_loop_ms_per_step"] = {
+        name: statistics.median(ce[a].elapsed_time(ce[a + 1]) for ce in copy_ev)
+        for name, a in (("h2d", 0), ("d2h_td", 2), ("d2h_fd", 4))}
+    link["e2e_ms_per_step"] = 1e3 * t_e2e / e2e_steps
 
     if world > 1:
         t_total, t_e2e = max_over_ranks([t_total, t_e2e], dev)
