@@ -35,6 +35,12 @@ if ROOT not in sys.path:
 
 import numpy as np
 
+# The end-to-end loop runs compute, H2D and two D2H streams at once.  With the default 8
+# hardware work queues streams can share a queue, and then a step's kernels wait behind the
+# previous step's D2H copy (measured: 51.4 ms per step with copies of 9.4 ms beside 39.6 ms of
+# compute); 32 queues keep the four streams apart.  Read when CUDA starts, so set it first.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 N_SAMPLES, N_DIRS, N_MICS = 16384, 2048, 32
 METRIC = "energyscapes/s at 32ch x 16384 samples x 2048 dirs; error vs FP64 oracle"
 WORKLOAD = "hemisphere: 32 mics (12 cm square, seeded), 16384 samples @ 450 kHz, 2048 Fibonacci half-sphere dirs, " \
@@ -44,13 +50,13 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each beamformer (ncu capture of this
 # workload, see profiles/); set to None whenever that kernel changes until it is re-captured
 TD_TRAFFIC_BYTES = 5552896
-FD_TRAFFIC_BYTES = 1790000  # ncu prints 1.79 MB read, 0 written
+FD_TRAFFIC_BYTES = None  # the per-direction kernel's last pass changed since its capture (1.79 MB then)
 # bb_beamform_kernel on the hemisphere workload (the <4, 5> layout; z and the tables, E stays in L2)
 BB_TRAFFIC_BYTES = 2921472
 # td_adjoint_kernel on the calibration workload (32 x 16384 x 2048)
-ADJ_TRAFFIC_BYTES = 20115456
-# fd_gemm_kernel<BF16> captured at 400 bins (DRAM read + write), per bin; X and Y both grow with the bins
-FD_GEMM_TRAFFIC_PER_BIN = (13952256 + 358419200) / 400
+ADJ_TRAFFIC_BYTES = 20026112 + 44800
+# fd_gemm_kernel_ws<BF16> captured at 400 bins (DRAM read + write), per bin; X and Y both grow with the bins
+FD_GEMM_TRAFFIC_PER_BIN = (13974784 + 358491648) / 400
 N_REF_DIRS = 16   # directions per step of the reference arm (the FP64 oracle)
 
 
@@ -1057,53 +1063,73 @@ def run_hemisphere_batched(args, rank, world, local):
     for e_ in ev_done + ev_out + ev_out2:
         e_.record(ks)
 
-    copy_ev = []  # per timed e2e step: event pairs around its H2D and its two D2H copies
+    copy_ev = []  # per timed e2e step: events around its compute and its two D2H copies
+    h2d_ev = []   # per timed e2e step: events around its H2D
 
-    def e2e_step(i, timed=False):
+    def h2d(i, timed):
+        # step i's input into buffer i & 1, once the compute that last read that buffer is done
+        b = i & 1
+        hs.wait_event(ev_done[b])
+        e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) if timed else None
+        with torch.cuda.stream(hs):
+            if e:
+                e[0].record(hs)
+            xd[b].copy_(xh, non_blocking=True)
+            if e:
+                e[1].record(hs)
+        ev_in[b].record(hs)
+        if e:
+            h2d_ev.append(e)
+
+    def e2e_step(i, n, timed):
+        # step i: the next step's H2D is queued before this step's D2H copies, which wait for
+        # this step's compute; the copy engines run their queues in order, so queued behind
+        # them the next input would hold up the next step's compute
         b = i & 1
         ce = [torch.cuda.Event(enable_timing=True) for _ in range(6)] if timed else None
-        hs.wait_event(ev_done[b])
-        with torch.cuda.stream(hs):
-            if ce:
-                ce[0].record(hs)
-            xd[b].copy_(xh, non_blocking=True)
-            if ce:
-                ce[1].record(hs)
-        ev_in[b].record(hs)
+        if i + 1 < n:
+            h2d(i + 1, timed)
         ks.wait_event(ev_in[b])
         ks.wait_event(ev_out[b])
         ks.wait_event(ev_out2[b])
+        if ce:
+            ce[4].record(ks)
         nat.rtis_process_many(h, xd[b], B, Ed_td[b], Ed_fd[b], ksh)
+        if ce:
+            ce[5].record(ks)
         ev_done[b].record(ks)
         cs.wait_event(ev_done[b])
         cs2.wait_event(ev_done[b])
         with torch.cuda.stream(cs):
             if ce:
-                ce[2].record(cs)
+                ce[0].record(cs)
             Eh_td[b].copy_(Ed_td[b], non_blocking=True)
             if ce:
-                ce[3].record(cs)
+                ce[1].record(cs)
         with torch.cuda.stream(cs2):
             if ce:
-                ce[4].record(cs2)
+                ce[2].record(cs2)
             Eh_fd[b].copy_(Ed_fd[b], non_blocking=True)
             if ce:
-                ce[5].record(cs2)
+                ce[3].record(cs2)
         ev_out[b].record(cs)
         ev_out2[b].record(cs2)
         if ce:
             copy_ev.append(ce)
 
-    for i in range(2):
-        e2e_step(i)
+    def run_e2e(n, timed):
+        h2d(0, timed)
+        for i in range(n):
+            e2e_step(i, n, timed)
+
+    run_e2e(2, False)
     torch.cuda.synchronize()
     e2e_steps = max(args.steps // 2, 3)
     ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ee0.record(ks)
     for c in (hs, cs, cs2):
         c.wait_event(ee0)
-    for i in range(e2e_steps):
-        e2e_step(i, timed=True)
+    run_e2e(e2e_steps, True)
     for e_ in ev_out + ev_out2:
         ks.wait_event(e_)
     ee1.record(ks)
@@ -1115,7 +1141,14 @@ def run_hemisphere_batched(args, rank, world, local):
     # the same copies' durations inside the loop, where they overlap compute and each other
     link["in_loop_ms_per_step"] = {
         name: statistics.median(ce[a].elapsed_time(ce[a + 1]) for ce in copy_ev)
-        for name, a in (("h2d", 0), ("d2h_td", 2), ("d2h_fd", 4))}
+        for name, a in (("d2h_td", 0), ("d2h_fd", 2), ("compute", 4))}
+    link["in_loop_ms_per_step"]["h2d"] = statistics.median(e[0].elapsed_time(e[1]) for e in h2d_ev)
+    # idle time of the compute stream between one step's compute and the next one's
+    gaps = [copy_ev[i][5].elapsed_time(copy_ev[i + 1][4]) for i in range(len(copy_ev) - 1)]
+    link["compute_gap_ms"] = {"mean": statistics.mean(gaps), "max": max(gaps)} if gaps else None
+    link["compute_ms_mean"] = statistics.mean(ce[4].elapsed_time(ce[5]) for ce in copy_ev)
+    link["before_first_compute_ms"] = ee0.elapsed_time(copy_ev[0][4])
+    link["after_last_compute_ms"] = copy_ev[-1][5].elapsed_time(ee1)
     link["e2e_ms_per_step"] = 1e3 * t_e2e / e2e_steps
 
     if world > 1:
