@@ -30,6 +30,9 @@
 namespace rtis {
 namespace {
 
+// coarse low-pass taps per residue class for R = 10 and the 41-tap filter
+constexpr int kBbFastTaps = 11;
+
 using ptx::fma2;
 using ptx::mul2;
 using ptx::pack2;
@@ -280,7 +283,12 @@ __global__ void __launch_bounds__(kBbThreads, 1)
                 const float* e = env + (jlo - jS);
                 const float* hc = hs + (num & 3) * A.ntap;  // taps for this residue of R i - half
                 float acc_e = 0.f;
-                for (int l = 0; l < A.ntap; ++l) acc_e = fmaf(hc[l], e[l], acc_e);
+                if (A.ntap == kBbFastTaps) {  // R = 10 with the 41-tap low-pass: unrolled, same order
+#pragma unroll
+                    for (int l = 0; l < kBbFastTaps; ++l) acc_e = fmaf(hc[l], e[l], acc_e);
+                } else {
+                    for (int l = 0; l < A.ntap; ++l) acc_e = fmaf(hc[l], e[l], acc_e);
+                }
                 if (!isfinite(acc_e)) atomicOr(A.status, RTIS_DEV_NONFINITE);
                 Erow[i] = acc_e;
             }
