@@ -50,9 +50,9 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each beamformer (ncu capture of this
 # workload, see profiles/); set to None whenever that kernel changes until it is re-captured
 TD_TRAFFIC_BYTES = 5552896
-FD_TRAFFIC_BYTES = None  # the per-direction kernel's last pass changed since its capture (1.79 MB then)
-# bb_beamform_kernel on the hemisphere workload (the <4, 5> layout; z and the tables, E stays in L2)
-BB_TRAFFIC_BYTES = 2921472
+FD_TRAFFIC_BYTES = 1774592  # the per-direction kernel (--batch 1): ncu prints 1.77 MB read, 0 written
+# bb_beamform_kernel on the hemisphere workload (the <8, 4> layout; z and the tables, E stays in L2)
+BB_TRAFFIC_BYTES = 2937344 + 512
 # td_adjoint_kernel on the calibration workload (32 x 16384 x 2048)
 ADJ_TRAFFIC_BYTES = 20026112 + 44800
 # fd_gemm_kernel_ws<BF16> captured at 400 bins (DRAM read + write), per bin; X and Y both grow with the bins
