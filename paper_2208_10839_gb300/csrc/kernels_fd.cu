@@ -26,10 +26,10 @@
 // while it walks consecutive bins.  Per item: X of the next bin arrives by a
 // bulk async copy; A and B are built; one thread issues the MMAs; an earlier
 // item's accumulator goes TMEM -> registers -> 128B-swizzled shared staging
-// -> 3-D TMA tensor stores (which clip ragged tiles and frames).  With BF16
-// or FP16 operands separate warps build and drain, overlapping the two; the
-// FP32 mode's larger build (hi and lo halves of both operands) keeps all
-// warps on both in turn.
+// -> 3-D TMA tensor stores (which clip ragged tiles and frames).  Separate
+// warps build and drain, so the two overlap: 8 and 8 with BF16 or FP16
+// operands, 16 and 4 in the FP32 mode, whose build (hi and lo halves of both
+// operands) is twice as large.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -43,7 +43,6 @@
 namespace rtis {
 namespace {
 
-constexpr int kFdThreads = 512;
 constexpr int kFdDirTile = 128;  // directions per item (MMA M)
 constexpr int kFdFrames = 64;    // frames per item (MMA N = 128)
 constexpr int kFdK = 64;         // 2 x 32 mics
@@ -131,254 +130,24 @@ struct FdSmem {
     static constexpr uint32_t ALLOC = BYTES + 1024;                  // room to align the base
 };
 
-// The form for the FP32 mode (three BF16 products): every warp builds its share of item j's
-// operands, one thread issues the MMAs, and the same warps then drain item j - 1 (its MMAs ran
-// while item j was being built).  The FP32 mode's operand build (hi and lo halves) is the
-// larger share of an item, so it keeps all 16 warps.
-template <int PREC>
-__global__ void __launch_bounds__(kFdThreads, 1)
-    fd_gemm_kernel_sync(const __grid_constant__ CUtensorMap ymap, const FdArgs args) {
-    using L = FdSmem<PREC>;
-    constexpr uint32_t NCOL = 2 * kFdFrames;  // accumulator columns per buffer
-    constexpr uint32_t IDESC = ptx::idesc_f16(PREC == RTIS_PREC_FP16 ? 0u : 1u, 128u, NCOL);
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    unsigned char* sm = sm_raw + ((1024 - (ptx::smem_u32(sm_raw) & 1023)) & 1023);
-    uint64_t* mma_bar = reinterpret_cast<uint64_t*>(sm + L::BAR_OFF);  // [2]
-    uint64_t* x_bar = mma_bar + 2;                                       // [2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(x_bar + 4);   // the same layout as the other form
-    float* s_scale = reinterpret_cast<float*>(tmem_slot + 1);  // [65]: s_m, S, 1/s_m
-    auto A_ptr = [&](int buf, int split) { return sm + L::A_OFF + (buf * L::NSPLIT + split) * L::OP_BYTES; };
-    auto B_ptr = [&](int buf, int split) { return sm + L::B_OFF + (buf * L::NSPLIT + split) * L::OP_BYTES; };
-    auto X_ptr = [&](int buf) { return reinterpret_cast<float2*>(sm + L::X_OFF + buf * L::X_BYTES); };
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int M = args.M, D = args.D, T = args.T, K = args.K;
-    const int first = static_cast<int>((static_cast<long long>(blockIdx.x) * args.n_items) / gridDim.x);
-    const int last = static_cast<int>((static_cast<long long>(blockIdx.x + 1) * args.n_items) / gridDim.x);
-    const int n_local = last - first;
-    const uint32_t x_bytes = static_cast<uint32_t>(M * T * 8);
-
-    if (warp == 0) {
-        ptx::tmem_alloc(tmem_slot, 2 * NCOL);
-        ptx::tmem_relinquish();
-    }
-    if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
-            ptx::mbar_init(&mma_bar[i], 1);
-            ptx::mbar_init(&x_bar[i], 1);
-        }
-        ptx::fence_mbar_init();
-        if (args.tma_y) ptx::prefetch_tmap(&ymap);
-    }
-    if (tid < 32) {
-        // s_m = smallest power of two >= max |Re X|, |Im X| of mic m (1 if silent or not finite)
-        float s = 1.f;
-        if (tid < M) {
-            const float amax = __uint_as_float(reinterpret_cast<const unsigned*>(args.scale)[tid]);
-            if (amax > 0.f && isfinite(amax)) s = exp2f(ceilf(log2f(amax)));
-        }
-        float mx = tid < M ? s : 0.f;
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        s_scale[tid] = s;
-        s_scale[33 + tid] = 1.0f / s;  // exact: s is a power of two
-        if (tid == 0) s_scale[32] = mx;
-    }
-    ptx::tc_fence_before();
-    __syncthreads();
-    ptx::tc_fence_after();
-    const float S = s_scale[32];
-    const uint32_t tmem = *tmem_slot;
-
-    auto issue_x = [&](int j) {  // thread 0: bin of local item j -> X buffer j & 1
-        if (!args.bulk_x || j >= n_local) return;
-        const int k = (first + j) % K;
-        ptx::mbar_arrive_expect_tx(&x_bar[j & 1], x_bytes);
-        ptx::bulk_load(X_ptr(j & 1), args.X + static_cast<size_t>(k) * M * T, x_bytes, &x_bar[j & 1]);
-    };
-    if (tid == 0) issue_x(0);
-
-    // A role: 128 directions x 4 mic octets
-    const int dl = tid & 127, mo = tid >> 7;
-    float gsc[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int m = mo * 8 + i;
-        gsc[i] = m < M ? __ldg(args.gain + m) * (s_scale[m] / S) : 0.f;
-    }
-    float2 tv[8];
-    int tile_loaded = -1;
-    // B role: 64 frames x 4 mic octets x {row 2t, row 2t+1}
-    const int bt = tid & 63, bo = (tid >> 6) & 3, bpart = tid >> 8;
-    float bsc[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int m = bo * 8 + i;
-        bsc[i] = (m < M && bt < T) ? s_scale[33 + m] : 0.f;  // zero also masks padded mics and frames
-    }
-
-    // drain role: TMEM lane quarter q = warp % 4 (rows), column quarter h = warp / 4;
-    // each warp stores its own 32-row x 128-byte box
-    const int q = warp & 3, h = warp >> 2;
-    const int row = 32 * q + lane;
-    unsigned char* stg = sm + L::STG_OFF + warp * L::STG_WARP;
-    bool timed_out = false;
-
-    auto wait_bar = [&](uint64_t* bar, uint32_t parity) {
-        if (!timed_out && !ptx::mbar_wait_bounded(bar, parity, kFdPolls)) {
-            timed_out = true;
-            atomicOr(args.status, RTIS_DEV_TIMEOUT);
-        }
-    };
-
-    // Iteration j: build item j's operands (buffer j & 1), issue its MMAs, then
-    // drain item j-1 (its MMAs ran while item j was being built).
-    int tile = first / K, k = first - tile * K;  // item j = tile * K + k
-    int ptile = tile, pk = k;                     // item j - 1
-    float2 f_next = n_local > 0 ? __ldg(args.freq + k) : make_float2(0.f, 0.f);
-    for (int j = 0; j <= n_local; ++j) {
-        const int b = j & 1;
-        if (j < n_local) {
-            if (tid == 0) issue_x(j + 1);  // its X buffer was last read before the previous barrier
-            const float2 f = f_next;
-            {  // frequency of item j + 1
-                const int kn = (k + 1 == K) ? 0 : k + 1;
-                if (j + 1 < n_local) f_next = __ldg(args.freq + kn);
-            }
-            if (args.bulk_x) wait_bar(&x_bar[b], static_cast<uint32_t>((j >> 1) & 1));
-            {
-                float va[8], vb[8];  // row 2t: [Re X | -Im X], row 2t+1: [Im X | Re X]
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int m = bo * 8 + i;
-                    float2 x = make_float2(0.f, 0.f);
-                    if (bsc[i] != 0.f)
-                        x = args.bulk_x ? X_ptr(b)[m * T + bt]
-                                        : __ldg(args.X + (static_cast<size_t>(k) * M + m) * T + bt);
-                    const float xr = x.x * bsc[i], xi = x.y * bsc[i];
-                    va[i] = bpart ? xi : xr;
-                    vb[i] = bpart ? xr : -xi;
-                }
-                store_chunk<PREC>(B_ptr(b, 0), B_ptr(b, L::NSPLIT - 1), kmajor_off(2 * bt + bpart, bo), va);
-                store_chunk<PREC>(B_ptr(b, 0), B_ptr(b, L::NSPLIT - 1), kmajor_off(2 * bt + bpart, 4 + bo), vb);
-            }
-            if (tile != tile_loaded) {
-                const int d = tile * kFdDirTile + dl;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int m = mo * 8 + i;
-                    tv[i] = (d < D && m < M) ? __ldg(args.tau + static_cast<size_t>(d) * M + m) : make_float2(0.f, 0.f);
-                }
-                tile_loaded = tile;
-            }
-            float wr[8], wi[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                float sn, cs;
-                __sincosf(6.28318530717958647692f * phase_cycles(f, tv[i]), &sn, &cs);
-                wr[i] = cs * gsc[i];
-                wi[i] = sn * gsc[i];
-            }
-            store_chunk<PREC>(A_ptr(b, 0), A_ptr(b, L::NSPLIT - 1), kmajor_off(dl, mo), wr);
-            store_chunk<PREC>(A_ptr(b, 0), A_ptr(b, L::NSPLIT - 1), kmajor_off(dl, 4 + mo), wi);
-            // operands visible to the tensor core; accumulator b's last reads (item j-2) retired
-            ptx::fence_proxy_async();
-            ptx::tc_fence_before();
-            __syncthreads();
-            ptx::tc_fence_after();
-            if (tid == 0 && !timed_out) {
-                const uint32_t d_tmem = tmem + static_cast<uint32_t>(b) * NCOL;
-#pragma unroll
-                for (int pass = 0; pass < L::NPASS; ++pass) {
-                    const unsigned char* Ap = A_ptr(b, pass == 2 ? 1 : 0);
-                    const unsigned char* Bp = B_ptr(b, pass == 1 ? 1 : 0);
-#pragma unroll
-                    for (int ks = 0; ks < kFdK / 16; ++ks) {
-                        const uint64_t ad = ptx::smem_desc_kmajor(Ap + ks * 2 * kFdLbo, kFdLbo, kFdSbo);
-                        const uint64_t bd = ptx::smem_desc_kmajor(Bp + ks * 2 * kFdLbo, kFdLbo, kFdSbo);
-                        ptx::tc_mma_f16(d_tmem, ad, bd, IDESC, (pass | ks) != 0 ? 1u : 0u);
-                    }
-                }
-                ptx::tc_commit(&mma_bar[b]);
-            }
-        }
-        // drain item j-1: accumulator b^1 -> registers -> this warp's staging box -> TMA
-        if (j > 0) {
-            wait_bar(&mma_bar[b ^ 1], static_cast<uint32_t>(((j - 1) >> 1) & 1));
-            ptx::tc_fence_after();
-            if (!__any_sync(0xffffffffu, timed_out)) {
-                uint32_t r[32];
-                ptx::tmem_ld_32x32b_x32(
-                    tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(b ^ 1) * NCOL + 32u * h, r);
-                ptx::tmem_ld_wait_regs(r);
-                ptx::tc_fence_before();
-                if (args.tma_y) {
-                    if (lane == 0) ptx::bulk_wait_read0();  // this warp's previous box has been read
-                    __syncwarp();
-                    // row `lane`, 16-byte chunk c at (c ^ (lane & 7)): the 128B swizzle
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const float4 v =
-                            make_float4(S * __uint_as_float(r[4 * c]), S * __uint_as_float(r[4 * c + 1]),
-                                        S * __uint_as_float(r[4 * c + 2]), S * __uint_as_float(r[4 * c + 3]));
-                        *static_cast<float4*>(__builtin_assume_aligned(stg + lane * 128 + ((c ^ (lane & 7)) << 4), 16)) = v;
-                    }
-                    ptx::fence_proxy_async();
-                    __syncwarp();
-                    if (lane == 0) {
-                        if (args.y_dkt)
-                            ptx::tma_store_3d(&ymap, stg, 32 * h, pk, ptile * kFdDirTile + 32 * q);
-                        else
-                            ptx::tma_store_3d(&ymap, stg, 32 * h, ptile * kFdDirTile + 32 * q, pk);
-                        ptx::bulk_commit();
-                    }
-                } else {
-                    const int d = ptile * kFdDirTile + row;
-                    if (d < D) {
-                        float2* dst = args.Y + (args.y_dkt ? (static_cast<size_t>(d) * K + pk)
-                                                           : (static_cast<size_t>(pk) * D + d)) * T;
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) {
-                            const int t = 16 * h + c;
-                            if (t < T)
-                                dst[t] = make_float2(S * __uint_as_float(r[2 * c]), S * __uint_as_float(r[2 * c + 1]));
-                        }
-                    }
-                }
-            }
-        }
-        ptile = tile;
-        pk = k;
-        if (++k == K) {
-            k = 0;
-            ++tile;
-        }
-    }
-    if (lane == 0 && args.tma_y) ptx::bulk_wait0();
-
-    // on a timeout: give MMAs and copies in flight a bounded chance to finish before TMEM is released
-    if (__syncthreads_or(timed_out)) {
-        if (tid == 0) {
-            for (int i = 0; i < 2; ++i) {
-                ptx::mbar_wait_bounded(&mma_bar[i], 0u, kFdPolls);
-                ptx::mbar_wait_bounded(&mma_bar[i], 1u, kFdPolls);
-                ptx::mbar_wait_bounded(&x_bar[i], 0u, kFdPolls);
-                ptx::mbar_wait_bounded(&x_bar[i], 1u, kFdPolls);
-            }
-        }
-        __syncthreads();
-    }
-    ptx::tc_fence_after();
-    if (warp == 0) ptx::tmem_dealloc(tmem, 2 * NCOL);
-}
-
-// The form for BF16 and FP16 operands: warp-specialised.  Warps 0-7 build item j's operands
-// (X and W into buffer j & 1) and thread 0 issues its MMAs once every builder has passed a named
-// barrier; warps 8-15 drain accumulators (TMEM -> registers -> swizzled staging -> TMA store).
+// The warp-specialised form: NB builder warps build item j's operands (X and W into buffer
+// j & 1) and thread 0 issues its MMAs once every builder has passed a named barrier; the drain
+// warps after them empty the accumulators (TMEM -> registers -> swizzled staging -> TMA store).
 // The two groups hand over through mbarriers: mma_bar (MMAs of an item retired: its operand
-// buffer is free and its accumulator ready) and tfree (an accumulator drained).
-template <int PREC>
-__global__ void __launch_bounds__(kFdThreads, 1)
+// buffer is free and its accumulator ready) and tfree (an accumulator drained).  NB = 8 (BF16,
+// FP16: 8 drain warps, each builder thread two mic octets of W and both rows of a frame's X
+// octet) or 16 (FP32, whose hi/lo build is twice as large: 4 drain warps, each builder thread one
+// octet of W and one row of X, as in the all-warps form).
+template <int NB>
+__host__ __device__ constexpr int fd_ws_threads() { return 32 * (NB + (NB == 8 ? 8 : 4)); }
+
+template <int PREC, int NB>
+__global__ void __launch_bounds__(fd_ws_threads<NB>(), 1)
     fd_gemm_kernel_ws(const __grid_constant__ CUtensorMap ymap, const FdArgs args) {
+    static_assert(NB == 8 || NB == 16, "8 or 16 builder warps");
+    constexpr int NDW = NB == 8 ? 8 : 4;       // drain warps
+    constexpr int NOCT = NB == 8 ? 2 : 1;      // W mic octets per builder thread
+    constexpr int GPW = 16 / NDW;              // 32-column groups per drain warp
     using L = FdSmem<PREC>;
     constexpr uint32_t NCOL = 2 * kFdFrames;  // accumulator columns per buffer
     constexpr uint32_t IDESC = ptx::idesc_f16(PREC == RTIS_PREC_FP16 ? 0u : 1u, 128u, NCOL);
@@ -408,7 +177,7 @@ __global__ void __launch_bounds__(kFdThreads, 1)
         for (int i = 0; i < 2; ++i) {
             ptx::mbar_init(&mma_bar[i], 1);
             ptx::mbar_init(&x_bar[i], 1);
-            ptx::mbar_init(&tfree[i], kFdThreads / 64);  // the drain warps
+            ptx::mbar_init(&tfree[i], NDW);  // the drain warps
         }
         ptx::fence_mbar_init();
         if (args.tma_y) ptx::prefetch_tmap(&ymap);
@@ -448,23 +217,24 @@ __global__ void __launch_bounds__(kFdThreads, 1)
         }
     };
 
-    if (warp < kFdThreads / 64) {
-        // ---------------- builders (warps 0-7): X and W into the operand buffers, then the MMAs
-        const int bt_id = tid;                           // 0 .. 255
-        // A role: 128 directions x mic octets {mo, mo + 2}
+    if (warp < NB) {
+        // ---------------- builders: X and W into the operand buffers, then the MMAs
+        const int bt_id = tid;                           // 0 .. 32 NB - 1
+        // A role: 128 directions x mic octets {mo0, mo0 + 2} (NB = 8) or {mo0} (NB = 16)
         const int dl = bt_id & 127, mo0 = bt_id >> 7;
-        float gsc[2][8];
+        float gsc[NOCT][8];
 #pragma unroll
-        for (int o = 0; o < 2; ++o)
+        for (int o = 0; o < NOCT; ++o)
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int m = (mo0 + 2 * o) * 8 + i;
                 gsc[o][i] = m < M ? __ldg(args.gain + m) * (s_scale[m] / S) : 0.f;
             }
-        float2 tv[2][8];
+        float2 tv[NOCT][8];
         int tile_loaded = -1;
-        // B role: frame bt, mic octet bo, both rows 2t ([Re X | -Im X]) and 2t + 1 ([Im X | Re X])
-        const int bt = bt_id & 63, bo = bt_id >> 6;
+        // B role: frame bt, mic octet bo; rows 2t ([Re X | -Im X]) and 2t + 1 ([Im X | Re X]),
+        // both (NB = 8) or row 2t + bpart (NB = 16)
+        const int bt = bt_id & 63, bo = (bt_id >> 6) & 3, bpart = bt_id >> 8;
         float bsc[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -499,14 +269,18 @@ __global__ void __launch_bounds__(kFdThreads, 1)
                     wa[i] = xi;
                     wb[i] = xr;
                 }
-                store_chunk<PREC>(B_ptr(b, 0), B_ptr(b, L::NSPLIT - 1), kmajor_off(2 * bt, bo), va);
-                store_chunk<PREC>(B_ptr(b, 0), B_ptr(b, L::NSPLIT - 1), kmajor_off(2 * bt, 4 + bo), vb);
-                store_chunk<PREC>(B_ptr(b, 0), B_ptr(b, L::NSPLIT - 1), kmajor_off(2 * bt + 1, bo), wa);
-                store_chunk<PREC>(B_ptr(b, 0), B_ptr(b, L::NSPLIT - 1), kmajor_off(2 * bt + 1, 4 + bo), wb);
+                if (NB == 8 || bpart == 0) {
+                    store_chunk<PREC>(B_ptr(b, 0), B_ptr(b, L::NSPLIT - 1), kmajor_off(2 * bt, bo), va);
+                    store_chunk<PREC>(B_ptr(b, 0), B_ptr(b, L::NSPLIT - 1), kmajor_off(2 * bt, 4 + bo), vb);
+                }
+                if (NB == 8 || bpart == 1) {
+                    store_chunk<PREC>(B_ptr(b, 0), B_ptr(b, L::NSPLIT - 1), kmajor_off(2 * bt + 1, bo), wa);
+                    store_chunk<PREC>(B_ptr(b, 0), B_ptr(b, L::NSPLIT - 1), kmajor_off(2 * bt + 1, 4 + bo), wb);
+                }
                 if (tile != tile_loaded) {
                     const int d = tile * kFdDirTile + dl;
 #pragma unroll
-                    for (int o = 0; o < 2; ++o)
+                    for (int o = 0; o < NOCT; ++o)
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
                             const int m = (mo0 + 2 * o) * 8 + i;
@@ -516,7 +290,7 @@ __global__ void __launch_bounds__(kFdThreads, 1)
                     tile_loaded = tile;
                 }
 #pragma unroll
-                for (int o = 0; o < 2; ++o) {
+                for (int o = 0; o < NOCT; ++o) {
                     float wr[8], wi[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -532,7 +306,7 @@ __global__ void __launch_bounds__(kFdThreads, 1)
             }
             // the operands are visible to the tensor core once every builder has passed here
             ptx::fence_proxy_async();
-            asm volatile("bar.sync 1, %0;" ::"n"(kFdThreads / 2) : "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * NB) : "memory");
             if (bt_id == 0) {
                 // accumulator b was last read by the drain of item j - 2
                 if (j >= 2) wait_bar(&tfree[b], static_cast<uint32_t>(((j - 2) >> 1) & 1));
@@ -559,9 +333,9 @@ __global__ void __launch_bounds__(kFdThreads, 1)
             }
         }
     } else {
-        // ---------------- drain (warps 8-15): accumulator -> registers -> staging -> TMA
-        // TMEM lane quarter q, frame half h: column groups 2h, 2h + 1 (32 columns = 16 frames each)
-        const int dw = warp - kFdThreads / 64;
+        // ---------------- drain: accumulator -> registers -> staging -> TMA
+        // TMEM lane quarter q; column groups GPW h .. GPW h + GPW - 1 (32 columns = 16 frames each)
+        const int dw = warp - NB;
         const int q = dw & 3, h = dw >> 2;
         const int row = 32 * q + lane;
         for (int j = 0; j < n_local; ++j) {
@@ -572,9 +346,9 @@ __global__ void __launch_bounds__(kFdThreads, 1)
             ptx::tc_fence_after();
             if (!__any_sync(0xffffffffu, timed_out)) {
 #pragma unroll
-                for (int c2 = 0; c2 < 2; ++c2) {
-                    const int cg = 2 * h + c2;
-                    unsigned char* stg = sm + L::STG_OFF + (2 * dw + c2) * L::STG_WARP;
+                for (int c2 = 0; c2 < GPW; ++c2) {
+                    const int cg = GPW * h + c2;
+                    unsigned char* stg = sm + L::STG_OFF + (GPW * dw + c2) * L::STG_WARP;
                     uint32_t r[32];
                     ptx::tmem_ld_32x32b_x32(
                         tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(b) * NCOL + 32u * cg, r);
@@ -674,11 +448,12 @@ __global__ void __launch_bounds__(256) fd_absmax_kernel(const float2* __restrict
 template <int PREC>
 cudaError_t fd_launch_t(const CUtensorMap& ymap, const FdArgs& a, int grid, cudaStream_t st) {
     const size_t sm = FdSmem<PREC>::ALLOC;
-    // FP32 (three BF16 products): the all-warps form; BF16 / FP16: the warp-specialised form
-    auto kern = (PREC == RTIS_PREC_FP32) ? fd_gemm_kernel_sync<PREC> : fd_gemm_kernel_ws<PREC>;
+    // warp-specialised: 8 builder and 8 drain warps (BF16 / FP16), 16 and 4 (FP32)
+    constexpr int NB = (PREC == RTIS_PREC_FP32) ? 16 : 8;
+    auto kern = fd_gemm_kernel_ws<PREC, NB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
     if (e != cudaSuccess) return e;
-    kern<<<grid, kFdThreads, sm, st>>>(ymap, a);
+    kern<<<grid, fd_ws_threads<NB>(), sm, st>>>(ymap, a);
     return cudaGetLastError();
 }
 
