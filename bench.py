@@ -50,7 +50,7 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each beamformer (ncu capture of this
 # workload, see profiles/); set to None whenever that kernel changes until it is re-captured
 TD_TRAFFIC_BYTES = 5552896
-FD_TRAFFIC_BYTES = 1774592  # the per-direction kernel (--batch 1): ncu prints 1.77 MB read, 0 written
+FD_TRAFFIC_BYTES = None  # the per-direction kernel (--batch 1); changed since its last capture
 # bb_beamform_kernel on the hemisphere workload (the <8, 4> layout; z and the tables, E stays in L2)
 BB_TRAFFIC_BYTES = 2937344 + 512
 # td_adjoint_kernel on the calibration workload (32 x 16384 x 2048)

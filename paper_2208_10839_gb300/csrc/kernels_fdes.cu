@@ -340,7 +340,11 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fd_energyscape_kernel(c
     static_assert(NZ >= 1 && NZ <= R0, "nonzero first-pass slots");
     float* env = reinterpret_cast<float*>(fbuf);  // |b(4p + q)|, written by the last pass
     const int half = (a.lpf_len - 1) >> 1;
-    // the register fold: outputs i = tid + NT m, m < kFoldOut; taps j0 + 4 s, s < kFoldTaps
+    // the register fold: outputs i = tid + NT m, m < kFoldOut; taps j0 + 4 s, s < kFoldTaps.
+    // The sums over the phases stay in registers (FACC_REGS) or go to the thread's own entries
+    // of Eacc: the per-direction kernel, whose steering loop needs the registers, measured
+    // faster with Eacc (spills 56 -> 36 B), the from-Y kernel with the registers
+    constexpr bool FACC_REGS = FROM_Y;
     float facc[kFoldOut];
 #pragma unroll
     for (int m = 0; m < kFoldOut; ++m) facc[m] = 0.f;
@@ -396,7 +400,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fd_energyscape_kernel(c
                         for (int s4 = 0; s4 < kFoldTaps; ++s4)
                             if (e0 + s4 >= 0) acc = fmaf(hreg[s4], env[e0 + s4], acc);
                     }
-                    facc[m] += acc;
+                    if constexpr (FACC_REGS)
+                        facc[m] += acc;
+                    else
+                        Eacc[i] += acc;
                 }
             }
         } else {
@@ -416,7 +423,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) fd_energyscape_kernel(c
         __syncthreads();
     }
     float* Erow = a.E + (static_cast<size_t>(t_meas) * a.D + d) * a.n_out;
-    if constexpr (FOLD) {
+    if constexpr (FOLD && FACC_REGS) {
 #pragma unroll
         for (int m = 0; m < kFoldOut; ++m) {
             const int i = tid + m * NT;
