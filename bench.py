@@ -1182,11 +1182,17 @@ def run_hemisphere_batched(args, rank, world, local):
     gemm_ms = statistics.mean(launch_ms.get("fd_gemm", [float("nan")]))
     gemm_bytes = float(plan.Kb) * N_MICS * B * 8 + float(plan.Kb) * N_DIRS * B * 8
     hbm = load_peaks().get("hbm_gbs")
+    # the IFFT kernel's memory side: Y read once (K_b x D complex per measurement), E written once
+    fdes_bytes = (float(plan.Kb) * N_DIRS * 8 + float(N_DIRS) * plan.n_out * 4) * B
+    fdes_gbs = fdes_bytes / (fdes_ms / 1e3) / 1e9
     rooflines_other = {
         "fd_energyscape_kernel": {"bound": "alu", "achieved": fdes_flops * B / (fdes_ms / 1e3) / 1e12, "peak": peak_tf,
                                   "unit": "TFLOP/s", "frac": fdes_flops * B / (fdes_ms / 1e3) / 1e12 / peak_tf,
                                   "launch_ms": fdes_ms, "measurements_per_launch": B,
-                                  "algorithmic_flops_per_launch": fdes_flops * B, "timing": timing},
+                                  "algorithmic_flops_per_launch": fdes_flops * B, "timing": timing,
+                                  "hbm": {"algorithmic_bytes_per_launch": fdes_bytes, "achieved": fdes_gbs,
+                                          "peak": hbm, "unit": "GB/s",
+                                          "frac": fdes_gbs / hbm if hbm else None}},
         "fd_gemm_kernel": {"bound": "hbm", "achieved": gemm_bytes / (gemm_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                            "frac": gemm_bytes / (gemm_ms / 1e3) / 1e9 / hbm if hbm else None, "launch_ms": gemm_ms,
                            "algorithmic_bytes_per_launch": gemm_bytes, "precision": "fp32 (3 x bf16)",
