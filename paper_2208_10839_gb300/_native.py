@@ -29,6 +29,7 @@ RTIS_DEV_TIMEOUT = 0x2
 RTIS_DEV_NONFINITE = 0x4
 RTIS_PATH_TD, RTIS_PATH_FD, RTIS_PATH_BB = 0, 1, 2
 RTIS_PREC_FP32, RTIS_PREC_BF16, RTIS_PREC_FP16 = 0, 1, 2
+RTIS_FD_IFFT_AUTO, RTIS_FD_IFFT_FFT, RTIS_FD_IFFT_TC = 0, 1, 2
 
 
 class rtis_options(C.Structure):

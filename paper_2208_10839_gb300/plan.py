@@ -43,7 +43,7 @@ class Plan:
         o.grid_mode = {"tile": 1, "persistent": 2}[grid]
         # process_many's frequency-domain inverse transform: "auto" (the faster form, today the FFT),
         # "fft" (FFT kernel on the FP32 pipe) or "tc" (dense DFT stages on the tensor cores, or fail)
-        o.fd_ifft = {"auto": 0, "fft": 1, "tc": 2}[fd_ifft]
+        o.fd_ifft = {"auto": nat.RTIS_FD_IFFT_AUTO, "fft": nat.RTIS_FD_IFFT_FFT, "tc": nat.RTIS_FD_IFFT_TC}[fd_ifft]
         self.handle = nat.rtis_plan_create(mic_xyz, fs, chirp, directions, n_samples, o)
         self.info_path = path
         self.info = nat.rtis_plan_get_info(self.handle)

@@ -180,6 +180,46 @@ def test_pdm_and_baseband_argument_checks(nat):
     assert lib.rtis_beamform_bb(None, None, None, None) == E
 
 
+def test_binding_mirrors_header_layouts_and_constants(nat, tmp_path):
+    """Each ctypes mirror of a header struct has the header's size and field offsets, and each
+    constant of the binding the header's value: a mirror that drifted from rtis.h would pass
+    wrong arguments to every call that takes it.  A C program built against the header prints
+    the header's side."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not found")
+    structs = [nat.rtis_options, nat.rtis_plan_info, nat.rtis_batch_info, nat.rtis_trace_entry]
+    consts = [n for n in dir(nat) if re.fullmatch(r"RTIS_(OK|ERR_[A-Z_]+|DEV_[A-Z_]+|PATH_[A-Z]+|PREC_[A-Z0-9]+|"
+                                                 r"FD_IFFT_[A-Z]+)", n)]
+    kernel_ids = {f"RTIS_KERNEL_{name.upper()}": kid for kid, name in nat.KERNEL_NAMES.items()}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "rtis.h"', "int main(void) {"]
+    for st in structs:
+        lines.append(f'printf("{st.__name__} sizeof %zu\\n", sizeof({st.__name__}));')
+        for field, _ in st._fields_:
+            lines.append(f'printf("{st.__name__} {field} %zu\\n", offsetof({st.__name__}, {field}));')
+    for name in consts + sorted(kernel_ids) + ["RTIS_TRACE_MAX"]:
+        lines.append(f'printf("const {name} %ld\\n", (long)({name}));')
+    lines.append("return 0; }")
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    header = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln}
+    for st in structs:
+        assert header[(st.__name__, "sizeof")] == C.sizeof(st), st.__name__
+        for field, _ in st._fields_:
+            assert header[(st.__name__, field)] == getattr(st, field).offset, (st.__name__, field)
+    for name in consts:
+        assert header[("const", name)] == getattr(nat, name), name
+    for name, kid in kernel_ids.items():
+        assert header[("const", name)] == kid, name
+    assert header[("const", "RTIS_TRACE_MAX")] == nat.TRACE_MAX
+    assert len(consts) >= 17  # the statuses, device bits, paths, precisions and IFFT forms
+
+
 def test_header_is_plain_c(tmp_path):
     # the boundary is a C ABI: the header compiles as strict C99 (and as C++), no torch types
     import shutil
