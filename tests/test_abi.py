@@ -57,6 +57,8 @@ def test_options_default(nat):
     assert o.c == 343.0 and o.decim == 10 and o.lpf_len == 0
     assert o.band_lo_hz == 20e3 and o.band_hi_hz == 80e3
     assert o.path == nat.RTIS_PATH_TD and o.precision == nat.RTIS_PREC_FP32
+    assert o.max_batch == 0 and o.td_layout == 0 and o.bb_layout == 0 and o.grid_mode == 0
+    assert o.fd_ifft == nat.RTIS_FD_IFFT_AUTO
 
 
 def _args():
@@ -80,6 +82,8 @@ def _args():
     (dict(td_layout=6), 1),               # 5 time-domain layouts
     (dict(bb_layout=7), 1),               # 6 baseband layouts
     (dict(grid_mode=3), 1),
+    (dict(fd_ifft=3), 1),                 # AUTO, FFT or TC
+    (dict(fd_ifft=-1), 1),
 ])
 def test_plan_create_rejects(nat, kw, status):
     mic, ch, dirs = _args()
@@ -99,7 +103,7 @@ def test_plan_create_rejects(nat, kw, status):
         o.precision = kw["precision"]
     if "path" in kw:
         o.path = kw["path"]
-    for f in ("td_layout", "bb_layout", "grid_mode"):
+    for f in ("td_layout", "bb_layout", "grid_mode", "fd_ifft"):
         if f in kw:
             setattr(o, f, kw[f])
     with pytest.raises(nat.RtisError) as ei:
